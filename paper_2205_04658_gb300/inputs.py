@@ -1,0 +1,94 @@
+"""Seeded synthetic inputs shared by the CUDA path and its checks.
+
+This module holds input generators only (initial macroscopic fields, impurity
+masks, workload shapes); none of the update's arithmetic lives here.  Every
+generator is deterministic in its seed.
+
+Workload shapes follow the paper's runs: square periodic lattices stirred in a
+shell of wave numbers (Part I, "Model and Methods"), and a wide sample with
+circular impurities (Part II, "Model and Methods"), with dt = 0.05.
+"""
+import numpy as np
+
+
+def shear_wave(nx, ny, amp=0.01):
+    """u^x = amp sin(2 pi y / N_y), u^y = 0, eps = 1: a decaying transverse shear wave."""
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    return np.ones((ny, nx)), amp * np.sin(2.0 * np.pi * y / ny), np.zeros((ny, nx))
+
+
+def smooth_random_fields(nx, ny, seed, eps_amp=0.05, u_amp=0.05, kmax=4):
+    """eps = 1 + eps_amp * g1, u^x = u_amp * g2, u^y = u_amp * g3 where g are sums of
+    random low-wave-number Fourier modes (|k| <= kmax), periodic on the lattice and
+    normalised to unit maximum."""
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    out = []
+    for _ in range(3):
+        g = np.zeros((ny, nx))
+        for kx in range(-kmax, kmax + 1):
+            for ky in range(0, kmax + 1):
+                if kx == 0 and ky == 0:
+                    continue
+                g += rng.standard_normal() * np.cos(2.0 * np.pi * (kx * X / nx + ky * Y / ny)
+                                                     + rng.uniform(0.0, 2.0 * np.pi))
+        out.append(g / np.abs(g).max())
+    return 1.0 + eps_amp * out[0], u_amp * out[1], u_amp * out[2]
+
+
+def disc_mask(nx, ny, radius, fraction, seed, walls_y=True, max_trials=1_000_000):
+    """Solid mask (N_y x N_x, uint8) of non-overlapping discs of the given radius at
+    seeded random integer centres: a cell is solid when (x - cx)^2 + (y - cy)^2 <= r^2
+    (x periodic).  The disc count is round(fraction * N_x N_y / cells_per_disc);
+    centres keep a distance >= 2r + 2 from each other and >= r + 1 from the walls."""
+    r = int(radius)
+    offs = [(dx, dy) for dy in range(-r, r + 1) for dx in range(-r, r + 1) if dx * dx + dy * dy <= r * r]
+    ndisc = int(round(fraction * nx * ny / len(offs)))
+    rng = np.random.default_rng(seed)
+    centres = []
+    trials = 0
+    lo = r + 1 if walls_y else 0
+    hi = ny - r - 1 if walls_y else ny - 1
+    while len(centres) < ndisc:
+        trials += 1
+        if trials > max_trials:
+            raise RuntimeError("disc placement did not converge")
+        cx = int(rng.integers(0, nx))
+        cy = int(rng.integers(lo, hi + 1))
+        ok = True
+        for (px, py) in centres:
+            dx = abs(cx - px)
+            dx = min(dx, nx - dx)
+            dy = abs(cy - py)
+            if not walls_y:
+                dy = min(dy, ny - dy)
+            if dx * dx + dy * dy < (2 * r + 2) ** 2:
+                ok = False
+                break
+        if ok:
+            centres.append((cx, cy))
+    mask = np.zeros((ny, nx), np.uint8)
+    for (cx, cy) in centres:
+        for (dx, dy) in offs:
+            mask[(cy + dy) % ny, (cx + dx) % nx] = 1
+    return mask, centres
+
+
+def ensemble_sides(nmembers, seed, choices=(256, 512, 768, 1024)):
+    """Lattice side of each ensemble member, uniform over `choices`."""
+    rng = np.random.default_rng(seed)
+    return [int(choices[i]) for i in rng.integers(0, len(choices), size=nmembers)]
+
+
+# Workload shapes (dt = 0.05 everywhere, spacing a = 0.1 so dt/a = 0.5).
+SHEAR_WAVE_64 = dict(nx=64, ny=64, precision="f64", eta_over_s=0.1, steps=200)
+STIRRED_1024 = dict(nx=1024, ny=1024, precision="f32", eta_over_s=0.05, kmin=8, kmax=10,
+                    force_amp=1e-4, seed=2, steps=20000, spectrum_every=500)
+STIRRED_4096 = dict(STIRRED_1024, nx=4096, ny=4096, steps=200)
+GRAPHENE_2048x512 = dict(nx=2048, ny=512, precision="f16", walls_y=1, body_force=(1e-6, 0.0),
+                         eta_over_s=0.05, radius=6, fractions=(0.01, 0.05, 0.15),
+                         geometry_seeds=(31, 35, 315), steps=50000)
+ENSEMBLE_64 = dict(nmembers=64, side_seed=4, member_seed0=1000, precision="bf16",
+                   eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4, steps=5000)
+ADJOINT_512 = dict(nx=512, ny=512, precision="f32", eta_over_s=0.05, kmin=4, kmax=6,
+                   force_amp=1e-4, seed=5, steps=2000)
