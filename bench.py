@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput of the fused relativistic lattice Boltzmann step on GB300.
+
+One step = one launch of the fused kernel (pull-streaming with bounce-back, moments,
+Landau matching, equilibrium, Anderson-Witting relaxation, projected stirring force,
+store) over the whole lattice, plus the stirring table the same launch prepares for
+the next step.  Default workload: 1024 x 1024 periodic lattice, FP32, eps0 = 1 at
+rest, stirring shell 8 <= |k| <= 10 with amplitude 1e-4 redrawn every step, eta/s =
+0.05, dt = 0.05, a = 0.1.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun), every rank advances its own independently seeded lattice
+(replicas: the update has no cross-lattice exchange), and `value` counts the cell
+updates of all ranks over the slowest rank's time.  L2 is flushed (a 256 MiB write)
+before every timed step; only the step launches are inside the CUDA-event windows.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM GB/s fraction of peak, plain vs mixed/batched at stated error"
+ALG_BYTES = {"f64": 272, "f32": 136, "f16": 68, "bf16": 68}  # 2 x 17 planes x storage bytes per cell update
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_step_kernel_stirred1024_f32.txt")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--nx", type=int, default=1024)
+    p.add_argument("--ny", type=int, default=1024)
+    p.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(args, rank):
+    return dict(eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4, seed=2 + rank)
+
+
+def workload_name(args):
+    return ("stirred %dx%d %s, shell 8<=|k|<=10, amp 1e-4 (Philox per step and mode), eta/s 0.05, "
+            "dt 0.05, a 0.1, eps0 1 at rest" % (args.nx, args.ny, args.precision.upper()))
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2205_04658_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def committed_traffic(args):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source and this workload; else None."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_digest") != csrc_digest():
+            return None
+        if kv.get("workload") != "%dx%d %s" % (args.nx, args.ny, args.precision):
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) of the SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--id=%d" % self.device, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_mlups(nx, ny, rows, steps, kw):
+    """Time the FP64 oracle on a band of `rows` rows of the lattice for `steps` steps."""
+    import numpy as np
+    from oracle import rlbm_oracle as O
+    cfg = dict(nx=nx, ny=ny, **kw)
+    o = O.Oracle(cfg, xs=np.arange(nx), ys=np.arange(rows))
+    t0 = time.perf_counter()
+    o.run(steps)
+    dt = time.perf_counter() - t0
+    return nx * rows * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    kw = workload(args, 0)
+    # size the band so that warm-up + timed steps take about two minutes of CPU
+    probe, dtp = oracle_mlups(args.nx, args.ny, 8, 1, kw)
+    per_cell = dtp / (args.nx * 8)
+    rows = int(max(8, min(args.ny, 120.0 / max(1, args.steps + args.warmup) / (per_cell * args.nx))))
+    import numpy as np
+    from oracle import rlbm_oracle as O
+    o = O.Oracle(dict(nx=args.nx, ny=args.ny, **kw), xs=np.arange(args.nx), ys=np.arange(rows))
+    o.run(args.warmup)
+    t0 = time.perf_counter()
+    o.run(args.steps)
+    dt = time.perf_counter() - t0
+    value = args.nx * rows * args.steps / dt / 1e6
+    sample = "%d x %d band of the %dx%d lattice, %d steps after %d warm-up" % (args.nx, rows, args.nx, args.ny,
+                                                                              args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args), "lattice": [args.nx, args.ny], "sample_rows": rows},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2205_04658_gb300 import rlbm, inputs  # noqa: F401
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    rlbm.lib()  # fails loudly when the library is missing
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    nx, ny, prec = args.nx, args.ny, args.precision
+    cells = nx * ny
+    kw = workload(args, rank)
+    lat = rlbm.Lattice(nx, ny, precision=prec, **kw)
+    stream = lat.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            lat.step(1)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            lat.step(1)
+            b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    lat.sync()
+    times = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * cells * args.steps / (total_ms / 1e3) / 1e6
+    peak, peak_kind = measured_peak()
+    achieved = ALG_BYTES[prec] * cells / (statistics.mean(times) / 1e3) / 1e9
+    traffic = committed_traffic(args)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "step_kernel (fused stream+collide)", "alg_bytes_per_cell": ALG_BYTES[prec]}
+    lat.close()
+    del flush
+
+    # end to end through the C ABI with host buffers: initial fields H2D (rlbm_init),
+    # K steps, eps/u^x/u^y/totals D2H (rlbm_moments)
+    e2e = None
+    if not args.no_e2e:
+        e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=rank, eps_amp=0.0, u_amp=0.0)
+        pin = [torch.empty((ny, nx), dtype=torch.float64).pin_memory() for _ in range(6)]
+        pin[0].numpy()[:] = e
+        pin[1].numpy()[:] = ux
+        pin[2].numpy()[:] = uy
+        tot = torch.empty(4, dtype=torch.float64).pin_memory()
+        cfg, keep = rlbm.make_config(nx, ny, precision=prec, init_eps=pin[0].numpy(), init_ux=pin[1].numpy(),
+                                     init_uy=pin[2].numpy(), **kw)
+        # make_config copies non-contiguous input; these are contiguous, so it points at pinned memory
+        nbytes = rlbm.rlbm_query_workspace(cfg)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = (ws.data_ptr() + 255) // 256 * 256
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ctx = rlbm.rlbm_init(cfg, ptr, nbytes, torch.cuda.current_stream().cuda_stream)
+        rlbm.rlbm_step(ctx, args.steps)
+        rlbm.rlbm_moments(ctx, pin[3].numpy(), pin[4].numpy(), pin[5].numpy(), tot.numpy())
+        t1 = time.perf_counter()
+        rlbm.rlbm_free(ctx)
+        dt = t1 - t0
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * cells * args.steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 3 * 8 * cells / args.steps,
+               "d2h_bytes_per_step": (3 * 8 * cells + 32) / args.steps,
+               "note": "rlbm_init from pinned host fields + %d steps + rlbm_moments to pinned host" % args.steps}
+        del ws
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows = 256
+        v, dt = oracle_mlups(nx, ny, rows, 2, kw)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle, 2 steps of a %d x %d band of the %dx%d workload (%.1f s)" % (nx, rows, nx, ny, dt)}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": prec, "data": "synthetic",
+                "config": {"workload": workload_name(args), "lattice": [nx, ny], "precision": prec,
+                           "l2": "flushed before every timed step (256 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

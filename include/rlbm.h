@@ -1,0 +1,152 @@
+/*
+ * rlbm.h -- C ABI of the GB300 (sm_103a) relativistic lattice Boltzmann library.
+ *
+ * The library advances the relativistic lattice Boltzmann method for a massless
+ * two-dimensional fluid of M. Watson, "Turbulence in two-dimensional relativistic
+ * hydrodynamic systems with a lattice Boltzmann model" (arXiv 2205.04658):
+ *
+ *   f*_0 = f_eq(eps_init, u_init)                (Sec. "The Standard/Classical LBM",
+ *   repeat:                                        enumerated procedure, item 1)
+ *     f_n = stream(f*_n)     bilinear pull of the off-lattice momenta, bounce-back at
+ *                            solid cells (Sec. "Boltzmann to Lattice Boltzmann";
+ *                            Part II "Model and Methods")
+ *     T^{mu nu}(f_n) -> Landau matching u_mu T^{mu nu} = eps u^nu -> eps, u^mu,
+ *                       T = (pi^2 eps / 3)^{1/4}, tau_R = 5 (eta/s) / T
+ *                       (Sec. "Relativistic Lattice Boltzmann"; Sec. "Boltzmann to
+ *                       Lattice Boltzmann")
+ *     f*_{n+1} = f_n + dt/tau_R (u^0 - v.u)(f_eq - f_n) + dt S_n
+ *                       (Eq. boltzmanneq_rel; Eq. forceTerm and App. B for S_n)
+ *
+ * "The state after n steps" is f_n = stream(f*_n); rlbm_moments reports its moments.
+ *
+ * Conventions for every entry point:
+ *   - Nothing aborts, throws or prints.  A bad argument returns RLBM_E_INVAL and sets
+ *     the message returned by rlbm_last_error.
+ *   - Device memory is owned by the caller: rlbm_init receives one workspace of at
+ *     least rlbm_query_workspace bytes (256-byte aligned) and never frees it.  The
+ *     library owns only its host-side context.  All host arrays passed in are copied
+ *     before the call returns.
+ *   - Work is queued on the CUDA stream given to rlbm_init (0 = legacy default
+ *     stream).  rlbm_step is asynchronous; rlbm_moments, rlbm_spectrum, rlbm_sync and
+ *     rlbm_get_state synchronise that stream and report conditions the kernels
+ *     latched in a device error word (RLBM_E_UNSTABLE, RLBM_E_UNPHYSICAL).  After
+ *     such an error the context accepts only rlbm_free.
+ *   - Lattice arrays are row-major with x fastest: index = y * nx + x.
+ *   - The workspace is reused by every call on the context; calls on one context
+ *     must not overlap from several host threads.
+ */
+#ifndef RLBM_H
+#define RLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RLBM_API __attribute__((visibility("default")))
+#else
+#define RLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlbm_ctx rlbm_ctx;  /* opaque; created by rlbm_init, destroyed by rlbm_free */
+
+typedef enum {
+  RLBM_OK = 0,
+  RLBM_E_INVAL = 1,       /* invalid argument or configuration */
+  RLBM_E_NOMEM = 2,       /* workspace too small, or host allocation failed */
+  RLBM_E_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+  RLBM_E_UNSTABLE = 4,    /* a cell went non-finite, eps <= 0 or |v| >= 1 */
+  RLBM_E_UNPHYSICAL = 5,  /* Landau matching found no timelike eigenvector */
+  RLBM_E_TIMEOUT = 6,     /* a bounded device-side wait expired */
+  RLBM_E_STATE = 7        /* the context is in an error state, or the call is out of order */
+} rlbm_status;
+
+/* Storage precision of the populations.  F64 and F32 store the normalised deviation
+ * h_i = f_i / (w_i eps0) - 1 in that type and compute in it (F32 falls back to FP64
+ * for the Landau solve of a cell whose |v| exceeds fp64_landau_vmax or whose FP32
+ * Newton solve does not converge).  F16 and BF16 store h_i in 16 bits and compute
+ * in FP32. */
+typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_F16 = 2, RLBM_BF16 = 3 } rlbm_precision;
+
+typedef struct {
+  int32_t nx, ny;          /* lattice size, 8 <= nx, ny <= 32768; x is always periodic */
+  int32_t walls_y;         /* 0: y periodic; 1: solid ghost rows at y = -1 and y = ny */
+  int32_t vset;            /* 3: the paper's 26-direction spherical set (P = eps/3);
+                              2: 8 directions on the unit circle (P = eps/2, no force) */
+  int32_t precision;       /* rlbm_precision */
+  int32_t reserved0;       /* must be 0 */
+  double a, dt;            /* lattice spacing and time step; requires 0 < dt/a <= 1 */
+  double eta_over_s;       /* > 0; tau_R = 5 (eta/s) / T (4 (eta/s) / T for vset 2) */
+  double eps0;             /* > 0; reference energy density, T0 = T(eps0) */
+  double body_force[2];    /* uniform force (F^x, F^y) added everywhere */
+  int32_t kmin, kmax;      /* stirring shell kmin <= |k| <= kmax in integer wave-number
+                              units; 0 <= kmin <= kmax < min(nx, ny) / 2 */
+  double force_amp;        /* Gaussian amplitude scale of the stirring modes; 0 = off */
+  uint64_t seed;           /* Philox4x32-10 key of the stirring draws */
+  const uint8_t *solid;    /* host, nx*ny, nonzero = impurity cell; NULL = none */
+  const double *init_eps;  /* host, nx*ny initial energy density; NULL = eps0 */
+  const double *init_ux;   /* host, nx*ny initial u^x (spatial part of u^mu); NULL = 0 */
+  const double *init_uy;   /* host, nx*ny initial u^y; NULL = 0 */
+  double fp64_landau_vmax; /* F32/F16/BF16: |v| above which Landau runs in FP64; 0 = 0.5 */
+} rlbm_config;
+
+/* Device bytes the workspace must hold for this configuration (the populations,
+ * two buffers of 17 planes for vset 3 or 8 for vset 2, plus tables and scratch).
+ * Validates the configuration.  The paper has no counterpart (memory management). */
+RLBM_API rlbm_status rlbm_query_workspace(const rlbm_config *cfg, size_t *bytes);
+
+/* Create a context on the current CUDA device.  dev_workspace: device pointer, at
+ * least rlbm_query_workspace bytes, 256-byte aligned, owned by the caller and kept
+ * alive until rlbm_free.  cuda_stream: a cudaStream_t (NULL = default stream).
+ * Initialises the state to f*_0 = f_eq(eps_init, u_init) (procedure item 1 of Sec.
+ * "The Standard/Classical LBM") and resets the step counter to 0.  *out is NULL on
+ * failure. */
+RLBM_API rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
+                      void *cuda_stream, rlbm_ctx **out);
+
+/* Queue nsteps >= 0 time steps (stream + moments + Landau + equilibrium + collision
+ * + force, one fused kernel per step).  Step n uses the stirring draws
+ * Philox4x32-10(counter = (n mod 2^32, mode, n div 2^32, 0), key = seed).  Async. */
+RLBM_API rlbm_status rlbm_step(rlbm_ctx *ctx, int64_t nsteps);
+
+/* Moments of the current state f_n: eps, u^x, u^y (host arrays of nx*ny, each may be
+ * NULL; zero at solid cells) and totals (host double[4], may be NULL):
+ * sum T^00, sum T^0x, sum T^0y, sum 1/2 |v|^2 over fluid cells, v = u^i / u^0.
+ * Runs the streaming and Landau matching of the next step without storing it. Syncs. */
+RLBM_API rlbm_status rlbm_moments(rlbm_ctx *ctx, double *eps, double *ux, double *uy, double *totals);
+
+/* Energy spectrum of the current state's velocity v = u^i / u^0 (Sec. "Turbulence"):
+ * E[n] = 1/2 sum_{k: round(|k|) = n} |v^(k)|^2 / (nx ny)^2, n = 0 .. nbins-1, integer
+ * wave numbers, v^(k) = sum_x v(x) exp(-i k.x), v = 0 at solid cells.  E: host array of
+ * nbins doubles.  Syncs. */
+RLBM_API rlbm_status rlbm_spectrum(rlbm_ctx *ctx, int32_t nbins, double *E);
+
+/* Copy the stored populations out or in (checkpoint / resume).  host: (planes x ny x nx)
+ * values of h_i = f*_i / (w_i eps0) - 1 in double, plane order of the library's folded
+ * velocity classes (rlbm_num_planes gives the count).  set_state also sets the step
+ * counter.  Both sync.  The paper has no counterpart (it records moments only). */
+RLBM_API rlbm_status rlbm_get_state(rlbm_ctx *ctx, double *host, int64_t *step);
+RLBM_API rlbm_status rlbm_set_state(rlbm_ctx *ctx, const double *host, int64_t step);
+RLBM_API int32_t rlbm_num_planes(const rlbm_ctx *ctx);
+
+/* Wait for queued work and report latched device errors. */
+RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);
+
+/* Number of steps taken since rlbm_init (or set by rlbm_set_state); -1 if ctx is NULL. */
+RLBM_API int64_t rlbm_current_step(const rlbm_ctx *ctx);
+
+/* Human-readable message of the last failing call on ctx, or of the last failing
+ * rlbm_query_workspace / rlbm_init on this thread when ctx is NULL.  Never NULL. */
+RLBM_API const char *rlbm_last_error(const rlbm_ctx *ctx);
+
+/* Release the host context (does not free the caller's workspace).  NULL is a no-op. */
+RLBM_API void rlbm_free(rlbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLBM_H */

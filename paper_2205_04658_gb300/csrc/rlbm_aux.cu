@@ -1,0 +1,183 @@
+// Reductions and the energy spectrum of the velocity field.
+//
+// Spectrum (Sec. "Turbulence": E(k) is the shell density of 1/2 |v(k)|^2): with
+// z = v_x + i v_y, |V_x(k)|^2 + |V_y(k)|^2 = (|Z(k)|^2 + |Z(-k)|^2) / 2, and every shell
+// round(|k|) = n is closed under k -> -k, so the shell sum of |V_x|^2 + |V_y|^2 equals the
+// shell sum of |Z|^2: one complex 2-D transform serves both components.  The
+// transform is a mixed-radix Stockham FFT (radices 2-8 in registers, any larger prime
+// factor as a direct DFT stage), rows then a tiled transpose then rows, FP64.
+#include "rlbm_launch.h"
+
+namespace rlbm {
+
+// ---------------------------------------------------------------------------
+// Deterministic sum of per-block partials: thread t sums blocks t, t+256, ... in
+// order, then thread 0 adds the 256 thread sums in order.
+// ---------------------------------------------------------------------------
+__global__ void reduce_partials_kernel(const double *__restrict__ partials, long long nblocks,
+                                       double *__restrict__ totals) {
+  __shared__ double s[4][256];
+  const int t = threadIdx.x;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long i = t; i < nblocks; i += 256)
+    for (int k = 0; k < 4; ++k) a[k] += partials[i * 4 + k];
+  for (int k = 0; k < 4; ++k) s[k][t] = a[k];
+  __syncthreads();
+  if (t < 4) {
+    double v = 0.0;
+    for (int i = 0; i < 256; ++i) v += s[t][i];
+    totals[t] = v;
+  }
+}
+
+cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st) {
+  reduce_partials_kernel<<<1, 256, 0, st>>>(partials, nblocks, totals);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FFT
+// ---------------------------------------------------------------------------
+struct FftPlan {
+  int n, nstages;
+  int radix[40];
+};
+
+static FftPlan make_plan(int n) {
+  FftPlan p;
+  p.n = n;
+  p.nstages = 0;
+  int m = n;
+  const int pref[] = {8, 4, 2, 3, 5, 7};
+  for (int r : pref)
+    while (m % r == 0 && (r != 8 || m % 8 == 0)) { p.radix[p.nstages++] = r; m /= r; }
+  for (int f = 11; m > 1; f += 2)
+    while (m % f == 0) { p.radix[p.nstages++] = f; m /= f; }
+  return p;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// One block transforms one row of length n in place (ping-pong between a and b);
+// tw[t] = exp(-2 pi i t / n).  Stage with radix R after radices of product Ns:
+//   v_r = x[j + r n/R] * w^(r (j mod Ns) n/(Ns R)),  y[(j div Ns) Ns R + (j mod Ns) + k Ns] = DFT_R(v)_k.
+__global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restrict__ tw,
+                                FftPlan plan) {
+  const int n = plan.n;
+  double2 *src = a + (long long)blockIdx.x * n;
+  double2 *dst = b + (long long)blockIdx.x * n;
+  int Ns = 1;
+  for (int s = 0; s < plan.nstages; ++s) {
+    const int R = plan.radix[s];
+    const int nR = n / R;
+    const int stride = n / (Ns * R);
+    for (int j = threadIdx.x; j < nR; j += blockDim.x) {
+      const int jm = j % Ns;
+      const int base = (j / Ns) * Ns * R + jm;
+      if (R <= 8) {
+        double2 v[8];
+        for (int r = 0; r < R; ++r) {
+          const long long t = ((long long)r * jm * stride) % n;
+          v[r] = cmul(src[j + r * nR], tw[t]);
+        }
+        for (int k = 0; k < R; ++k) {
+          double2 acc = v[0];
+          for (int r = 1; r < R; ++r) {
+            const long long t = ((long long)r * k % R) * nR;
+            acc.x += v[r].x * tw[t].x - v[r].y * tw[t].y;
+            acc.y += v[r].x * tw[t].y + v[r].y * tw[t].x;
+          }
+          dst[base + k * Ns] = acc;
+        }
+      } else {
+        for (int k = 0; k < R; ++k) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int r = 0; r < R; ++r) {
+            const long long t1 = ((long long)r * jm * stride) % n;
+            const double2 v = cmul(src[j + r * nR], tw[t1]);
+            const double2 e = tw[((long long)r * k % R) * nR];
+            acc.x += v.x * e.x - v.y * e.y;
+            acc.y += v.x * e.y + v.y * e.x;
+          }
+          dst[base + k * Ns] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    double2 *tmp = src; src = dst; dst = tmp;
+    Ns *= R;
+  }
+}
+
+__global__ void make_z_kernel(const double *__restrict__ ux, const double *__restrict__ uy, double2 *__restrict__ z,
+                              long long ncell) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const double a = ux[c], b = uy[c];
+  const double u0 = sqrt(1.0 + a * a + b * b);
+  z[c] = make_double2(a / u0, b / u0);
+}
+
+// out[x * ny + y] = in[y * nx + x]
+__global__ void transpose_kernel(const double2 *__restrict__ in, double2 *__restrict__ out, int nx, int ny) {
+  __shared__ double2 tile[32][33];
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int x = x0 + threadIdx.x, y = y0 + k;
+    if (x < nx && y < ny) tile[k][threadIdx.x] = in[(long long)y * nx + x];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int y = y0 + threadIdx.x, x = x0 + k;
+    if (x < nx && y < ny) out[(long long)x * ny + y] = tile[threadIdx.x][k];
+  }
+}
+
+// Z is transposed: row = k_x index, column = k_y index.  E[round|k|] += 1/2 |Z|^2 / (nx ny)^2.
+__global__ void bin_kernel(const double2 *__restrict__ Z, int nx, int ny, double *__restrict__ bins, int nbins,
+                           double scale) {
+  extern __shared__ double sb[];
+  const bool use_smem = nbins <= 6144;
+  if (use_smem)
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) sb[i] = 0.0;
+  __syncthreads();
+  const int qx = blockIdx.x;
+  const int kx = qx < (nx + 1) / 2 ? qx : qx - nx;
+  for (int qy = threadIdx.x; qy < ny; qy += blockDim.x) {
+    const int ky = qy < (ny + 1) / 2 ? qy : qy - ny;
+    const int n = __double2int_rn(sqrt((double)kx * kx + (double)ky * ky));
+    if (n >= nbins) continue;
+    const double2 v = Z[(long long)qx * ny + qy];
+    const double e = scale * (v.x * v.x + v.y * v.y);
+    if (use_smem) atomicAdd(&sb[n], e);
+    else atomicAdd(&bins[n], e);
+  }
+  __syncthreads();
+  if (use_smem)
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+      if (sb[i] != 0.0) atomicAdd(&bins[i], sb[i]);
+}
+
+cudaError_t launch_spectrum(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
+                            const double2 *twy, double2 *z0, double2 *z1, double *bins, int nbins,
+                            cudaStream_t st) {
+  const long long ncell = (long long)nx * ny;
+  make_z_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(ux, uy, z0, ncell);
+  const FftPlan px = make_plan(nx), py = make_plan(ny);
+  fft_rows_kernel<<<ny, 256, 0, st>>>(z0, z1, twx, px);
+  double2 *r = (px.nstages % 2) ? z1 : z0;  // result of the row transforms
+  double2 *o = (px.nstages % 2) ? z0 : z1;
+  transpose_kernel<<<dim3((nx + 31) / 32, (ny + 31) / 32), dim3(32, 8), 0, st>>>(r, o, nx, ny);
+  fft_rows_kernel<<<nx, 256, 0, st>>>(o, r, twy, py);
+  double2 *Z = (py.nstages % 2) ? r : o;
+  cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(double) * nbins, st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = nbins <= 6144 ? sizeof(double) * nbins : 0;
+  const double scale = 0.5 / ((double)ncell * (double)ncell);
+  bin_kernel<<<nx, 256, smem, st>>>(Z, nx, ny, bins, nbins, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace rlbm

@@ -1,0 +1,586 @@
+// C ABI of the relativistic lattice Boltzmann library: configuration checks, the
+// workspace layout in the caller's device memory, host-built tables (streaming
+// weights, stirring modes and phase tables, FFT twiddles, solid-neighbour masks) and
+// the dispatch of the kernels of each storage type.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rlbm.h"
+#include "rlbm_device.cuh"
+#include "rlbm_launch.h"
+
+using namespace rlbm;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int num_classes(int vset) { return vset == 3 ? VSet<3>::Q : VSet<2>::Q; }
+size_t store_bytes(int prec) { return prec == RLBM_F64 ? 8 : prec == RLBM_F32 ? 4 : 2; }
+size_t real_bytes(int prec) { return prec == RLBM_F64 ? 8 : 4; }
+
+struct Modes {
+  std::vector<int> kx, ky, row_start, row_ky;
+};
+
+// Half-plane integer wave vectors of the shell kmin^2 <= |k|^2 <= kmax^2, sorted by
+// (k_y, k_x), grouped into rows of equal k_y.
+Modes shell_modes(int kmin, int kmax) {
+  Modes m;
+  for (int ky = 0; ky <= kmax; ++ky)
+    for (int kx = -kmax; kx <= kmax; ++kx) {
+      const int k2 = kx * kx + ky * ky;
+      if ((ky > 0 || kx > 0) && kmin * kmin <= k2 && k2 <= kmax * kmax) {
+        if (m.row_ky.empty() || m.row_ky.back() != ky) {
+          m.row_ky.push_back(ky);
+          m.row_start.push_back((int)m.kx.size());
+        }
+        m.kx.push_back(kx);
+        m.ky.push_back(ky);
+      }
+    }
+  m.row_start.push_back((int)m.kx.size());
+  return m;
+}
+
+bool stirring_on(const rlbm_config &c) { return c.force_amp != 0.0; }
+
+struct Layout {
+  size_t pop[2], nbmask, err, EX, EY, G[2], coef[2], mode_kx, mode_ky, row_start;
+  size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, total;
+  long long plane;
+  int pitch, Q, nrows, nmodes, max_bins;
+  long long max_blocks;
+};
+
+Layout make_layout(const rlbm_config &c) {
+  Layout L{};
+  L.Q = num_classes(c.vset);
+  L.pitch = (c.nx + 31) / 32 * 32;
+  L.plane = (long long)L.pitch * c.ny;
+  const size_t sb = store_bytes(c.precision), rb = real_bytes(c.precision);
+  const size_t ncell = (size_t)c.nx * c.ny;
+  Modes m;
+  if (stirring_on(c)) m = shell_modes(c.kmin, c.kmax);
+  L.nmodes = (int)m.kx.size();
+  L.nrows = (int)m.row_ky.size();
+  L.max_blocks = (long long)((c.nx + 31) / 32) * c.ny;
+  L.max_bins = (int)std::ceil(std::sqrt((c.nx / 2 + 1.0) * (c.nx / 2 + 1.0) + (c.ny / 2 + 1.0) * (c.ny / 2 + 1.0))) + 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1)); return o; };
+  L.pop[0] = take(sb * L.Q * L.plane);
+  L.pop[1] = take(sb * L.Q * L.plane);
+  L.nbmask = take((c.solid || c.walls_y) ? 2 * ncell : 0);
+  L.err = take(16);
+  L.EX = take(2 * rb * c.nx);
+  L.EY = take(2 * rb * (size_t)L.nrows * c.ny);
+  L.G[0] = take(4 * rb * (size_t)L.nrows * c.nx);
+  L.G[1] = take(4 * rb * (size_t)L.nrows * c.nx);
+  L.coef[0] = take(4 * rb * L.nmodes);
+  L.coef[1] = take(4 * rb * L.nmodes);
+  L.mode_kx = take(4 * L.nmodes);
+  L.mode_ky = take(4 * L.nmodes);
+  L.row_start = take(4 * (L.nrows + 1));
+  L.eps = take(8 * ncell);
+  L.ux = take(8 * ncell);
+  L.uy = take(8 * ncell);
+  L.partials = take(32 * (size_t)L.max_blocks);
+  L.totals = take(32);
+  L.twx = take(16 * (size_t)c.nx);
+  L.twy = take(16 * (size_t)c.ny);
+  L.z0 = take(16 * ncell);
+  L.z1 = take(16 * ncell);
+  L.bins = take(8 * (size_t)L.max_bins);
+  L.total = off;
+  return L;
+}
+
+std::string validate(const rlbm_config *c) {
+  if (!c) return "cfg is NULL";
+  if (c->nx < 8 || c->ny < 8 || c->nx > 32768 || c->ny > 32768) return "nx and ny must lie in [8, 32768]";
+  if (c->walls_y != 0 && c->walls_y != 1) return "walls_y must be 0 or 1";
+  if (c->vset != 2 && c->vset != 3) return "vset must be 2 or 3";
+  if (c->precision < RLBM_F64 || c->precision > RLBM_BF16) return "precision must be one of RLBM_F64..RLBM_BF16";
+  if (c->reserved0 != 0) return "reserved0 must be 0";
+  if (!(c->a > 0.0) || !(c->dt > 0.0) || !std::isfinite(c->a) || !std::isfinite(c->dt))
+    return "a and dt must be positive and finite";
+  if (c->dt / c->a > 1.0) return "dt / a must not exceed 1 (the streaming displacement stays within one cell)";
+  if (!(c->eta_over_s > 0.0) || !std::isfinite(c->eta_over_s)) return "eta_over_s must be positive and finite";
+  if (!(c->eps0 > 0.0) || !std::isfinite(c->eps0)) return "eps0 must be positive and finite";
+  if (!std::isfinite(c->body_force[0]) || !std::isfinite(c->body_force[1])) return "body_force must be finite";
+  if (!std::isfinite(c->force_amp)) return "force_amp must be finite";
+  if (stirring_on(*c)) {
+    if (c->kmin < 0 || c->kmax < c->kmin) return "the stirring shell needs 0 <= kmin <= kmax";
+    if (2 * c->kmax >= std::min(c->nx, c->ny)) return "kmax must be below min(nx, ny) / 2";
+    if (shell_modes(c->kmin, c->kmax).kx.empty()) return "the stirring shell holds no wave vector";
+  }
+  if (c->vset == 2 && (stirring_on(*c) || c->body_force[0] != 0.0 || c->body_force[1] != 0.0))
+    return "the projected force is defined for the three-dimensional momentum set (vset 3) only";
+  if (!(c->fp64_landau_vmax >= 0.0 && c->fp64_landau_vmax < 1.0)) return "fp64_landau_vmax must lie in [0, 1)";
+  return "";
+}
+
+double temperature_of(double eps, int vset) {
+  return vset == 3 ? std::pow(M_PI * M_PI * eps / 3.0, 0.25) : std::cbrt(M_PI * eps);
+}
+
+template <int VS> void fill_beta(double C, double beta[17][4]) {
+  for (int q = 0; q < VSet<VS>::Q; ++q) {
+    const double ax = C * std::fabs(VSet<VS>::vx(q)), ay = C * std::fabs(VSet<VS>::vy(q));
+    beta[q][0] = (1.0 - ax) * (1.0 - ay);
+    beta[q][1] = ax * (1.0 - ay);
+    beta[q][2] = (1.0 - ax) * ay;
+    beta[q][3] = ax * ay;
+  }
+}
+
+struct Scoped {  // switch to the context's device for one call, restore afterwards
+  int prev = -1, want;
+  explicit Scoped(int dev) : want(dev) {
+    cudaGetDevice(&prev);
+    if (prev != want) cudaSetDevice(want);
+  }
+  ~Scoped() {
+    if (prev >= 0 && prev != want) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct rlbm_ctx {
+  rlbm_config cfg;
+  Layout L;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char *ws = nullptr;
+  int cur = 0;           // population buffer holding f*_n
+  int64_t step = 0;
+  rlbm_status latched = RLBM_OK;
+  std::string msg;
+  HostGeom geom;
+  HostPhys phys;
+  dim3 block{32, 8, 1};
+  std::vector<uint8_t> host_stage;
+
+  template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+
+  rlbm_status fail(rlbm_status s, const std::string &m) {
+    msg = m;
+    return s;
+  }
+  rlbm_status cuda_fail(cudaError_t e, const char *what) {
+    msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return RLBM_E_CUDA;
+  }
+};
+
+namespace {
+
+cudaError_t dispatch_step(rlbm_ctx *c, const void *fin, void *fout, const HostStir &s) {
+  unsigned *err = c->at<unsigned>(c->L.err);
+  switch (c->cfg.precision) {
+    case RLBM_F64: return launch_step_f64(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
+    case RLBM_F32: return launch_step_f32(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
+    case RLBM_F16: return launch_step_f16(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
+    default: return launch_step_bf16(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
+  }
+}
+
+cudaError_t dispatch_moments(rlbm_ctx *c) {
+  const void *fin = c->ws + c->L.pop[c->cur];
+  double *e = c->at<double>(c->L.eps), *ux = c->at<double>(c->L.ux), *uy = c->at<double>(c->L.uy);
+  double *part = c->at<double>(c->L.partials);
+  unsigned *err = c->at<unsigned>(c->L.err);
+  const double e0 = c->cfg.eps0;
+  cudaError_t r;
+  switch (c->cfg.precision) {
+    case RLBM_F64: r = launch_moments_f64(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
+    case RLBM_F32: r = launch_moments_f32(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
+    case RLBM_F16: r = launch_moments_f16(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
+    default: r = launch_moments_bf16(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
+  }
+  if (r != cudaSuccess) return r;
+  const long long nblocks = (long long)((c->cfg.nx + c->block.x - 1) / c->block.x) * ((c->cfg.ny + c->block.y - 1) / c->block.y);
+  return launch_reduce_partials(part, nblocks, c->at<double>(c->L.totals), c->stream);
+}
+
+cudaError_t dispatch_init(rlbm_ctx *c, void *fout, const double *e, const double *ux, const double *uy) {
+  switch (c->cfg.precision) {
+    case RLBM_F64: return launch_init_f64(c->cfg.vset, fout, c->geom, c->cfg.eps0, e, ux, uy, c->stream);
+    case RLBM_F32: return launch_init_f32(c->cfg.vset, fout, c->geom, c->cfg.eps0, e, ux, uy, c->stream);
+    case RLBM_F16: return launch_init_f16(c->cfg.vset, fout, c->geom, c->cfg.eps0, e, ux, uy, c->stream);
+    default: return launch_init_bf16(c->cfg.vset, fout, c->geom, c->cfg.eps0, e, ux, uy, c->stream);
+  }
+}
+
+HostStir stir_for_step(rlbm_ctx *c, int64_t n) {
+  HostStir s{};
+  const Layout &L = c->L;
+  s.nrows = L.nrows;
+  s.nmodes = L.nmodes;
+  if (L.nmodes == 0) return s;
+  s.G_cur = c->ws + L.G[n & 1];
+  s.G_next = c->ws + L.G[(n + 1) & 1];
+  s.coef_next = c->ws + L.coef[(n + 1) & 1];
+  s.coef_new = c->ws + L.coef[n & 1];
+  s.EY = c->ws + L.EY;
+  s.EX = c->ws + L.EX;
+  s.mode_kx = c->at<int>(L.mode_kx);
+  s.mode_ky = c->at<int>(L.mode_ky);
+  s.row_start = c->at<int>(L.row_start);
+  s.seed = c->cfg.seed;
+  s.step_new = n + 2;
+  s.amp = c->cfg.force_amp;
+  return s;
+}
+
+// Coefficients of steps n and n+1 and the table of step n.
+cudaError_t stir_prime(rlbm_ctx *c, int64_t n) {
+  if (c->L.nmodes == 0) return cudaSuccess;
+  HostStir s = stir_for_step(c, n);
+  void *cn = c->ws + c->L.coef[n & 1], *cn1 = c->ws + c->L.coef[(n + 1) & 1], *G = c->ws + c->L.G[n & 1];
+  switch (c->cfg.precision) {
+    case RLBM_F64: return launch_stir_prime_f64(s, cn, cn1, G, c->cfg.nx, n, c->stream);
+    case RLBM_F32: return launch_stir_prime_f32(s, cn, cn1, G, c->cfg.nx, n, c->stream);
+    case RLBM_F16: return launch_stir_prime_f16(s, cn, cn1, G, c->cfg.nx, n, c->stream);
+    default: return launch_stir_prime_bf16(s, cn, cn1, G, c->cfg.nx, n, c->stream);
+  }
+}
+
+template <typename R> void put_pairs(std::vector<uint8_t> &out, const std::vector<double> &re, const std::vector<double> &im) {
+  out.resize(re.size() * 2 * sizeof(R));
+  R *p = reinterpret_cast<R *>(out.data());
+  for (size_t i = 0; i < re.size(); ++i) { p[2 * i] = (R)re[i]; p[2 * i + 1] = (R)im[i]; }
+}
+
+// Reads the device error word after a synchronisation and latches it.
+rlbm_status check_device(rlbm_ctx *c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "cudaStreamSynchronize");
+  unsigned w = 0;
+  e = cudaMemcpy(&w, c->at<unsigned>(c->L.err), sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return c->cuda_fail(e, "cudaMemcpy(error word)");
+  if (w & ERR_UNSTABLE) {
+    c->latched = RLBM_E_UNSTABLE;
+    return c->fail(RLBM_E_UNSTABLE, "a cell became non-finite, eps <= 0 or |v| >= 1 (numerically unstable run)");
+  }
+  if (w & ERR_UNPHYSICAL) {
+    c->latched = RLBM_E_UNPHYSICAL;
+    return c->fail(RLBM_E_UNPHYSICAL, "Landau matching found no timelike eigenvector in some cell");
+  }
+  return RLBM_OK;
+}
+
+rlbm_status usable(rlbm_ctx *c) {
+  if (c->latched != RLBM_OK) {
+    c->msg = "the context is in an error state (" + std::to_string((int)c->latched) + "); only rlbm_free is allowed";
+    return RLBM_E_STATE;
+  }
+  return RLBM_OK;
+}
+
+template <typename S> double to_double(S v) { return (double)v; }
+template <> double to_double<__half>(__half v) { return (double)__half2float(v); }
+template <> double to_double<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <typename S> S from_double(double v) { return (S)v; }
+template <> __half from_double<__half>(double v) { return __float2half_rn((float)v); }
+template <> __nv_bfloat16 from_double<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+
+template <typename S> void unpack_state(const rlbm_ctx *c, const uint8_t *src, double *dst) {
+  const S *p = reinterpret_cast<const S *>(src);
+  const int nx = c->cfg.nx, ny = c->cfg.ny;
+  for (int q = 0; q < c->L.Q; ++q)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x)
+        dst[((size_t)q * ny + y) * nx + x] = to_double<S>(p[q * c->L.plane + (size_t)y * c->L.pitch + x]);
+}
+
+template <typename S> void pack_state(const rlbm_ctx *c, const double *src, uint8_t *dst) {
+  S *p = reinterpret_cast<S *>(dst);
+  const int nx = c->cfg.nx, ny = c->cfg.ny;
+  for (int q = 0; q < c->L.Q; ++q)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < c->L.pitch; ++x)
+        p[q * c->L.plane + (size_t)y * c->L.pitch + x] =
+            x < nx ? from_double<S>(src[((size_t)q * ny + y) * nx + x]) : from_double<S>(0.0);
+}
+
+}  // namespace
+
+extern "C" {
+
+rlbm_status rlbm_query_workspace(const rlbm_config *cfg, size_t *bytes) {
+  const std::string v = validate(cfg);
+  if (!v.empty()) { g_thread_error = v; return RLBM_E_INVAL; }
+  if (!bytes) { g_thread_error = "bytes is NULL"; return RLBM_E_INVAL; }
+  *bytes = make_layout(*cfg).total;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes, void *cuda_stream, rlbm_ctx **out) {
+  if (!out) { g_thread_error = "out is NULL"; return RLBM_E_INVAL; }
+  *out = nullptr;
+  const std::string v = validate(cfg);
+  if (!v.empty()) { g_thread_error = v; return RLBM_E_INVAL; }
+  const Layout L = make_layout(*cfg);
+  if (!dev_workspace) { g_thread_error = "dev_workspace is NULL"; return RLBM_E_INVAL; }
+  if (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign) { g_thread_error = "dev_workspace must be 256-byte aligned"; return RLBM_E_INVAL; }
+  if (bytes < L.total) {
+    g_thread_error = "workspace too small: " + std::to_string(bytes) + " < " + std::to_string(L.total) + " bytes";
+    return RLBM_E_NOMEM;
+  }
+  const size_t ncell = (size_t)cfg->nx * cfg->ny;
+  // host-side checks of the initial fields
+  for (size_t i = 0; cfg->init_eps && i < ncell; ++i)
+    if (!(cfg->init_eps[i] > 0.0) || !std::isfinite(cfg->init_eps[i])) { g_thread_error = "init_eps must be positive and finite"; return RLBM_E_INVAL; }
+  for (size_t i = 0; i < ncell; ++i) {
+    const double a = cfg->init_ux ? cfg->init_ux[i] : 0.0, b = cfg->init_uy ? cfg->init_uy[i] : 0.0;
+    if (!std::isfinite(a) || !std::isfinite(b)) { g_thread_error = "init_ux / init_uy must be finite"; return RLBM_E_INVAL; }
+  }
+
+  rlbm_ctx *c = new (std::nothrow) rlbm_ctx();
+  if (!c) { g_thread_error = "host allocation failed"; return RLBM_E_NOMEM; }
+  c->cfg = *cfg;
+  c->cfg.solid = nullptr; c->cfg.init_eps = c->cfg.init_ux = c->cfg.init_uy = nullptr;
+  c->L = L;
+  c->ws = static_cast<char *>(dev_workspace);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&c->device);
+  if (c->cfg.fp64_landau_vmax == 0.0) c->cfg.fp64_landau_vmax = 0.5;
+
+  auto bail = [&](rlbm_status s) { g_thread_error = c->msg; delete c; return s; };
+  auto put = [&](size_t off, const void *src, size_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyAsync(c->ws + off, src, n, cudaMemcpyHostToDevice, c->stream);
+  };
+
+  // streaming weights
+  const double C = cfg->dt / cfg->a;
+  std::memset(c->geom.beta, 0, sizeof(c->geom.beta));
+  if (cfg->vset == 3) fill_beta<3>(C, c->geom.beta); else fill_beta<2>(C, c->geom.beta);
+  c->geom.nx = cfg->nx; c->geom.ny = cfg->ny; c->geom.pitch = L.pitch; c->geom.plane = L.plane;
+  c->geom.nbmask = nullptr;
+
+  // relaxation and force constants
+  const double T0 = temperature_of(cfg->eps0, cfg->vset);
+  const double taunum = cfg->vset == 3 ? VSet<3>::TAU_NUM : VSet<2>::TAU_NUM;
+  c->phys.omega0 = cfg->dt * T0 / (taunum * cfg->eta_over_s);
+  c->phys.fpref = -6.0 * cfg->dt / T0;
+  c->phys.body_x = cfg->body_force[0];
+  c->phys.body_y = cfg->body_force[1];
+  c->phys.vmax2 = c->cfg.fp64_landau_vmax * c->cfg.fp64_landau_vmax;
+  c->phys.has_force = (stirring_on(*cfg) || cfg->body_force[0] != 0.0 || cfg->body_force[1] != 0.0) ? 1 : 0;
+
+  // Host staging buffers; copies from pageable memory have consumed their source when
+  // cudaMemcpyAsync returns, and init synchronises the stream before it returns.
+  std::vector<std::vector<uint8_t>> keep;
+  cudaError_t e = cudaSuccess;
+
+  // solid-neighbour masks: bit 4 = the cell, bit (dy+1)*3+(dx+1) = neighbour (x+dx, y+dy);
+  // rows y = -1 and y = ny are solid when walls_y is set.
+  if (cfg->solid || cfg->walls_y) {
+    keep.emplace_back(2 * ncell);
+    uint16_t *nb = reinterpret_cast<uint16_t *>(keep.back().data());
+    const int nx = cfg->nx, ny = cfg->ny;
+    auto solid_at = [&](int x, int y) -> bool {
+      if (y < 0 || y >= ny) {
+        if (cfg->walls_y) return true;
+        y = (y + ny) % ny;
+      }
+      x = (x + nx) % nx;
+      return cfg->solid && cfg->solid[(size_t)y * nx + x] != 0;
+    };
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        uint16_t m = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx)
+            if (solid_at(x + dx, y + dy)) m |= (uint16_t)(1u << ((dy + 1) * 3 + (dx + 1)));
+        nb[(size_t)y * nx + x] = m;
+      }
+    if ((e = put(L.nbmask, nb, 2 * ncell)) != cudaSuccess) { c->cuda_fail(e, "upload of the solid mask"); return bail(RLBM_E_CUDA); }
+    c->geom.nbmask = c->at<uint16_t>(L.nbmask);
+  }
+
+  // stirring tables (library's own; FP64-built, stored in the compute type)
+  if (L.nmodes) {
+    const Modes m = shell_modes(cfg->kmin, cfg->kmax);
+    std::vector<double> ex_re(cfg->nx), ex_im(cfg->nx), ey_re((size_t)L.nrows * cfg->ny), ey_im((size_t)L.nrows * cfg->ny);
+    for (int j = 0; j < cfg->nx; ++j) {
+      ex_re[j] = std::cos(2.0 * M_PI * j / cfg->nx);
+      ex_im[j] = std::sin(2.0 * M_PI * j / cfg->nx);
+    }
+    for (int r = 0; r < L.nrows; ++r)
+      for (int y = 0; y < cfg->ny; ++y) {
+        const long long j = ((long long)m.row_ky[r] * y) % cfg->ny;
+        ey_re[(size_t)r * cfg->ny + y] = std::cos(2.0 * M_PI * j / cfg->ny);
+        ey_im[(size_t)r * cfg->ny + y] = std::sin(2.0 * M_PI * j / cfg->ny);
+      }
+    keep.emplace_back();
+    keep.emplace_back();
+    if (cfg->precision == RLBM_F64) { put_pairs<double>(keep[keep.size() - 2], ex_re, ex_im); put_pairs<double>(keep.back(), ey_re, ey_im); }
+    else { put_pairs<float>(keep[keep.size() - 2], ex_re, ex_im); put_pairs<float>(keep.back(), ey_re, ey_im); }
+    if ((e = put(L.EX, keep[keep.size() - 2].data(), keep[keep.size() - 2].size())) != cudaSuccess ||
+        (e = put(L.EY, keep.back().data(), keep.back().size())) != cudaSuccess ||
+        (e = put(L.mode_kx, m.kx.data(), 4 * m.kx.size())) != cudaSuccess ||
+        (e = put(L.mode_ky, m.ky.data(), 4 * m.ky.size())) != cudaSuccess ||
+        (e = put(L.row_start, m.row_start.data(), 4 * m.row_start.size())) != cudaSuccess) {
+      c->cuda_fail(e, "upload of the stirring tables");
+      return bail(RLBM_E_CUDA);
+    }
+  }
+
+  // FFT twiddles exp(-2 pi i t / n)
+  {
+    std::vector<double> twx(2 * (size_t)cfg->nx), twy(2 * (size_t)cfg->ny);
+    for (int t = 0; t < cfg->nx; ++t) { twx[2 * t] = std::cos(2.0 * M_PI * t / cfg->nx); twx[2 * t + 1] = -std::sin(2.0 * M_PI * t / cfg->nx); }
+    for (int t = 0; t < cfg->ny; ++t) { twy[2 * t] = std::cos(2.0 * M_PI * t / cfg->ny); twy[2 * t + 1] = -std::sin(2.0 * M_PI * t / cfg->ny); }
+    keep.emplace_back(reinterpret_cast<uint8_t *>(twx.data()), reinterpret_cast<uint8_t *>(twx.data()) + 16 * (size_t)cfg->nx);
+    keep.emplace_back(reinterpret_cast<uint8_t *>(twy.data()), reinterpret_cast<uint8_t *>(twy.data()) + 16 * (size_t)cfg->ny);
+    if ((e = put(L.twx, keep[keep.size() - 2].data(), 16 * (size_t)cfg->nx)) != cudaSuccess ||
+        (e = put(L.twy, keep.back().data(), 16 * (size_t)cfg->ny)) != cudaSuccess) {
+      c->cuda_fail(e, "upload of the FFT twiddles");
+      return bail(RLBM_E_CUDA);
+    }
+  }
+
+  // initial fields -> f*_0 = f_eq in both population buffers
+  const double *de = nullptr, *dux = nullptr, *duy = nullptr;
+  if (cfg->init_eps) { if ((e = put(L.eps, cfg->init_eps, 8 * ncell)) != cudaSuccess) { c->cuda_fail(e, "upload of init_eps"); return bail(RLBM_E_CUDA); } de = c->at<double>(L.eps); }
+  if (cfg->init_ux) { if ((e = put(L.ux, cfg->init_ux, 8 * ncell)) != cudaSuccess) { c->cuda_fail(e, "upload of init_ux"); return bail(RLBM_E_CUDA); } dux = c->at<double>(L.ux); }
+  if (cfg->init_uy) { if ((e = put(L.uy, cfg->init_uy, 8 * ncell)) != cudaSuccess) { c->cuda_fail(e, "upload of init_uy"); return bail(RLBM_E_CUDA); } duy = c->at<double>(L.uy); }
+  for (int b = 0; b < 2; ++b)
+    if ((e = dispatch_init(c, c->ws + L.pop[b], de, dux, duy)) != cudaSuccess) { c->cuda_fail(e, "init kernel"); return bail(RLBM_E_CUDA); }
+  if ((e = cudaMemsetAsync(c->ws + L.err, 0, 16, c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaMemsetAsync"); return bail(RLBM_E_CUDA); }
+  if ((e = stir_prime(c, 0)) != cudaSuccess) { c->cuda_fail(e, "stirring set-up kernels"); return bail(RLBM_E_CUDA); }
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaStreamSynchronize"); return bail(RLBM_E_CUDA); }
+  c->cur = 0;
+  c->step = 0;
+  *out = c;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_step(rlbm_ctx *c, int64_t nsteps) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (nsteps < 0) return c->fail(RLBM_E_INVAL, "nsteps must be >= 0");
+  Scoped dev(c->device);
+  for (int64_t i = 0; i < nsteps; ++i) {
+    const HostStir s = stir_for_step(c, c->step);
+    cudaError_t e = dispatch_step(c, c->ws + c->L.pop[c->cur], c->ws + c->L.pop[c->cur ^ 1], s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "step kernel launch");
+    c->cur ^= 1;
+    ++c->step;
+  }
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_moments(rlbm_ctx *c, double *eps, double *ux, double *uy, double *totals) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  Scoped dev(c->device);
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny * sizeof(double);
+  cudaError_t e = dispatch_moments(c);
+  if (e != cudaSuccess) return c->cuda_fail(e, "moments kernel launch");
+  if (eps && (e = cudaMemcpyAsync(eps, c->ws + c->L.eps, n, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of eps");
+  if (ux && (e = cudaMemcpyAsync(ux, c->ws + c->L.ux, n, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of ux");
+  if (uy && (e = cudaMemcpyAsync(uy, c->ws + c->L.uy, n, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of uy");
+  if (totals && (e = cudaMemcpyAsync(totals, c->ws + c->L.totals, 32, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of totals");
+  return check_device(c);
+}
+
+rlbm_status rlbm_spectrum(rlbm_ctx *c, int32_t nbins, double *E) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (nbins < 1 || !E) return c->fail(RLBM_E_INVAL, "nbins must be >= 1 and E non-NULL");
+  Scoped dev(c->device);
+  cudaError_t e = dispatch_moments(c);
+  if (e != cudaSuccess) return c->cuda_fail(e, "moments kernel launch");
+  const int nb = std::min(nbins, c->L.max_bins);
+  e = launch_spectrum(c->at<double>(c->L.ux), c->at<double>(c->L.uy), c->cfg.nx, c->cfg.ny,
+                      c->at<double2>(c->L.twx), c->at<double2>(c->L.twy), c->at<double2>(c->L.z0),
+                      c->at<double2>(c->L.z1), c->at<double>(c->L.bins), nb, c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "spectrum kernels");
+  if ((e = cudaMemcpyAsync(E, c->ws + c->L.bins, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return c->cuda_fail(e, "copy of the spectrum");
+  rlbm_status s = check_device(c);
+  for (int i = nb; i < nbins; ++i) E[i] = 0.0;  // beyond the largest |k| of the lattice
+  return s;
+}
+
+rlbm_status rlbm_get_state(rlbm_ctx *c, double *host, int64_t *step) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (!host) return c->fail(RLBM_E_INVAL, "host is NULL");
+  Scoped dev(c->device);
+  const size_t bytes = store_bytes(c->cfg.precision) * c->L.Q * c->L.plane;
+  c->host_stage.resize(bytes);
+  cudaError_t e = cudaMemcpyAsync(c->host_stage.data(), c->ws + c->L.pop[c->cur], bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "copy of the state");
+  rlbm_status s = check_device(c);
+  if (s != RLBM_OK) return s;
+  switch (c->cfg.precision) {
+    case RLBM_F64: unpack_state<double>(c, c->host_stage.data(), host); break;
+    case RLBM_F32: unpack_state<float>(c, c->host_stage.data(), host); break;
+    case RLBM_F16: unpack_state<__half>(c, c->host_stage.data(), host); break;
+    default: unpack_state<__nv_bfloat16>(c, c->host_stage.data(), host); break;
+  }
+  if (step) *step = c->step;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (!host || step < 0) return c->fail(RLBM_E_INVAL, "host must be non-NULL and step >= 0");
+  Scoped dev(c->device);
+  const size_t bytes = store_bytes(c->cfg.precision) * c->L.Q * c->L.plane;
+  c->host_stage.assign(bytes, 0);
+  switch (c->cfg.precision) {
+    case RLBM_F64: pack_state<double>(c, host, c->host_stage.data()); break;
+    case RLBM_F32: pack_state<float>(c, host, c->host_stage.data()); break;
+    case RLBM_F16: pack_state<__half>(c, host, c->host_stage.data()); break;
+    default: pack_state<__nv_bfloat16>(c, host, c->host_stage.data()); break;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->ws + c->L.pop[c->cur], c->host_stage.data(), bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "copy of the state");
+  c->step = step;
+  if ((e = stir_prime(c, step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
+  return check_device(c);
+}
+
+int32_t rlbm_num_planes(const rlbm_ctx *c) { return c ? c->L.Q : -1; }
+
+rlbm_status rlbm_sync(rlbm_ctx *c) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  Scoped dev(c->device);
+  return check_device(c);
+}
+
+int64_t rlbm_current_step(const rlbm_ctx *c) { return c ? c->step : -1; }
+
+const char *rlbm_last_error(const rlbm_ctx *c) { return c ? c->msg.c_str() : g_thread_error.c_str(); }
+
+void rlbm_free(rlbm_ctx *c) {
+  if (!c) return;
+  {
+    Scoped dev(c->device);
+    cudaStreamSynchronize(c->stream);
+  }
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Host-side launch interface between the C ABI (rlbm_capi.cu) and the kernels of
+// each storage type (rlbm_kernels_*.cu).  Plain structs, no templates.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rlbm {
+
+struct HostGeom {
+  int nx, ny, pitch;
+  long long plane;
+  const uint16_t *nbmask;  // device; NULL when the lattice has no solid cells or walls
+  double beta[17][4];
+};
+
+struct HostPhys {
+  double omega0, fpref, body_x, body_y, vmax2;
+  int has_force;
+};
+
+struct HostStir {
+  int nrows, nmodes;
+  const void *G_cur, *EY;
+  void *G_next;
+  const void *coef_next;
+  void *coef_new;
+  const int *mode_kx, *mode_ky, *row_start;
+  const void *EX;
+  unsigned long long seed;
+  long long step_new;
+  double amp;
+};
+
+#define RLBM_DECLARE_LAUNCHERS(SUF)                                                                      \
+  cudaError_t launch_step_##SUF(int vset, const void *fin, void *fout, const HostGeom &g,               \
+                                const HostPhys &p, const HostStir &s, unsigned *err, dim3 b,            \
+                                cudaStream_t st);                                                        \
+  cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
+                                   double *ux, double *uy, double *part, unsigned *err, dim3 b,         \
+                                   cudaStream_t st);                                                     \
+  cudaError_t launch_init_##SUF(int vset, void *fout, const HostGeom &g, double eps0, const double *e,  \
+                                const double *ux, const double *uy, cudaStream_t st);                   \
+  cudaError_t launch_stir_prime_##SUF(const HostStir &s, void *cn, void *cn1, void *G, int nx,          \
+                                      long long n, cudaStream_t st);
+
+RLBM_DECLARE_LAUNCHERS(f64)
+RLBM_DECLARE_LAUNCHERS(f32)
+RLBM_DECLARE_LAUNCHERS(f16)
+RLBM_DECLARE_LAUNCHERS(bf16)
+
+// Reductions and spectrum (rlbm_aux.cu)
+cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st);
+cudaError_t launch_spectrum(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
+                            const double2 *twy, double2 *z0, double2 *z1, double *bins, int nbins,
+                            cudaStream_t st);
+
+}  // namespace rlbm

@@ -18,20 +18,19 @@ def shear_wave(nx, ny, amp=0.01):
 
 
 def smooth_random_fields(nx, ny, seed, eps_amp=0.05, u_amp=0.05, kmax=4):
-    """eps = 1 + eps_amp * g1, u^x = u_amp * g2, u^y = u_amp * g3 where g are sums of
-    random low-wave-number Fourier modes (|k| <= kmax), periodic on the lattice and
-    normalised to unit maximum."""
+    """eps = 1 + eps_amp * g1, u^x = u_amp * g2, u^y = u_amp * g3, where each g is a real
+    periodic field with Gaussian random Fourier coefficients on the wave numbers
+    |k_x|, |k_y| <= kmax (k != 0), normalised to unit maximum modulus."""
     rng = np.random.default_rng(seed)
-    X, Y = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
     out = []
     for _ in range(3):
-        g = np.zeros((ny, nx))
-        for kx in range(-kmax, kmax + 1):
-            for ky in range(0, kmax + 1):
-                if kx == 0 and ky == 0:
+        S = np.zeros((ny, nx // 2 + 1), dtype=np.complex128)
+        for ky in range(-kmax, kmax + 1):
+            for kx in range(0, kmax + 1):
+                if kx == 0 and ky <= 0:
                     continue
-                g += rng.standard_normal() * np.cos(2.0 * np.pi * (kx * X / nx + ky * Y / ny)
-                                                     + rng.uniform(0.0, 2.0 * np.pi))
+                S[ky % ny, kx] = rng.standard_normal() + 1j * rng.standard_normal()
+        g = np.fft.irfft2(S, s=(ny, nx))
         out.append(g / np.abs(g).max())
     return 1.0 + eps_amp * out[0], u_amp * out[1], u_amp * out[2]
 

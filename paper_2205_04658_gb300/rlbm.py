@@ -1,0 +1,232 @@
+"""ctypes binding of librlbm.so (include/rlbm.h), the GB300 relativistic lattice
+Boltzmann library.  Argument marshalling only: every step of the update runs in
+the library's CUDA kernels.  PyTorch provides the device workspace and the stream.
+
+The functions keep the C names (rlbm_init, rlbm_step, rlbm_moments, ...); the
+``Lattice`` class bundles a workspace, a stream and a context.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librlbm.so")
+
+RLBM_OK, RLBM_E_INVAL, RLBM_E_NOMEM, RLBM_E_CUDA = 0, 1, 2, 3
+RLBM_E_UNSTABLE, RLBM_E_UNPHYSICAL, RLBM_E_TIMEOUT, RLBM_E_STATE = 4, 5, 6, 7
+PRECISION = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+class RlbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("rlbm status %d: %s" % (status, message))
+        self.status = status
+
+
+class rlbm_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("walls_y", ctypes.c_int32),
+        ("vset", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("a", ctypes.c_double), ("dt", ctypes.c_double), ("eta_over_s", ctypes.c_double),
+        ("eps0", ctypes.c_double), ("body_force", ctypes.c_double * 2),
+        ("kmin", ctypes.c_int32), ("kmax", ctypes.c_int32), ("force_amp", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("solid", ctypes.POINTER(ctypes.c_uint8)),
+        ("init_eps", ctypes.POINTER(ctypes.c_double)), ("init_ux", ctypes.POINTER(ctypes.c_double)),
+        ("init_uy", ctypes.POINTER(ctypes.c_double)), ("fp64_landau_vmax", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librlbm.so is not built (%s); run paper_2205_04658_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, c_i32, c_i64, c_sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        dp = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "rlbm_query_workspace": (c_i32, [ctypes.POINTER(rlbm_config), ctypes.POINTER(c_sz)]),
+            "rlbm_init": (c_i32, [ctypes.POINTER(rlbm_config), P, c_sz, P, ctypes.POINTER(P)]),
+            "rlbm_step": (c_i32, [P, c_i64]),
+            "rlbm_moments": (c_i32, [P, dp, dp, dp, dp]),
+            "rlbm_spectrum": (c_i32, [P, c_i32, dp]),
+            "rlbm_get_state": (c_i32, [P, dp, ctypes.POINTER(c_i64)]),
+            "rlbm_set_state": (c_i32, [P, dp, c_i64]),
+            "rlbm_num_planes": (c_i32, [P]),
+            "rlbm_sync": (c_i32, [P]),
+            "rlbm_current_step": (c_i64, [P]),
+            "rlbm_last_error": (ctypes.c_char_p, [P]),
+            "rlbm_free": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != RLBM_OK:
+        raise RlbmError(status, lib().rlbm_last_error(ctx).decode())
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_config(nx, ny, precision="f32", walls_y=0, vset=3, a=0.1, dt=0.05, eta_over_s=0.1, eps0=1.0,
+                body_force=(0.0, 0.0), kmin=0, kmax=0, force_amp=0.0, seed=0, solid=None,
+                init_eps=None, init_ux=None, init_uy=None, fp64_landau_vmax=0.0):
+    """An rlbm_config and the host arrays it points to (keep both alive until rlbm_init
+    returns)."""
+    keep = {}
+
+    def arr(x, dtype, name):
+        if x is None:
+            return None
+        a_ = np.ascontiguousarray(np.asarray(x, dtype=dtype).reshape(ny, nx))
+        keep[name] = a_
+        return a_.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8 if dtype == np.uint8 else ctypes.c_double))
+
+    c = rlbm_config()
+    c.nx, c.ny, c.walls_y, c.vset = nx, ny, int(walls_y), int(vset)
+    c.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    c.reserved0 = 0
+    c.a, c.dt, c.eta_over_s, c.eps0 = a, dt, eta_over_s, eps0
+    c.body_force[0], c.body_force[1] = body_force
+    c.kmin, c.kmax, c.force_amp, c.seed = int(kmin), int(kmax), float(force_amp), int(seed)
+    c.solid = arr(solid, np.uint8, "solid")
+    c.init_eps = arr(init_eps, np.float64, "eps")
+    c.init_ux = arr(init_ux, np.float64, "ux")
+    c.init_uy = arr(init_uy, np.float64, "uy")
+    c.fp64_landau_vmax = fp64_landau_vmax
+    return c, keep
+
+
+# ----- C names ---------------------------------------------------------------
+def rlbm_query_workspace(cfg):
+    n = ctypes.c_size_t(0)
+    _check(lib().rlbm_query_workspace(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def rlbm_init(cfg, dev_workspace, nbytes, cuda_stream):
+    ctx = ctypes.c_void_p()
+    _check(lib().rlbm_init(ctypes.byref(cfg), ctypes.c_void_p(dev_workspace), nbytes,
+                           ctypes.c_void_p(cuda_stream), ctypes.byref(ctx)))
+    return ctx
+
+
+def rlbm_step(ctx, nsteps):
+    _check(lib().rlbm_step(ctx, int(nsteps)), ctx)
+
+
+def rlbm_moments(ctx, eps=None, ux=None, uy=None, totals=None):
+    _check(lib().rlbm_moments(ctx, _dptr(eps), _dptr(ux), _dptr(uy), _dptr(totals)), ctx)
+
+
+def rlbm_spectrum(ctx, nbins, E):
+    _check(lib().rlbm_spectrum(ctx, int(nbins), _dptr(E)), ctx)
+
+
+def rlbm_get_state(ctx, host):
+    step = ctypes.c_int64(0)
+    _check(lib().rlbm_get_state(ctx, _dptr(host), ctypes.byref(step)), ctx)
+    return step.value
+
+
+def rlbm_set_state(ctx, host, step):
+    _check(lib().rlbm_set_state(ctx, _dptr(host), int(step)), ctx)
+
+
+def rlbm_num_planes(ctx):
+    return lib().rlbm_num_planes(ctx)
+
+
+def rlbm_sync(ctx):
+    _check(lib().rlbm_sync(ctx), ctx)
+
+
+def rlbm_current_step(ctx):
+    return lib().rlbm_current_step(ctx)
+
+
+def rlbm_last_error(ctx=None):
+    return lib().rlbm_last_error(ctx).decode()
+
+
+def rlbm_free(ctx):
+    lib().rlbm_free(ctx)
+
+
+# ----- convenience -----------------------------------------------------------
+class Lattice:
+    """A lattice on the current CUDA device: a torch-allocated workspace, a stream
+    (torch's current stream unless one is given) and a library context."""
+
+    def __init__(self, nx, ny, stream=None, **kw):
+        import torch
+        self.nx, self.ny = nx, ny
+        cfg, keep = make_config(nx, ny, **kw)
+        self.nbytes = rlbm_query_workspace(cfg)
+        self._ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        self.ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = rlbm_init(cfg, self.ptr, self.nbytes, self.stream.cuda_stream)
+        del keep
+
+    def step(self, n=1):
+        rlbm_step(self.ctx, n)
+
+    def moments(self):
+        e = np.empty((self.ny, self.nx))
+        ux = np.empty_like(e)
+        uy = np.empty_like(e)
+        tot = np.empty(4)
+        rlbm_moments(self.ctx, e, ux, uy, tot)
+        return e, ux, uy, tot
+
+    def totals(self):
+        tot = np.empty(4)
+        rlbm_moments(self.ctx, None, None, None, tot)
+        return tot
+
+    def spectrum(self, nbins):
+        E = np.empty(nbins)
+        rlbm_spectrum(self.ctx, nbins, E)
+        return E
+
+    def get_state(self):
+        q = rlbm_num_planes(self.ctx)
+        h = np.empty((q, self.ny, self.nx))
+        step = rlbm_get_state(self.ctx, h)
+        return h, step
+
+    def set_state(self, h, step):
+        rlbm_set_state(self.ctx, np.ascontiguousarray(h, dtype=np.float64), step)
+
+    @property
+    def current_step(self):
+        return rlbm_current_step(self.ctx)
+
+    def sync(self):
+        rlbm_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            rlbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
