@@ -2,6 +2,7 @@
 // workspace layout in the caller's device memory, host-built tables (streaming
 // weights, stirring modes and phase tables, FFT twiddles, solid-neighbour masks) and
 // the dispatch of the kernels of each storage type.
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -58,19 +59,22 @@ Modes shell_modes(int kmin, int kmax) {
 bool stirring_on(const rlbm_config &c) { return c.force_amp != 0.0; }
 
 struct Layout {
-  size_t pop[2], nbmask, err, EX, EY, G[2], coef[2], mode_kx, mode_ky, row_start;
+  size_t pop[2], nbmask, err, EX, EY, G[2], coef[2], mode_kx, row_start;
   size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, total;
   long long plane;
-  int pitch, Q, nrows, nmodes, max_bins;
+  int pitch, xoff, Q, nrows, nmodes, max_bins;
   long long max_blocks;
 };
 
 Layout make_layout(const rlbm_config &c) {
   Layout L{};
   L.Q = num_classes(c.vset);
-  L.pitch = (c.nx + 31) / 32 * 32;
-  L.plane = (long long)L.pitch * c.ny;
   const size_t sb = store_bytes(c.precision), rb = real_bytes(c.precision);
+  // ghost-padded planes: 128-byte left margin (interior starts on a line), one ghost
+  // column each side, rows padded to whole 128-byte lines; one ghost row each side
+  L.xoff = (int)(128 / sb);
+  L.pitch = (int)((L.xoff + c.nx + 1 + L.xoff - 1) / L.xoff * L.xoff);
+  L.plane = (long long)L.pitch * (c.ny + 2);
   const size_t ncell = (size_t)c.nx * c.ny;
   Modes m;
   if (stirring_on(c)) m = shell_modes(c.kmin, c.kmax);
@@ -91,7 +95,6 @@ Layout make_layout(const rlbm_config &c) {
   L.coef[0] = take(4 * rb * L.nmodes);
   L.coef[1] = take(4 * rb * L.nmodes);
   L.mode_kx = take(4 * L.nmodes);
-  L.mode_ky = take(4 * L.nmodes);
   L.row_start = take(4 * (L.nrows + 1));
   L.eps = take(8 * ncell);
   L.ux = take(8 * ncell);
@@ -171,7 +174,9 @@ struct rlbm_ctx {
   std::string msg;
   HostGeom geom;
   HostPhys phys;
-  dim3 block{32, 8, 1};
+  dim3 block{32, 8, 1};       // moments kernel
+  int grid_limit = 0;          // step kernel: 0 = one wave of resident CTAs
+  CUtensorMap tmap_in[2], tmap_out[2];
   std::vector<uint8_t> host_stage;
 
   template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
@@ -188,14 +193,68 @@ struct rlbm_ctx {
 
 namespace {
 
-cudaError_t dispatch_step(rlbm_ctx *c, const void *fin, void *fout, const HostStir &s) {
+cudaError_t dispatch_step(rlbm_ctx *c, int src, const HostStir &s) {
   unsigned *err = c->at<unsigned>(c->L.err);
+  const void *ti = &c->tmap_in[src], *to = &c->tmap_out[src ^ 1];
+  void *fout = c->ws + c->L.pop[src ^ 1];
   switch (c->cfg.precision) {
-    case RLBM_F64: return launch_step_f64(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
-    case RLBM_F32: return launch_step_f32(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
-    case RLBM_F16: return launch_step_f16(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
-    default: return launch_step_bf16(c->cfg.vset, fin, fout, c->geom, c->phys, s, err, c->block, c->stream);
+    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    default: return launch_step_bf16(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
   }
+}
+
+cudaError_t dispatch_ghosts(rlbm_ctx *c, int b) {
+  void *f = c->ws + c->L.pop[b];
+  switch (c->cfg.precision) {
+    case RLBM_F64: return launch_ghosts_f64(c->cfg.vset, f, c->geom, c->stream);
+    case RLBM_F32: return launch_ghosts_f32(c->cfg.vset, f, c->geom, c->stream);
+    case RLBM_F16: return launch_ghosts_f16(c->cfg.vset, f, c->geom, c->stream);
+    default: return launch_ghosts_bf16(c->cfg.vset, f, c->geom, c->stream);
+  }
+}
+
+// Tensor maps of one population buffer: loads see the whole ghost-padded planes,
+// {pitch, ny + 2, Q}, in boxes of {32 + 2 V, 10, Q} (a 32 x 8 tile with its halo,
+// V = 16 bytes of elements); stores are clipped at the last interior column and row,
+// {xoff + nx, ny + 1, Q}, in boxes of {32, 8, Q}.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+std::string make_tensor_maps(rlbm_ctx *c) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return "cuTensorMapEncodeTiled is not available";
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const int prec = c->cfg.precision;
+  const size_t eb = store_bytes(prec);
+  const CUtensorMapDataType dt = prec == RLBM_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : prec == RLBM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : prec == RLBM_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint32_t V = (cuuint32_t)(16 / eb);
+  const cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * eb, (cuuint64_t)c->L.plane * eb};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int b = 0; b < 2; ++b) {
+    void *base = c->ws + c->L.pop[b];
+    const cuuint64_t din[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->cfg.ny + 2, (cuuint64_t)c->L.Q};
+    const cuuint32_t bin[3] = {32 + 2 * V, 10, (cuuint32_t)c->L.Q};
+    CUresult r = encode(&c->tmap_in[b], dt, 3, base, din, strides, bin, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (load map) failed with " + std::to_string((int)r);
+    const cuuint64_t dout[3] = {(cuuint64_t)(c->L.xoff + c->cfg.nx), (cuuint64_t)c->cfg.ny + 1, (cuuint64_t)c->L.Q};
+    const cuuint32_t bout[3] = {32, 8, (cuuint32_t)c->L.Q};
+    r = encode(&c->tmap_out[b], dt, 3, base, dout, strides, bout, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (store map) failed with " + std::to_string((int)r);
+  }
+  return "";
 }
 
 cudaError_t dispatch_moments(rlbm_ctx *c) {
@@ -238,7 +297,6 @@ HostStir stir_for_step(rlbm_ctx *c, int64_t n) {
   s.EY = c->ws + L.EY;
   s.EX = c->ws + L.EX;
   s.mode_kx = c->at<int>(L.mode_kx);
-  s.mode_ky = c->at<int>(L.mode_ky);
   s.row_start = c->at<int>(L.row_start);
   s.seed = c->cfg.seed;
   s.step_new = n + 2;
@@ -304,7 +362,7 @@ template <typename S> void unpack_state(const rlbm_ctx *c, const uint8_t *src, d
   for (int q = 0; q < c->L.Q; ++q)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x)
-        dst[((size_t)q * ny + y) * nx + x] = to_double<S>(p[q * c->L.plane + (size_t)y * c->L.pitch + x]);
+        dst[((size_t)q * ny + y) * nx + x] = to_double<S>(p[q * c->L.plane + (size_t)(y + 1) * c->L.pitch + x + c->L.xoff]);
 }
 
 template <typename S> void pack_state(const rlbm_ctx *c, const double *src, uint8_t *dst) {
@@ -312,9 +370,8 @@ template <typename S> void pack_state(const rlbm_ctx *c, const double *src, uint
   const int nx = c->cfg.nx, ny = c->cfg.ny;
   for (int q = 0; q < c->L.Q; ++q)
     for (int y = 0; y < ny; ++y)
-      for (int x = 0; x < c->L.pitch; ++x)
-        p[q * c->L.plane + (size_t)y * c->L.pitch + x] =
-            x < nx ? from_double<S>(src[((size_t)q * ny + y) * nx + x]) : from_double<S>(0.0);
+      for (int x = 0; x < nx; ++x)
+        p[q * c->L.plane + (size_t)(y + 1) * c->L.pitch + x + c->L.xoff] = from_double<S>(src[((size_t)q * ny + y) * nx + x]);
 }
 
 }  // namespace
@@ -371,7 +428,12 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   std::memset(c->geom.beta, 0, sizeof(c->geom.beta));
   if (cfg->vset == 3) fill_beta<3>(C, c->geom.beta); else fill_beta<2>(C, c->geom.beta);
   c->geom.nx = cfg->nx; c->geom.ny = cfg->ny; c->geom.pitch = L.pitch; c->geom.plane = L.plane;
+  c->geom.walls = cfg->walls_y;
   c->geom.nbmask = nullptr;
+  {
+    const std::string tm = make_tensor_maps(c);
+    if (!tm.empty()) { c->msg = tm; return bail(RLBM_E_CUDA); }
+  }
 
   // relaxation and force constants
   const double T0 = temperature_of(cfg->eps0, cfg->vset);
@@ -435,7 +497,6 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
     if ((e = put(L.EX, keep[keep.size() - 2].data(), keep[keep.size() - 2].size())) != cudaSuccess ||
         (e = put(L.EY, keep.back().data(), keep.back().size())) != cudaSuccess ||
         (e = put(L.mode_kx, m.kx.data(), 4 * m.kx.size())) != cudaSuccess ||
-        (e = put(L.mode_ky, m.ky.data(), 4 * m.ky.size())) != cudaSuccess ||
         (e = put(L.row_start, m.row_start.data(), 4 * m.row_start.size())) != cudaSuccess) {
       c->cuda_fail(e, "upload of the stirring tables");
       return bail(RLBM_E_CUDA);
@@ -461,8 +522,13 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   if (cfg->init_eps) { if ((e = put(L.eps, cfg->init_eps, 8 * ncell)) != cudaSuccess) { c->cuda_fail(e, "upload of init_eps"); return bail(RLBM_E_CUDA); } de = c->at<double>(L.eps); }
   if (cfg->init_ux) { if ((e = put(L.ux, cfg->init_ux, 8 * ncell)) != cudaSuccess) { c->cuda_fail(e, "upload of init_ux"); return bail(RLBM_E_CUDA); } dux = c->at<double>(L.ux); }
   if (cfg->init_uy) { if ((e = put(L.uy, cfg->init_uy, 8 * ncell)) != cudaSuccess) { c->cuda_fail(e, "upload of init_uy"); return bail(RLBM_E_CUDA); } duy = c->at<double>(L.uy); }
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
+    if ((e = cudaMemsetAsync(c->ws + L.pop[b], 0, store_bytes(cfg->precision) * L.Q * L.plane, c->stream)) != cudaSuccess) {
+      c->cuda_fail(e, "cudaMemsetAsync");
+      return bail(RLBM_E_CUDA);
+    }
     if ((e = dispatch_init(c, c->ws + L.pop[b], de, dux, duy)) != cudaSuccess) { c->cuda_fail(e, "init kernel"); return bail(RLBM_E_CUDA); }
+  }
   if ((e = cudaMemsetAsync(c->ws + L.err, 0, 16, c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaMemsetAsync"); return bail(RLBM_E_CUDA); }
   if ((e = stir_prime(c, 0)) != cudaSuccess) { c->cuda_fail(e, "stirring set-up kernels"); return bail(RLBM_E_CUDA); }
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaStreamSynchronize"); return bail(RLBM_E_CUDA); }
@@ -479,7 +545,7 @@ rlbm_status rlbm_step(rlbm_ctx *c, int64_t nsteps) {
   Scoped dev(c->device);
   for (int64_t i = 0; i < nsteps; ++i) {
     const HostStir s = stir_for_step(c, c->step);
-    cudaError_t e = dispatch_step(c, c->ws + c->L.pop[c->cur], c->ws + c->L.pop[c->cur ^ 1], s);
+    cudaError_t e = dispatch_step(c, c->cur, s);
     if (e != cudaSuccess) return c->cuda_fail(e, "step kernel launch");
     c->cur ^= 1;
     ++c->step;
@@ -557,6 +623,7 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
   cudaError_t e = cudaMemcpyAsync(c->ws + c->L.pop[c->cur], c->host_stage.data(), bytes, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return c->cuda_fail(e, "copy of the state");
   c->step = step;
+  if ((e = dispatch_ghosts(c, c->cur)) != cudaSuccess) return c->cuda_fail(e, "ghost fill kernel");
   if ((e = stir_prime(c, step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
   return check_device(c);
 }

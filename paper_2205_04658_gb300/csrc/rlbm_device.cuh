@@ -17,7 +17,7 @@
 
 namespace rlbm {
 
-enum : unsigned { ERR_UNSTABLE = 1u, ERR_UNPHYSICAL = 2u };
+enum : unsigned { ERR_UNSTABLE = 1u, ERR_UNPHYSICAL = 2u, ERR_TIMEOUT = 4u };
 
 // ---------------------------------------------------------------------------
 // Velocity classes.  VS = 3: the paper's set folded to 17 in-plane classes
@@ -92,6 +92,11 @@ template <> __device__ __forceinline__ float load_h<__half, float>(const __half 
 template <> __device__ __forceinline__ float load_h<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
   return __bfloat162float(__ldg(p));
 }
+template <typename S, typename R> __device__ __forceinline__ R load_h_s(const S *p) { return (R)*p; }
+template <> __device__ __forceinline__ float load_h_s<__half, float>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float load_h_s<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+  return __bfloat162float(*p);
+}
 template <typename S, typename R> __device__ __forceinline__ S store_h(R v) { return (S)v; }
 template <> __device__ __forceinline__ __half store_h<__half, float>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 store_h<__nv_bfloat16, float>(float v) {
@@ -102,6 +107,17 @@ template <typename S> struct RealOf { using type = float; };
 template <> struct RealOf<double> { using type = double; };
 
 // ---------------------------------------------------------------------------
+// Storage layout.  Each population plane holds (ny + 2) rows of `pitch` elements:
+// interior cell (x, y) sits at row y + 1, column x + XOFF; column XOFF - 1 and XOFF + nx
+// and rows 0 and ny + 1 are ghost copies of the periodic neighbours (solid walls keep
+// zero ghost rows).  XOFF is 128 bytes, so interior rows start on a 128-byte line.
+// ---------------------------------------------------------------------------
+template <typename S> struct PadLayout {
+  static constexpr int XOFF = 128 / (int)sizeof(S);
+  static constexpr int V = 16 / (int)sizeof(S);  // TMA x granule (16 bytes)
+};
+
+// ---------------------------------------------------------------------------
 // Parameters
 // ---------------------------------------------------------------------------
 template <typename R> struct alignas(16) R4 { R x, y, z, w; };
@@ -109,7 +125,8 @@ template <typename R> struct alignas(2 * sizeof(R)) R2 { R x, y; };
 
 template <typename R> struct Geometry {
   int nx, ny, pitch;
-  long long plane;          // elements per plane (pitch * ny)
+  long long plane;          // elements per plane (pitch * (ny + 2))
+  int walls;                // y ghost rows are solid (never written)
   const uint16_t *nbmask;   // bit 4: cell solid; bit (dy+1)*3+(dx+1): neighbour (x+dx, y+dy) solid
   R beta[17][4];            // bilinear weights of corners (0,0), (s_x,0), (0,s_y), (s_x,s_y)
 };
@@ -118,8 +135,7 @@ template <typename R> struct Physics {
   R omega0;        // dt T0 / (TAU_NUM eta/s): relaxation factor at eps = eps0
   R fpref;         // -6 dt / T0: force prefactor including dt
   R body_x, body_y;
-  double vmax2;    // FP32 path: |v|^2 above which Landau runs in FP64
-  int has_force;   // any force (body or stirring)
+  R vmax2;         // FP32 path: |v|^2 above which Landau runs in FP64
 };
 
 template <typename R> struct Stir {
@@ -132,7 +148,6 @@ template <typename R> struct Stir {
   const R4<R> *coef_next;  // [nmodes]: (cx.re, cx.im, cy.re, cy.im) of step n+1
   R4<R> *coef_new;         // [nmodes] of step n+2 (written)
   const int *mode_kx;      // [nmodes]
-  const int *mode_ky;      // [nmodes]
   const int *row_start;    // [nrows+1] mode range of each row (modes sorted by k_y)
   const R2<R> *EX;         // [nx]: exp(i 2 pi j / nx)
   unsigned long long seed;
@@ -188,16 +203,15 @@ __device__ inline R4<R> stir_row_entry(const Stir<R> &s, const R4<R> *coef, int 
   return g;
 }
 
-// Work a step launch does for the following steps: thread t < nrows*nx builds one
-// entry of G for step n+1, thread t < nmodes draws mode t of step n+2.
+// Work a step launch does for the following steps (grid-stride over all threads of
+// the launch): the table of step n+1 and the Philox draws of step n+2.
 template <typename R>
-__device__ inline void stir_prepare(const Stir<R> &s, long long t, int nx) {
+__device__ inline void stir_prepare(const Stir<R> &s, long long t0, long long nthreads, int nx) {
   if (s.nrows == 0) return;
-  if (t < (long long)s.nrows * nx) {
-    const int r = (int)(t / nx), x = (int)(t % nx);
-    s.G_next[t] = stir_row_entry<R>(s, s.coef_next, r, x, nx);
-  }
-  if (t < s.nmodes) {
+  const long long entries = (long long)s.nrows * nx;
+  for (long long t = t0; t < entries; t += nthreads)
+    s.G_next[t] = stir_row_entry<R>(s, s.coef_next, (int)(t / nx), (int)(t % nx), nx);
+  for (long long t = t0; t < s.nmodes; t += nthreads) {
     double c[4];
     stir_draw(s.seed, s.step_new, (int)t, s.amp, c);
     s.coef_new[t] = R4<R>{(R)c[0], (R)c[1], (R)c[2], (R)c[3]};
@@ -205,102 +219,147 @@ __device__ inline void stir_prepare(const Stir<R> &s, long long t, int nx) {
 }
 
 // ---------------------------------------------------------------------------
-// Streaming: bilinear pull of every class with bounce-back (solid source corners
-// contribute the reversed population of the receiving cell).
+// Arithmetic helpers: exact in FP64, hardware approximations (<= 2 ulp) in FP32.
 // ---------------------------------------------------------------------------
-template <typename S, typename R, int VS, bool MASK>
-__device__ __forceinline__ void pull(const S *__restrict__ fin, const Geometry<R> &g, int x, int y,
-                                     unsigned nb, R h[VSet<VS>::Q]) {
-  constexpr int Q = VSet<VS>::Q;
-  const int xm = x == 0 ? g.nx - 1 : x - 1;
-  const int xp = x == g.nx - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? g.ny - 1 : y - 1;
-  const int yp = y == g.ny - 1 ? 0 : y + 1;
-  R c[Q];
-#pragma unroll
-  for (int q = 0; q < Q; ++q) c[q] = load_h<S, R>(fin + q * g.plane + (long long)y * g.pitch + x);
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
-    const S *pl = fin + q * g.plane;
-    const int cx = sx > 0 ? xm : xp;        // source column x - s_x
-    const int ry = sy > 0 ? ym : yp;        // source row    y - s_y
-    R acc = g.beta[q][0] * c[q];
-    if (sx != 0) {
-      const bool solid = MASK && ((nb >> (4 - sx)) & 1u);
-      const R v = solid ? c[VSet<VS>::opp(q)] : load_h<S, R>(pl + (long long)y * g.pitch + cx);
-      acc += g.beta[q][1] * v;
-    }
-    if (sy != 0) {
-      const bool solid = MASK && ((nb >> (4 - 3 * sy)) & 1u);
-      const R v = solid ? c[VSet<VS>::opp(q)] : load_h<S, R>(pl + (long long)ry * g.pitch + x);
-      acc += g.beta[q][2] * v;
-    }
-    if (sx != 0 && sy != 0) {
-      const bool solid = MASK && ((nb >> (4 - 3 * sy - sx)) & 1u);
-      const R v = solid ? c[VSet<VS>::opp(q)] : load_h<S, R>(pl + (long long)ry * g.pitch + cx);
-      acc += g.beta[q][3] * v;
-    }
-    h[q] = acc;
-  }
-}
+template <typename T> struct FM;
+template <> struct FM<double> {
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double qroot(double x) { return sqrt(sqrt(x)); }
+  static __device__ __forceinline__ double croot(double x) { return cbrt(x); }
+};
+template <> struct FM<float> {
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+  static __device__ __forceinline__ float qroot(float x) { return rsqrtf(rsqrtf(x)); }
+  static __device__ __forceinline__ float croot(float x) { return cbrtf(x); }
+};
 
 // ---------------------------------------------------------------------------
-// Moments and Landau matching.  In units of eps0:
-//   T^00 = 1 + e,  T^0a = m_a,  T^ab = delta_ab / 3 + t_ab  (a, b in {x, y})
-// with e = sum w h, m = sum w h v, t = sum w h v v (the rest-equilibrium parts are
-// exact constants).  Landau: the timelike eigenvector u = gamma (1, v) of T^mu_nu on
-// the (t, x, y) block solves  R(v) = m - T^{ab} v_b - (T^00 - m.v) v = 0  (2-D Newton).
+// Moments.  In units of eps0, with h the normalised deviations:
+//   T^00 = 1 + e,  T^0a = m_a,  T^ab = delta_ab / D_p + t_ab  (a, b in {x, y})
+//   e = sum w h, m = sum w h v, t = sum w h v v, and (for the force) the third
+//   moments w_abc = sum w h v_a v_b v_c.  The rest-equilibrium parts are exact.
 // ---------------------------------------------------------------------------
-template <typename T> struct Mom { T e, mx, my, txx, txy, tyy; };
+template <typename T> struct Mom { T e, mx, my, txx, txy, tyy, wxxx, wxxy, wxyy, wyyy; };
 
-template <typename T, typename R, int VS>
-__device__ __forceinline__ Mom<T> moments_of(const R h[VSet<VS>::Q]) {
-  constexpr int Q = VSet<VS>::Q;
-  Mom<T> M{T(0), T(0), T(0), T(0), T(0), T(0)};
+// Generic sum over classes with compile-time coefficients.
+template <typename T, typename R, int VS, bool THIRD>
+__device__ __forceinline__ Mom<T> moments_generic(const R h[VSet<VS>::Q]) {
+  using V = VSet<VS>;
+  Mom<T> M{};
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const T wh = T(VSet<VS>::w(q)) * (T)h[q];
-    const T vx = T(VSet<VS>::vx(q)), vy = T(VSet<VS>::vy(q));
-    M.e += wh;
-    if (vx != T(0)) M.mx += wh * vx;
-    if (vy != T(0)) M.my += wh * vy;
-    if (vx != T(0)) M.txx += wh * (vx * vx);
-    if (vx != T(0) && vy != T(0)) M.txy += wh * (vx * vy);
-    if (vy != T(0)) M.tyy += wh * (vy * vy);
+  for (int q = 0; q < V::Q; ++q) {
+    const double w = V::w(q), vx = V::vx(q), vy = V::vy(q);
+    const T hq = (T)h[q];
+    M.e += T(w) * hq;
+    if (vx != 0.0) { M.mx += T(w * vx) * hq; M.txx += T(w * vx * vx) * hq; }
+    if (vy != 0.0) { M.my += T(w * vy) * hq; M.tyy += T(w * vy * vy) * hq; }
+    if (vx != 0.0 && vy != 0.0) M.txy += T(w * vx * vy) * hq;
+    if (THIRD) {
+      if (vx != 0.0) M.wxxx += T(w * vx * vx * vx) * hq;
+      if (vx != 0.0 && vy != 0.0) { M.wxxy += T(w * vx * vx * vy) * hq; M.wxyy += T(w * vx * vy * vy) * hq; }
+      if (vy != 0.0) M.wyyy += T(w * vy * vy * vy) * hq;
+    }
   }
   return M;
 }
 
-// Returns false when Newton did not converge to |R| <= tol * T^00 (or |v| >= 1).
+// The 17 folded classes of the paper's set come in four sign-symmetric groups
+// {(+a,+b), (-a,+b), (-a,-b), (+a,-b)} (diagonals) or {(+a,0), (0,+a), (-a,0), (0,-a)}
+// (axes).  Sums and differences within a group (a butterfly) give each moment from one
+// product per group instead of one per class.
+template <typename T, typename R, bool THIRD>
+__device__ __forceinline__ void moments_axis_group(Mom<T> &M, double w, double a, T h0, T h1, T h2, T h3) {
+  // classes (+a,0), (0,+a), (-a,0), (0,-a)
+  const T sx = h0 + h2, dx = h0 - h2, sy = h1 + h3, dy = h1 - h3;
+  M.e += T(w) * (sx + sy);
+  M.mx += T(w * a) * dx;
+  M.my += T(w * a) * dy;
+  M.txx += T(w * a * a) * sx;
+  M.tyy += T(w * a * a) * sy;
+  if (THIRD) { M.wxxx += T(w * a * a * a) * dx; M.wyyy += T(w * a * a * a) * dy; }
+}
+template <typename T, typename R, bool THIRD>
+__device__ __forceinline__ void moments_diag_group(Mom<T> &M, double w, double a, T h0, T h1, T h2, T h3) {
+  // classes (+a,+a), (-a,+a), (-a,-a), (+a,-a)
+  const T s02 = h0 + h2, d02 = h0 - h2, s13 = h1 + h3, d31 = h3 - h1;
+  const T P0 = s02 + s13, Pxy = s02 - s13, Px = d02 + d31, Py = d02 - d31;
+  M.e += T(w) * P0;
+  M.txx += T(w * a * a) * P0;
+  M.tyy += T(w * a * a) * P0;
+  M.mx += T(w * a) * Px;
+  M.my += T(w * a) * Py;
+  M.txy += T(w * a * a) * Pxy;
+  if (THIRD) {
+    M.wxxx += T(w * a * a * a) * Px;
+    M.wxyy += T(w * a * a * a) * Px;
+    M.wxxy += T(w * a * a * a) * Py;
+    M.wyyy += T(w * a * a * a) * Py;
+  }
+}
+
+template <typename T, typename R, int VS, bool THIRD>
+__device__ __forceinline__ Mom<T> moments_of(const R h[VSet<VS>::Q]) {
+  if constexpr (VS == 3) {
+    using V = VSet<3>;
+    Mom<T> M{};
+    M.e = T(V::w(0)) * (T)h[0];
+    moments_axis_group<T, R, THIRD>(M, V::w(1), 1.0, (T)h[1], (T)h[2], (T)h[3], (T)h[4]);
+    moments_diag_group<T, R, THIRD>(M, V::w(5), RLBM_S2, (T)h[5], (T)h[6], (T)h[7], (T)h[8]);
+    moments_axis_group<T, R, THIRD>(M, V::w(9), RLBM_S2, (T)h[9], (T)h[10], (T)h[11], (T)h[12]);
+    moments_diag_group<T, R, THIRD>(M, V::w(13), RLBM_S3, (T)h[13], (T)h[14], (T)h[15], (T)h[16]);
+    return M;
+  } else {
+    return moments_generic<T, R, VS, THIRD>(h);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Landau matching: the timelike eigenvector u = gamma (1, v) of T^mu_nu on the
+// (t, x, y) block solves  R(v) = m - T^{ab} v_b - (T^00 - m.v) v = 0.  Starting point:
+// the exact solution for an ideal fluid with the same T^00 and T^0a (for D_p = 3,
+// |m| / T^00 = 4 v / (3 + v^2); for D_p = 2, 3 v / (2 + v^2)), then Newton steps.
+// Returns false when the last Newton step is not small (|dv| > tol (|v| + 1e-6)) or
+// the result is not a subluminal flow with positive energy density.
+// ---------------------------------------------------------------------------
 template <typename T, int VS>
 __device__ __forceinline__ bool landau(const Mom<T> &M, int maxit, T tol, T &vx, T &vy) {
-  constexpr T third = T(1.0 / VSet<VS>::DP);
+  constexpr T dinv = T(1.0 / VSet<VS>::DP);
   const T T00 = T(1) + M.e;
-  const T Txx = third + M.txx, Txy = M.txy, Tyy = third + M.tyy;
-  const T s = T(VSet<VS>::DP) / T(VSet<VS>::DP + 1) / T00;  // small-v start: v = D m / ((D+1) T^00)
-  vx = s * M.mx;
-  vy = s * M.my;
-  T rx = T(0), ry = T(0);
+  const T i00 = FM<T>::rcp(T00);
+  const T ax = M.mx * i00, ay = M.my * i00, m2 = ax * ax + ay * ay;
+  T c;
+  if (VS == 3) c = T(3) * FM<T>::rcp(T(2) + FM<T>::sqrt_(fmax(T(4) - T(3) * m2, T(0))));
+  else c = T(4) * FM<T>::rcp(T(3) + FM<T>::sqrt_(fmax(T(9) - T(8) * m2, T(0))));
+  vx = c * ax;
+  vy = c * ay;
+  const T Txx = dinv + M.txx, Txy = M.txy, Tyy = dinv + M.tyy;
+  T d2 = T(0);
   for (int it = 0; it < maxit; ++it) {
     const T E = T00 - (M.mx * vx + M.my * vy);
-    rx = M.mx - (Txx * vx + Txy * vy) - E * vx;
-    ry = M.my - (Txy * vx + Tyy * vy) - E * vy;
+    const T rx = M.mx - (Txx * vx + Txy * vy) - E * vx;
+    const T ry = M.my - (Txy * vx + Tyy * vy) - E * vy;
     // J = dR/dv = -T^{ab} + v_a m_b - E delta_ab
     const T jxx = -Txx + vx * M.mx - E, jxy = -Txy + vx * M.my;
     const T jyx = -Txy + vy * M.mx, jyy = -Tyy + vy * M.my - E;
-    const T det = jxx * jyy - jxy * jyx;
-    const T dx = -(jyy * rx - jxy * ry) / det;
-    const T dy = -(-jyx * rx + jxx * ry) / det;
+    const T idet = FM<T>::rcp(jxx * jyy - jxy * jyx);
+    const T dx = (jxy * ry - jyy * rx) * idet;
+    const T dy = (jyx * rx - jxx * ry) * idet;
     vx += dx;
     vy += dy;
-    if (dx * dx + dy * dy <= tol * tol * (T(1e-30) + vx * vx + vy * vy)) { rx = ry = T(0); break; }
+    d2 = dx * dx + dy * dy;
+    if constexpr (sizeof(T) == 8) {
+      if (d2 <= 1e-32 * (vx * vx + vy * vy) + 1e-300) break;
+    } else {
+      if (d2 <= tol * tol * (T(1e-6) + vx * vx + vy * vy)) break;
+    }
   }
-  const T E = T00 - (M.mx * vx + M.my * vy);
-  rx = M.mx - (Txx * vx + Txy * vy) - E * vx;
-  ry = M.my - (Txy * vx + Tyy * vy) - E * vy;
   const T v2 = vx * vx + vy * vy;
-  return (v2 < T(1)) && (E > T(0)) && (sqrt(rx * rx + ry * ry) <= T(64) * tol * T00);
+  const T lim = tol * (T(1e-6) + v2);
+  return (v2 < T(1)) && (T00 - (M.mx * vx + M.my * vy) > T(0)) && (d2 <= tol * lim);
 }
 
 // Macroscopic result of one cell (eps^ = eps / eps0, u^mu = gamma (1, v)).
@@ -312,30 +371,101 @@ __device__ __forceinline__ Macro<T> macro_from(const Mom<T> &M, int maxit, T tol
   T vx, vy;
   const bool ok = landau<T, VS>(M, maxit, tol, vx, vy);
   const T v2 = vx * vx + vy * vy;
-  const T gam = T(1) / sqrt(T(1) - v2);
+  const T gam = FM<T>::rsqrt(T(1) - v2);
   r.eps_m1 = M.e - (M.mx * vx + M.my * vy);
   r.u0 = gam; r.ux = gam * vx; r.uy = gam * vy; r.vx = vx; r.vy = vy;
   r.ok = ok && (T(1) + r.eps_m1 > T(0)) && isfinite(r.eps_m1) && isfinite(gam);
   return r;
 }
 
-// Landau matching of one cell in the storage's compute type; the FP32 path re-solves
-// in FP64 (moments re-summed in FP64 from the same h) when its Newton solve fails or
-// |v|^2 exceeds vmax2.
+// Landau matching of one cell in the compute type; the FP32 path re-solves in FP64
+// (moments re-summed in FP64 from the same h) when its two Newton steps have not
+// converged or |v|^2 exceeds vmax2.
 template <typename R, int VS>
-__device__ __forceinline__ Macro<R> cell_macro(const R h[VSet<VS>::Q], const Mom<R> &M, double vmax2) {
+__device__ __forceinline__ Macro<R> cell_macro(const R h[VSet<VS>::Q], const Mom<R> &M, R vmax2) {
   if constexpr (sizeof(R) == 8) {
-    return macro_from<double, VS>(M, 40, 1e-15);
+    return macro_from<double, VS>(M, 40, 1e-12);
   } else {
-    Macro<float> m = macro_from<float, VS>(M, 8, 2e-7f);
-    if (!m.ok || (double)(m.vx * m.vx + m.vy * m.vy) > vmax2) {
-      const Mom<double> Md = moments_of<double, R, VS>(h);
-      const Macro<double> d = macro_from<double, VS>(Md, 40, 1e-15);
+    Macro<float> m = macro_from<float, VS>(M, 4, 3e-4f);
+    if (!m.ok || m.vx * m.vx + m.vy * m.vy > vmax2) {
+      const Mom<double> Md = moments_of<double, R, VS, false>(h);
+      const Macro<double> d = macro_from<double, VS>(Md, 40, 1e-12);
       m.eps_m1 = (float)d.eps_m1; m.u0 = (float)d.u0; m.ux = (float)d.ux; m.uy = (float)d.uy;
       m.vx = (float)d.vx; m.vy = (float)d.vy; m.ok = d.ok;
     }
     return m;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Collision and force of one cell, as per-class polynomials in v_i:
+//   h*_i = h_i + omega (u^0 - u.v_i)(h_eq,i - h_i) + dt S_i / (w_i eps0)
+//   h_eq,i = (eps^ - 1) + CA eps^ u^0 (u.v_i) + CB eps^ (u.v_i)^2 - CC eps^ |u|^2
+// (the equilibrium of Eq. rel_pdf_exp_coef with T_eq = (eps + P) u u - P g), so with
+// t = u.v_i:  h*_i = h_i (1 - omega u^0 + omega t) + p0 + p1 t + p2 t^2 + p3 t^3 + S_i.
+// The force (Eq. forceTerm with App. B's coefficients, prefactor -6/T0 dt):
+//   S_i = fpref [ F.M1 / 4 - (M0 / 2) F.v_i + 5/4 v_i.B.v_i - 5/2 (F.v_i)(v_i.M1) ]
+//       = s0 + s1.v_i + v_i.S2.v_i + szz v_z,i^2
+// with B_ab = sum f (F.v) v_a v_b and B_zz = F.M1 - B_xx - B_yy (|v| = 1).
+// ---------------------------------------------------------------------------
+template <typename R> struct Coll {
+  R ux, uy, k0, om, p0, p1, p2, p3;
+  R s0, s1x, s1y, sxx, sxy2, syy, szz;
+};
+
+template <typename R, int VS, bool FORCE>
+__device__ __forceinline__ Coll<R> coll_coeffs(const Mom<R> &M, const Macro<R> &m, R omega0, R fpref, R Fx, R Fy) {
+  using V = VSet<VS>;
+  Coll<R> c;
+  const R epsh = R(1) + m.eps_m1;
+  const R om = VS == 3 ? omega0 * FM<R>::qroot(epsh) : omega0 * FM<R>::croot(epsh);
+  const R u2 = m.ux * m.ux + m.uy * m.uy;
+  const R ca = R(V::CA) * epsh * m.u0, cb = R(V::CB) * epsh, cc = m.eps_m1 - R(V::CC) * epsh * u2;
+  c.ux = m.ux; c.uy = m.uy; c.om = om;
+  c.k0 = R(1) - om * m.u0;
+  c.p0 = om * m.u0 * cc;
+  c.p1 = om * (m.u0 * ca - cc);
+  c.p2 = om * (m.u0 * cb - ca);
+  c.p3 = -om * cb;
+  c.s0 = c.s1x = c.s1y = c.sxx = c.sxy2 = c.syy = c.szz = R(0);
+  if (FORCE) {
+    const R FM1 = Fx * M.mx + Fy * M.my, M0 = R(1) + M.e;
+    const R Bxx = Fx * M.wxxx + Fy * M.wxxy;
+    const R Bxy = Fx * M.wxxy + Fy * M.wxyy;
+    const R Byy = Fx * M.wxyy + Fy * M.wyyy;
+    const R Bzz = FM1 - Bxx - Byy;
+    const R f54 = R(1.25) * fpref;
+    c.s0 = R(0.25) * fpref * FM1;
+    c.s1x = R(-0.5) * fpref * M0 * Fx;
+    c.s1y = R(-0.5) * fpref * M0 * Fy;
+    c.sxx = f54 * (Bxx - R(2) * Fx * M.mx);
+    c.sxy2 = R(2) * f54 * (Bxy - Fx * M.my - Fy * M.mx);
+    c.syy = f54 * (Byy - R(2) * Fy * M.my);
+    c.szz = f54 * Bzz;
+  }
+  c.s0 += c.p0;
+  return c;
+}
+
+template <typename R, int VS, bool FORCE>
+__device__ __forceinline__ R collide_class(const Coll<R> &c, int q, R h) {
+  using V = VSet<VS>;
+  const double vx = V::vx(q), vy = V::vy(q), vz2 = V::vz2(q);
+  R t = R(0);
+  if (vx != 0.0) t = c.ux * R(vx);
+  if (vy != 0.0) t = fma(c.uy, R(vy), t);
+  R acc = c.s0;
+  if (FORCE) {
+    if (vx != 0.0) acc = fma(c.s1x, R(vx), acc);
+    if (vy != 0.0) acc = fma(c.s1y, R(vy), acc);
+    if (vx != 0.0) acc = fma(c.sxx, R(vx * vx), acc);
+    if (vx != 0.0 && vy != 0.0) acc = fma(c.sxy2, R(vx * vy), acc);
+    if (vy != 0.0) acc = fma(c.syy, R(vy * vy), acc);
+    if (vz2 != 0.0) acc = fma(c.szz, R(vz2), acc);
+  }
+  if (vx != 0.0 || vy != 0.0) acc = fma(t, fma(t, fma(t, c.p3, c.p2), c.p1), acc);
+  const R k = (vx != 0.0 || vy != 0.0) ? fma(c.om, t, c.k0) : c.k0;
+  return fma(h, k, acc);
 }
 
 }  // namespace rlbm

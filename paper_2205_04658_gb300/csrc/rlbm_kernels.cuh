@@ -1,96 +1,214 @@
 // Kernels of the relativistic lattice Boltzmann update (arXiv 2205.04658) and the
 // host launchers of one storage type.  Included once per storage type by
-// rlbm_kernels_<type>.cu, which defines RLBM_STORE and RLBM_SUFFIX.
+// rlbm_kernels_<type>.cu.
 #pragma once
 
 #include "rlbm_device.cuh"
 #include "rlbm_launch.h"
+#include "rlbm_tma.cuh"
+
+#include <climits>
 
 namespace rlbm {
 
+constexpr int TILE_X = 32, TILE_Y = 8, NTHREADS = TILE_X * TILE_Y;
+constexpr long long WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: bounded TMA waits
+
+template <typename S, int VS> struct Tile {
+  static constexpr int Q = VSet<VS>::Q;
+  static constexpr int V = PadLayout<S>::V;
+  static constexpr int XOFF = PadLayout<S>::XOFF;
+  static constexpr int TXB = TILE_X + 2 * V;         // staged columns (16-byte granules on both sides)
+  static constexpr int TYB = TILE_Y + 2;             // staged rows (one halo row each side)
+  static constexpr int IN_ELEMS = Q * TYB * TXB;
+  static constexpr int OUT_ELEMS = Q * TILE_Y * TILE_X;
+  static constexpr int IN_BYTES = IN_ELEMS * (int)sizeof(S);
+  static constexpr int OUT_BYTES = OUT_ELEMS * (int)sizeof(S);
+  static constexpr int IN_STRIDE = (IN_BYTES + 127) / 128 * 128;
+  static constexpr int OUT_STRIDE = (OUT_BYTES + 127) / 128 * 128;
+  static constexpr int NST = 2;                      // input stages
+  static constexpr int SMEM = NST * IN_STRIDE + 2 * OUT_STRIDE + 64;
+};
+
 // ---------------------------------------------------------------------------
-// The fused step (procedure items 2-5 of Sec. "The Standard/Classical LBM", with
-// the driving term of Sec. "The Driving Term"): pull-stream f*_n -> f_n, moments,
-// Landau matching, equilibrium, Anderson-Witting relaxation, projected force, store
-// f*_{n+1}.  One thread per cell.
+// The fused step (procedure items 2-5 of Sec. "The Standard/Classical LBM", with the
+// driving term of Sec. "The Driving Term").  Persistent CTAs walk the 32 x 8 tiles of
+// the lattice.  Per tile, one 3-D TMA copy stages all Q planes of the tile plus a
+// one-cell halo (ghost rows/columns carry the periodic wrap) into shared memory,
+// double-buffered on mbarriers; each thread pull-streams its cell from shared memory
+// (bilinear weights, bounce-back substitution from the mask), takes the moments,
+// Landau-matches, relaxes and adds the force, writes the Q results into a shared
+// output tile that one TMA store writes back, and refreshes the ghost copies of
+// boundary cells with plain stores.
 // ---------------------------------------------------------------------------
-template <typename S, int VS, bool MASK>
-__global__ void __launch_bounds__(256)
-step_kernel(const S *__restrict__ fin, S *__restrict__ fout, const Geometry<typename RealOf<S>::type> g,
+template <typename S, int VS, bool MASK, bool FORCE>
+__global__ void __launch_bounds__(NTHREADS)
+step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+            S *__restrict__ fout, const Geometry<typename RealOf<S>::type> g,
             const Physics<typename RealOf<S>::type> p, const Stir<typename RealOf<S>::type> st,
             unsigned *__restrict__ err) {
   using R = typename RealOf<S>::type;
   using V = VSet<VS>;
+  using TL = Tile<S, VS>;
   constexpr int Q = V::Q;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const long long t = ((long long)(blockIdx.y * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y) * blockDim.x
-                      + threadIdx.x;
-  stir_prepare<R>(st, t, g.nx);
-  if (x >= g.nx || y >= g.ny) return;
-  unsigned nb = 0;
-  if (MASK) {
-    nb = g.nbmask[(long long)y * g.nx + x];
-    if (nb & 16u) return;  // solid cell: holds no fluid, never read by its neighbours
-  }
-  R h[Q];
-  pull<S, R, VS, MASK>(fin, g, x, y, nb, h);
-  const Mom<R> M = moments_of<R, R, VS>(h);
-  const Macro<R> m = cell_macro<R, VS>(h, M, p.vmax2);
-  if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
-  const R epsh = R(1) + m.eps_m1;
-  const R omega = VS == 3 ? p.omega0 * sqrt(sqrt(epsh)) : p.omega0 * cbrt(epsh);
-  const R u2 = m.ux * m.ux + m.uy * m.uy;
-  const R ca = R(V::CA) * epsh * m.u0, cb = R(V::CB) * epsh, cc = m.eps_m1 - R(V::CC) * epsh * u2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S *sin = reinterpret_cast<S *>(smem);
+  S *sout = reinterpret_cast<S *>(smem + TL::NST * TL::IN_STRIDE);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TL::NST * TL::IN_STRIDE + 2 * TL::OUT_STRIDE);
 
-  // Force at this cell: uniform body force plus the stirring field
-  // F(x, y) = sum_rows Re[G_r(x) exp(i 2 pi k_y,r y / ny)].
-  R Fx = p.body_x, Fy = p.body_y;
-  for (int r = 0; r < st.nrows; ++r) {
-    const R4<R> G = st.G_cur[(long long)r * g.nx + x];
-    const R2<R> E = st.EY[(long long)r * g.ny + y];
-    Fx += G.x * E.x - G.y * E.y;
-    Fy += G.z * E.x - G.w * E.y;
+  const int tid = threadIdx.x;
+  const int lx = tid % TILE_X, ly = tid / TILE_X;
+  const int ntx = (g.nx + TILE_X - 1) / TILE_X, nty = (g.ny + TILE_Y - 1) / TILE_Y;
+  const int ntiles = ntx * nty;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < TL::NST; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
   }
-  // Force moments (App. B): M0 = T^00, M1 = T^0a, B_ab = sum f (F.v) v_a v_b, B_zz from
-  // the trace B_xx + B_yy + B_zz = F.M1 (|v| = 1).
-  R FM1 = R(0), M0 = R(0), Bxx = R(0), Bxy = R(0), Byy = R(0), Bzz = R(0);
-  if (VS == 3 && p.has_force) {
+  __syncthreads();
+  auto issue = [&](int k) {  // stage the k-th tile of this CTA into stage k % NST
+    const int t = blockIdx.x + k * gridDim.x;
+    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    uint64_t *b = &bar[k % TL::NST];
+    mbar_expect_tx(b, TL::IN_BYTES);
+    tma_load_3d(sin + (k % TL::NST) * (TL::IN_STRIDE / (int)sizeof(S)), &tin, b, x0 + TL::XOFF - TL::V, y0, 0);
+  };
+  if (tid == 0)
+    for (int k = 0; k < TL::NST && k < my_tiles; ++k) issue(k);
+
+  // preparation of the stirring table of step n+1 and the draws of step n+2
+  stir_prepare<R>(st, (long long)blockIdx.x * NTHREADS + tid, (long long)gridDim.x * NTHREADS, g.nx);
+
+  // Every thread waits for the staged tile (bounded); the vote in the barrier makes the
+  // whole CTA wind down together if a copy never lands.
+  bool alive = true;
+  {
+    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) alive = false;
+  }
+  for (int k = 0; alive && k < my_tiles; ++k) {
+    const int t = blockIdx.x + k * gridDim.x;
+    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    const int x = x0 + lx, y = y0 + ly;
+    const int s = k % TL::NST;
+    const S *tile = sin + s * (TL::IN_STRIDE / (int)sizeof(S));
+    S *otile = sout + (k & 1) * (TL::OUT_STRIDE / (int)sizeof(S));
+    const bool inside = x < g.nx && y < g.ny;
+    unsigned nb = 0;
+    if (MASK && inside) nb = g.nbmask[(long long)y * g.nx + x];
+    const bool fluid = inside && !(MASK && (nb & 16u));
+    R hn[Q];
+    if (fluid) {
+      // pull-streaming from the staged tile: cell (lx, ly) at row ly + 1, column lx + V
+      const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
+      R h[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const R vx = R(V::vx(q)), vy = R(V::vy(q));
-      if (vx == R(0) && vy == R(0)) continue;
-      const R whf = R(V::w(q)) * h[q] * (Fx * vx + Fy * vy);
-      Bxx += whf * (vx * vx);
-      Bxy += whf * (vx * vy);
-      Byy += whf * (vy * vy);
-    }
-    FM1 = Fx * M.mx + Fy * M.my;
-    M0 = R(1) + M.e;
-    Bzz = FM1 - Bxx - Byy;
-  }
-  const long long o = (long long)y * g.pitch + x;
+      for (int q = 0; q < Q; ++q) {
+        const S *pl = tile + q * TL::TYB * TL::TXB + b0;
+        const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
+        const R c = load_h_s<S, R>(pl);
+        R acc = g.beta[q][0] * c;
+        if (sx != 0) {
+          R v = load_h_s<S, R>(pl - sx);
+          if (MASK && ((nb >> (4 - sx)) & 1u)) v = load_h_s<S, R>(tile + V::opp(q) * TL::TYB * TL::TXB + b0);
+          acc = fma(g.beta[q][1], v, acc);
+        }
+        if (sy != 0) {
+          R v = load_h_s<S, R>(pl - sy * TL::TXB);
+          if (MASK && ((nb >> (4 - 3 * sy)) & 1u)) v = load_h_s<S, R>(tile + V::opp(q) * TL::TYB * TL::TXB + b0);
+          acc = fma(g.beta[q][2], v, acc);
+        }
+        if (sx != 0 && sy != 0) {
+          R v = load_h_s<S, R>(pl - sy * TL::TXB - sx);
+          if (MASK && ((nb >> (4 - 3 * sy - sx)) & 1u)) v = load_h_s<S, R>(tile + V::opp(q) * TL::TYB * TL::TXB + b0);
+          acc = fma(g.beta[q][3], v, acc);
+        }
+        h[q] = acc;
+      }
+      const Mom<R> M = moments_of<R, R, VS, FORCE>(h);
+      const Macro<R> m = cell_macro<R, VS>(h, M, p.vmax2);
+      if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+      R Fx = p.body_x, Fy = p.body_y;
+      if (FORCE) {
+        for (int r = 0; r < st.nrows; ++r) {
+          const R4<R> G = st.G_cur[(long long)r * g.nx + x];
+          const R2<R> E = st.EY[(long long)r * g.ny + y];
+          Fx += G.x * E.x - G.y * E.y;
+          Fy += G.z * E.x - G.w * E.y;
+        }
+      }
+      const Coll<R> cf = coll_coeffs<R, VS, FORCE>(M, m, p.omega0, p.fpref, Fx, Fy);
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const R vx = R(V::vx(q)), vy = R(V::vy(q));
-    const R uv = m.ux * vx + m.uy * vy;
-    const R heq = cc + uv * (ca + cb * uv);
-    R hn = h[q] + omega * (m.u0 - uv) * (heq - h[q]);
-    if (VS == 3 && p.has_force) {
-      const R Fv = Fx * vx + Fy * vy;
-      const R vBv = vx * vx * Bxx + R(2) * vx * vy * Bxy + vy * vy * Byy + R(V::vz2(q)) * Bzz;
-      const R vM1 = vx * M.mx + vy * M.my;
-      hn += p.fpref * (R(0.25) * FM1 - R(0.5) * Fv * M0 + R(1.25) * vBv - R(2.5) * Fv * vM1);
+      for (int q = 0; q < Q; ++q) hn[q] = collide_class<R, VS, FORCE>(cf, q, h[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) hn[q] = R(0);
     }
-    fout[q * g.plane + o] = store_h<S, R>(hn);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) otile[(q * TILE_Y + ly) * TILE_X + lx] = store_h<S, R>(hn[q]);
+    // ghost copies of the periodic neighbours (boundary cells only)
+    if (inside) {
+      const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
+      const int gyv = g.walls ? INT_MIN : (y == 0 ? g.ny : (y == g.ny - 1 ? -1 : INT_MIN));
+      if (gxv != INT_MIN || gyv != INT_MIN) {
+        const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
+        for (int a = 0; a < 3; ++a) {
+          if (px[a] == INT_MIN || py[a] == INT_MIN) continue;
+          S *o = fout + (long long)(py[a] + 1) * g.pitch + px[a] + TL::XOFF;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) o[q * g.plane] = store_h<S, R>(hn[q]);
+        }
+      }
+    }
+    fence_proxy_async_smem();
+    if (tid == 0) bulk_wait_read_all();  // the store of the previous tile has read its buffer
+    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % TL::NST], ((k + 1) / TL::NST) & 1, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {  // also the barrier after which stage s and buffer k&1 are free
+      alive = false;
+      break;
+    }
+    if (tid == 0) {
+      tma_store_3d(&tout, otile, x0 + TL::XOFF, y0 + 1, 0);
+      bulk_commit();
+      if (k + TL::NST < my_tiles) issue(k + TL::NST);
+    }
   }
+  if (!alive) {
+    // a staged copy did not land in time: latch the error and wait (bounded) once more
+    // for this CTA's copies still in flight before returning
+    if (tid == 0) {
+      atomicOr(err, ERR_TIMEOUT);
+      for (int s2 = 0; s2 < TL::NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
+    }
+  }
+  if (tid == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
-// Moments of the current state f_n = stream(f*_n) (procedure item 3): eps, u^x, u^y
-// per cell and per-block FP64 partial sums of T^00, T^0x, T^0y, 1/2 |v|^2.  Landau
-// runs in FP64 here for every storage type.
+// Moments of the current state f_n = stream(f*_n) (procedure item 3) straight from
+// global memory (ghost-padded planes): eps, u^x, u^y per cell and per-block FP64
+// partial sums of T^00, T^0x, T^0y, 1/2 |v|^2.  Landau runs in FP64 here.
 // ---------------------------------------------------------------------------
+template <typename S, typename R, int VS, bool MASK>
+__device__ __forceinline__ void pull_global(const S *__restrict__ fin, const Geometry<R> &g, int x, int y,
+                                            unsigned nb, R h[VSet<VS>::Q]) {
+  constexpr int Q = VSet<VS>::Q;
+  const long long o = (long long)(y + 1) * g.pitch + x + PadLayout<S>::XOFF;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const S *pl = fin + q * g.plane + o;
+    const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
+    R acc = g.beta[q][0] * load_h<S, R>(pl);
+    const R own = load_h<S, R>(fin + VSet<VS>::opp(q) * g.plane + o);
+    if (sx != 0) acc += g.beta[q][1] * ((MASK && ((nb >> (4 - sx)) & 1u)) ? own : load_h<S, R>(pl - sx));
+    if (sy != 0) acc += g.beta[q][2] * ((MASK && ((nb >> (4 - 3 * sy)) & 1u)) ? own : load_h<S, R>(pl - (long long)sy * g.pitch));
+    if (sx != 0 && sy != 0)
+      acc += g.beta[q][3] * ((MASK && ((nb >> (4 - 3 * sy - sx)) & 1u)) ? own : load_h<S, R>(pl - (long long)sy * g.pitch - sx));
+    h[q] = acc;
+  }
+}
+
 template <typename S, int VS, bool MASK>
 __global__ void __launch_bounds__(256)
 moments_kernel(const S *__restrict__ fin, const Geometry<typename RealOf<S>::type> g, double eps0,
@@ -108,9 +226,9 @@ moments_kernel(const S *__restrict__ fin, const Geometry<typename RealOf<S>::typ
       eps[c] = 0.0; ux[c] = 0.0; uy[c] = 0.0;
     } else {
       R h[Q];
-      pull<S, R, VS, MASK>(fin, g, x, y, nb, h);
-      const Mom<double> M = moments_of<double, R, VS>(h);
-      const Macro<double> m = macro_from<double, VS>(M, 40, 1e-15);
+      pull_global<S, R, VS, MASK>(fin, g, x, y, nb, h);
+      const Mom<double> M = moments_of<double, R, VS, false>(h);
+      const Macro<double> m = macro_from<double, VS>(M, 40, 1e-12);
       if (!m.ok) atomicOr(err, (1.0 + m.eps_m1 > 0.0 && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
       eps[c] = eps0 * (1.0 + m.eps_m1);
       ux[c] = m.ux;
@@ -121,7 +239,6 @@ moments_kernel(const S *__restrict__ fin, const Geometry<typename RealOf<S>::typ
       acc[3] = 0.5 * (m.vx * m.vx + m.vy * m.vy);
     }
   }
-  // block reduction (warp shuffles, then one warp over the warp sums)
   __shared__ double red[4][32];
   const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
   const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
@@ -145,6 +262,7 @@ moments_kernel(const S *__restrict__ fin, const Geometry<typename RealOf<S>::typ
 
 // ---------------------------------------------------------------------------
 // Initial state f*_0 = f_eq(eps, u) (procedure item 1); NULL fields mean eps0 at rest.
+// Writes the interior; ghost copies come from fill_ghosts.
 // ---------------------------------------------------------------------------
 template <typename S, int VS>
 __global__ void init_kernel(S *__restrict__ fout, const Geometry<typename RealOf<S>::type> g, double eps0,
@@ -159,13 +277,32 @@ __global__ void init_kernel(S *__restrict__ fout, const Geometry<typename RealOf
   const double ax = ux ? ux[c] : 0.0, ay = uy ? uy[c] : 0.0;
   const double u2 = ax * ax + ay * ay, u0 = sqrt(1.0 + u2);
   const bool solid = g.nbmask && (g.nbmask[c] & 16u);
+  const long long o = (long long)(y + 1) * g.pitch + x + PadLayout<S>::XOFF;
 #pragma unroll
   for (int q = 0; q < V::Q; ++q) {
     const double uv = ax * V::vx(q) + ay * V::vy(q);
     const double heq = (e - 1.0) + V::CA * e * u0 * uv + V::CB * e * uv * uv - V::CC * e * u2;
-    fout[q * g.plane + (long long)y * g.pitch + x] = store_h<S, typename RealOf<S>::type>(
-        (typename RealOf<S>::type)(solid ? 0.0 : heq));
+    fout[q * g.plane + o] = store_h<S, typename RealOf<S>::type>((typename RealOf<S>::type)(solid ? 0.0 : heq));
   }
+}
+
+// Ghost columns (x = -1, nx) and, for periodic y, ghost rows (y = -1, ny) and corners:
+// copies of the wrapped interior.  With walls the ghost rows stay zero.
+template <typename S, int VS>
+__global__ void fill_ghosts_kernel(S *__restrict__ f, const Geometry<typename RealOf<S>::type> g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  const int nper = 2 * (g.ny + 2) + 2 * g.nx;
+  if (i >= nper) return;
+  int gx, gy;  // ghost coordinate in cell units (-1 .. nx, -1 .. ny)
+  if (i < 2 * (g.ny + 2)) { gx = (i & 1) ? g.nx : -1; gy = i / 2 - 1; }
+  else { const int j = i - 2 * (g.ny + 2); gx = j / 2; gy = (j & 1) ? g.ny : -1; }
+  S *pl = f + q * g.plane;
+  const long long dst = (long long)(gy + 1) * g.pitch + gx + PadLayout<S>::XOFF;
+  const bool yghost = gy < 0 || gy >= g.ny;
+  if (yghost && g.walls) { pl[dst] = store_h<S, typename RealOf<S>::type>(0); return; }
+  const int sx = (gx + g.nx) % g.nx, sy = (gy + g.ny) % g.ny;
+  pl[dst] = pl[(long long)(sy + 1) * g.pitch + sx + PadLayout<S>::XOFF];
 }
 
 // Stirring pipeline start at step n: coefficients of steps n and n+1, table of step n.
@@ -192,7 +329,7 @@ __global__ void stir_table_kernel(const Stir<R> st, R4<R> *G, const R4<R> *coef,
 // ---------------------------------------------------------------------------
 template <typename R> static Geometry<R> to_geom(const HostGeom &h) {
   Geometry<R> g;
-  g.nx = h.nx; g.ny = h.ny; g.pitch = h.pitch; g.plane = h.plane; g.nbmask = h.nbmask;
+  g.nx = h.nx; g.ny = h.ny; g.pitch = h.pitch; g.plane = h.plane; g.walls = h.walls; g.nbmask = h.nbmask;
   for (int q = 0; q < 17; ++q)
     for (int k = 0; k < 4; ++k) g.beta[q][k] = (R)h.beta[q][k];
   return g;
@@ -203,32 +340,60 @@ template <typename R> static Stir<R> to_stir(const HostStir &h) {
   s.nrows = h.nrows; s.nmodes = h.nmodes;
   s.G_cur = (const R4<R> *)h.G_cur; s.EY = (const R2<R> *)h.EY; s.G_next = (R4<R> *)h.G_next;
   s.coef_next = (const R4<R> *)h.coef_next; s.coef_new = (R4<R> *)h.coef_new;
-  s.mode_kx = h.mode_kx; s.mode_ky = h.mode_ky; s.row_start = h.row_start; s.EX = (const R2<R> *)h.EX;
+  s.mode_kx = h.mode_kx; s.row_start = h.row_start; s.EX = (const R2<R> *)h.EX;
   s.seed = h.seed; s.step_new = h.step_new; s.amp = h.amp;
   return s;
 }
 
+template <typename S, int VS, bool MASK, bool FORCE>
+static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tout, void *fout, const Geometry<typename RealOf<S>::type> &g,
+                                 const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &s,
+                                 unsigned *err, int grid_limit, cudaStream_t stream) {
+  using TL = Tile<S, VS>;
+  auto kern = step_kernel<S, VS, MASK, FORCE>;
+  static int configured_dev = -1, max_blocks = 0, sms = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, kern, NTHREADS, TL::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  const int ntiles = ((g.nx + TILE_X - 1) / TILE_X) * ((g.ny + TILE_Y - 1) / TILE_Y);
+  int grid = max_blocks * sms;
+  if (grid_limit > 0 && grid_limit < grid) grid = grid_limit;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  kern<<<grid, NTHREADS, TL::SMEM, stream>>>(tin, tout, (S *)fout, g, p, s, err);
+  return cudaGetLastError();
+}
+
 template <typename S>
-static cudaError_t launch_step_t(int vset, const void *fin, void *fout, const HostGeom &hg, const HostPhys &hp,
-                                 const HostStir &hs, unsigned *err, dim3 block, cudaStream_t stream) {
+static cudaError_t launch_step_t(int vset, const void *tin, const void *tout, void *fout, const HostGeom &hg,
+                                 const HostPhys &hp, const HostStir &hs, unsigned *err, int grid_limit,
+                                 cudaStream_t stream) {
   using R = typename RealOf<S>::type;
   const Geometry<R> g = to_geom<R>(hg);
   Physics<R> p;
   p.omega0 = (R)hp.omega0; p.fpref = (R)hp.fpref; p.body_x = (R)hp.body_x; p.body_y = (R)hp.body_y;
-  p.vmax2 = hp.vmax2; p.has_force = hp.has_force;
+  p.vmax2 = (R)hp.vmax2;
   const Stir<R> s = to_stir<R>(hs);
-  const dim3 grid((hg.nx + block.x - 1) / block.x, (hg.ny + block.y - 1) / block.y);
+  const CUtensorMap &mi = *(const CUtensorMap *)tin, &mo = *(const CUtensorMap *)tout;
   const bool mask = hg.nbmask != nullptr;
-  const S *a = (const S *)fin;
-  S *b = (S *)fout;
   if (vset == 3) {
-    if (mask) step_kernel<S, 3, true><<<grid, block, 0, stream>>>(a, b, g, p, s, err);
-    else step_kernel<S, 3, false><<<grid, block, 0, stream>>>(a, b, g, p, s, err);
-  } else {
-    if (mask) step_kernel<S, 2, true><<<grid, block, 0, stream>>>(a, b, g, p, s, err);
-    else step_kernel<S, 2, false><<<grid, block, 0, stream>>>(a, b, g, p, s, err);
+    if (hp.has_force) {
+      if (mask) return launch_step_v<S, 3, true, true>(mi, mo, fout, g, p, s, err, grid_limit, stream);
+      return launch_step_v<S, 3, false, true>(mi, mo, fout, g, p, s, err, grid_limit, stream);
+    }
+    if (mask) return launch_step_v<S, 3, true, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
+    return launch_step_v<S, 3, false, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
   }
-  return cudaGetLastError();
+  if (mask) return launch_step_v<S, 2, true, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
+  return launch_step_v<S, 2, false, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
 }
 
 template <typename S>
@@ -251,6 +416,17 @@ static cudaError_t launch_moments_t(int vset, const void *fin, const HostGeom &h
 }
 
 template <typename S>
+static cudaError_t launch_ghosts_t(int vset, void *f, const HostGeom &hg, cudaStream_t stream) {
+  using R = typename RealOf<S>::type;
+  const Geometry<R> g = to_geom<R>(hg);
+  const int nper = 2 * (hg.ny + 2) + 2 * hg.nx;
+  const dim3 grid((nper + 255) / 256, vset == 3 ? VSet<3>::Q : VSet<2>::Q);
+  if (vset == 3) fill_ghosts_kernel<S, 3><<<grid, 256, 0, stream>>>((S *)f, g);
+  else fill_ghosts_kernel<S, 2><<<grid, 256, 0, stream>>>((S *)f, g);
+  return cudaGetLastError();
+}
+
+template <typename S>
 static cudaError_t launch_init_t(int vset, void *fout, const HostGeom &hg, double eps0, const double *eps,
                                  const double *ux, const double *uy, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
@@ -259,7 +435,9 @@ static cudaError_t launch_init_t(int vset, void *fout, const HostGeom &hg, doubl
   const dim3 grid((hg.nx + 31) / 32, (hg.ny + 7) / 8);
   if (vset == 3) init_kernel<S, 3><<<grid, block, 0, stream>>>((S *)fout, g, eps0, eps, ux, uy);
   else init_kernel<S, 2><<<grid, block, 0, stream>>>((S *)fout, g, eps0, eps, ux, uy);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_ghosts_t<S>(vset, fout, hg, stream);
 }
 
 template <typename S>
@@ -278,27 +456,27 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
 
 }  // namespace rlbm
 
-#define RLBM_CAT2(a, b) a##b
-#define RLBM_CAT(a, b) RLBM_CAT2(a, b)
 #define RLBM_DEFINE_LAUNCHERS(S, SUF)                                                                    \
   namespace rlbm {                                                                                       \
-  cudaError_t RLBM_CAT(launch_step_, SUF)(int vset, const void *fin, void *fout, const HostGeom &g,     \
-                                          const HostPhys &p, const HostStir &s, unsigned *err, dim3 b,  \
-                                          cudaStream_t st) {                                             \
-    return launch_step_t<S>(vset, fin, fout, g, p, s, err, b, st);                                       \
+  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, void *fout, const HostGeom &g, \
+                                const HostPhys &p, const HostStir &s, unsigned *err, int grid_limit,    \
+                                cudaStream_t st) {                                                       \
+    return launch_step_t<S>(vset, tin, tout, fout, g, p, s, err, grid_limit, st);                       \
   }                                                                                                      \
-  cudaError_t RLBM_CAT(launch_moments_, SUF)(int vset, const void *fin, const HostGeom &g, double eps0, \
-                                             double *e, double *ux, double *uy, double *part,           \
-                                             unsigned *err, dim3 b, cudaStream_t st) {                   \
+  cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
+                                   double *ux, double *uy, double *part, unsigned *err, dim3 b,         \
+                                   cudaStream_t st) {                                                    \
     return launch_moments_t<S>(vset, fin, g, eps0, e, ux, uy, part, err, b, st);                         \
   }                                                                                                      \
-  cudaError_t RLBM_CAT(launch_init_, SUF)(int vset, void *fout, const HostGeom &g, double eps0,         \
-                                          const double *e, const double *ux, const double *uy,          \
-                                          cudaStream_t st) {                                             \
+  cudaError_t launch_init_##SUF(int vset, void *fout, const HostGeom &g, double eps0, const double *e,  \
+                                const double *ux, const double *uy, cudaStream_t st) {                   \
     return launch_init_t<S>(vset, fout, g, eps0, e, ux, uy, st);                                         \
   }                                                                                                      \
-  cudaError_t RLBM_CAT(launch_stir_prime_, SUF)(const HostStir &s, void *cn, void *cn1, void *G, int nx, \
-                                                long long n, cudaStream_t st) {                          \
+  cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st) {              \
+    return launch_ghosts_t<S>(vset, f, g, st);                                                           \
+  }                                                                                                      \
+  cudaError_t launch_stir_prime_##SUF(const HostStir &s, void *cn, void *cn1, void *G, int nx,          \
+                                      long long n, cudaStream_t st) {                                    \
     return launch_stir_prime_t<S>(s, cn, cn1, G, nx, n, st);                                             \
   }                                                                                                      \
   }

@@ -9,7 +9,8 @@ namespace rlbm {
 
 struct HostGeom {
   int nx, ny, pitch;
-  long long plane;
+  long long plane;         // elements per ghost-padded plane: pitch * (ny + 2)
+  int walls;
   const uint16_t *nbmask;  // device; NULL when the lattice has no solid cells or walls
   double beta[17][4];
 };
@@ -25,7 +26,7 @@ struct HostStir {
   void *G_next;
   const void *coef_next;
   void *coef_new;
-  const int *mode_kx, *mode_ky, *row_start;
+  const int *mode_kx, *row_start;
   const void *EX;
   unsigned long long seed;
   long long step_new;
@@ -33,9 +34,10 @@ struct HostStir {
 };
 
 #define RLBM_DECLARE_LAUNCHERS(SUF)                                                                      \
-  cudaError_t launch_step_##SUF(int vset, const void *fin, void *fout, const HostGeom &g,               \
-                                const HostPhys &p, const HostStir &s, unsigned *err, dim3 b,            \
+  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, void *fout, const HostGeom &g, \
+                                const HostPhys &p, const HostStir &s, unsigned *err, int grid_limit,    \
                                 cudaStream_t st);                                                        \
+  cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st);               \
   cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
                                    double *ux, double *uy, double *part, unsigned *err, dim3 b,         \
                                    cudaStream_t st);                                                     \
