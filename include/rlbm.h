@@ -132,6 +132,12 @@ RLBM_API rlbm_status rlbm_get_state(rlbm_ctx *ctx, double *host, int64_t *step);
 RLBM_API rlbm_status rlbm_set_state(rlbm_ctx *ctx, const double *host, int64_t step);
 RLBM_API int32_t rlbm_num_planes(const rlbm_ctx *ctx);
 
+/* Launch shape of the fused step kernel: the number of persistent CTAs that walk the
+ * lattice's 32 x 8 tiles (0 = as many as are resident at once, the default; values
+ * above that are clamped).  A tuning control of this implementation: results do not
+ * depend on it.  The paper has no counterpart. */
+RLBM_API rlbm_status rlbm_set_grid(rlbm_ctx *ctx, int32_t ctas);
+
 /* Wait for queued work and report latched device errors. */
 RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);
 

@@ -62,7 +62,7 @@ struct Layout {
   size_t pop[2], nbmask, err, EX, EY, G[2], coef[2], mode_kx, row_start;
   size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, total;
   long long plane;
-  int pitch, xoff, Q, nrows, nmodes, max_bins;
+  int pitch, xoff, Q, nrows, nmodes, max_bins, eyp;
   long long max_blocks;
 };
 
@@ -89,7 +89,8 @@ Layout make_layout(const rlbm_config &c) {
   L.nbmask = take((c.solid || c.walls_y) ? 2 * ncell : 0);
   L.err = take(16);
   L.EX = take(2 * rb * c.nx);
-  L.EY = take(2 * rb * (size_t)L.nrows * c.ny);
+  L.eyp = (c.ny + 7) / 8 * 8;  // EY rows padded to 8 entries (16-byte TMA strides)
+  L.EY = take(2 * rb * (size_t)L.nrows * L.eyp);
   L.G[0] = take(4 * rb * (size_t)L.nrows * c.nx);
   L.G[1] = take(4 * rb * (size_t)L.nrows * c.nx);
   L.coef[0] = take(4 * rb * L.nmodes);
@@ -176,7 +177,7 @@ struct rlbm_ctx {
   HostPhys phys;
   dim3 block{32, 8, 1};       // moments kernel
   int grid_limit = 0;          // step kernel: 0 = one wave of resident CTAs
-  CUtensorMap tmap_in[2], tmap_out[2];
+  CUtensorMap tmap_in[2], tmap_out[2], tmap_G[2], tmap_EY;
   std::vector<uint8_t> host_stage;
 
   template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
@@ -196,12 +197,13 @@ namespace {
 cudaError_t dispatch_step(rlbm_ctx *c, int src, const HostStir &s) {
   unsigned *err = c->at<unsigned>(c->L.err);
   const void *ti = &c->tmap_in[src], *to = &c->tmap_out[src ^ 1];
+  const void *tg = &c->tmap_G[c->step & 1], *te = &c->tmap_EY;
   void *fout = c->ws + c->L.pop[src ^ 1];
   switch (c->cfg.precision) {
-    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
-    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
-    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
-    default: return launch_step_bf16(c->cfg.vset, ti, to, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    default: return launch_step_bf16(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
   }
 }
 
@@ -254,6 +256,29 @@ std::string make_tensor_maps(rlbm_ctx *c) {
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (store map) failed with " + std::to_string((int)r);
   }
+  // stirring tables of a tile: G rows {4 nx} (one R4 per column) in boxes {4 * 32, nrows},
+  // EY rows {2 eyp} in boxes {2 * 8, nrows}; staged only for shells of <= 16 k_y rows
+  std::memset(c->tmap_G, 0, sizeof(c->tmap_G));
+  std::memset(&c->tmap_EY, 0, sizeof(c->tmap_EY));
+  if (c->L.nrows > 0 && c->L.nrows <= 16) {
+    const CUtensorMapDataType rt = prec == RLBM_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const size_t rb = real_bytes(prec);
+    const cuuint32_t e2[2] = {1, 1};
+    for (int b = 0; b < 2; ++b) {
+      const cuuint64_t dg[2] = {(cuuint64_t)4 * c->cfg.nx, (cuuint64_t)c->L.nrows};
+      const cuuint64_t sg[1] = {(cuuint64_t)4 * c->cfg.nx * rb};
+      const cuuint32_t bg[2] = {4 * 32, (cuuint32_t)c->L.nrows};
+      CUresult r = encode(&c->tmap_G[b], rt, 2, c->ws + c->L.G[b], dg, sg, bg, e2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (stirring table map) failed with " + std::to_string((int)r);
+    }
+    const cuuint64_t de[2] = {(cuuint64_t)2 * c->L.eyp, (cuuint64_t)c->L.nrows};
+    const cuuint64_t se[1] = {(cuuint64_t)2 * c->L.eyp * rb};
+    const cuuint32_t be[2] = {2 * 8, (cuuint32_t)c->L.nrows};
+    CUresult r = encode(&c->tmap_EY, rt, 2, c->ws + c->L.EY, de, se, be, e2, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (phase table map) failed with " + std::to_string((int)r);
+  }
   return "";
 }
 
@@ -295,6 +320,7 @@ HostStir stir_for_step(rlbm_ctx *c, int64_t n) {
   s.coef_next = c->ws + L.coef[(n + 1) & 1];
   s.coef_new = c->ws + L.coef[n & 1];
   s.EY = c->ws + L.EY;
+  s.eyp = L.eyp;
   s.EX = c->ws + L.EX;
   s.mode_kx = c->at<int>(L.mode_kx);
   s.row_start = c->at<int>(L.row_start);
@@ -479,7 +505,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   // stirring tables (library's own; FP64-built, stored in the compute type)
   if (L.nmodes) {
     const Modes m = shell_modes(cfg->kmin, cfg->kmax);
-    std::vector<double> ex_re(cfg->nx), ex_im(cfg->nx), ey_re((size_t)L.nrows * cfg->ny), ey_im((size_t)L.nrows * cfg->ny);
+    std::vector<double> ex_re(cfg->nx), ex_im(cfg->nx), ey_re((size_t)L.nrows * L.eyp, 0.0), ey_im((size_t)L.nrows * L.eyp, 0.0);
     for (int j = 0; j < cfg->nx; ++j) {
       ex_re[j] = std::cos(2.0 * M_PI * j / cfg->nx);
       ex_im[j] = std::sin(2.0 * M_PI * j / cfg->nx);
@@ -487,8 +513,8 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
     for (int r = 0; r < L.nrows; ++r)
       for (int y = 0; y < cfg->ny; ++y) {
         const long long j = ((long long)m.row_ky[r] * y) % cfg->ny;
-        ey_re[(size_t)r * cfg->ny + y] = std::cos(2.0 * M_PI * j / cfg->ny);
-        ey_im[(size_t)r * cfg->ny + y] = std::sin(2.0 * M_PI * j / cfg->ny);
+        ey_re[(size_t)r * L.eyp + y] = std::cos(2.0 * M_PI * j / cfg->ny);
+        ey_im[(size_t)r * L.eyp + y] = std::sin(2.0 * M_PI * j / cfg->ny);
       }
     keep.emplace_back();
     keep.emplace_back();
@@ -629,6 +655,13 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
 }
 
 int32_t rlbm_num_planes(const rlbm_ctx *c) { return c ? c->L.Q : -1; }
+
+rlbm_status rlbm_set_grid(rlbm_ctx *c, int32_t ctas) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (ctas < 0) return c->fail(RLBM_E_INVAL, "ctas must be >= 0");
+  c->grid_limit = ctas;
+  return RLBM_OK;
+}
 
 rlbm_status rlbm_sync(rlbm_ctx *c) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }

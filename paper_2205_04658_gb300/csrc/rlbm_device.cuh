@@ -142,7 +142,8 @@ template <typename R> struct Stir {
   int nrows;               // distinct k_y of the shell (0 = no stirring)
   int nmodes;
   const R4<R> *G_cur;      // [nrows][nx]: (Gx.re, Gx.im, Gy.re, Gy.im) of this step
-  const R2<R> *EY;         // [nrows][ny]: exp(i 2 pi k_y(row) y / ny)
+  const R2<R> *EY;         // [nrows][eyp]: exp(i 2 pi k_y(row) y / ny), rows padded to eyp
+  int eyp;
   // pipelined preparation of the next steps (done by the same launch)
   R4<R> *G_next;           // [nrows][nx] of step n+1
   const R4<R> *coef_next;  // [nmodes]: (cx.re, cx.im, cy.re, cy.im) of step n+1
@@ -203,19 +204,22 @@ __device__ inline R4<R> stir_row_entry(const Stir<R> &s, const R4<R> *coef, int 
   return g;
 }
 
-// Work a step launch does for the following steps (grid-stride over all threads of
-// the launch): the table of step n+1 and the Philox draws of step n+2.
+// Work a step launch does for the following steps: the table of step n+1 (grid-stride
+// over the threads t0, t0 + nthreads, ...) and the Philox draws of step n+2 (mode m by
+// thread 0 of the CTA of rank m, m + ncta, ...).
 template <typename R>
-__device__ inline void stir_prepare(const Stir<R> &s, long long t0, long long nthreads, int nx) {
+__device__ inline void stir_prepare(const Stir<R> &s, long long t0, long long nthreads, int rank, int tid,
+                                    int ncta, int nx) {
   if (s.nrows == 0) return;
   const long long entries = (long long)s.nrows * nx;
   for (long long t = t0; t < entries; t += nthreads)
     s.G_next[t] = stir_row_entry<R>(s, s.coef_next, (int)(t / nx), (int)(t % nx), nx);
-  for (long long t = t0; t < s.nmodes; t += nthreads) {
-    double c[4];
-    stir_draw(s.seed, s.step_new, (int)t, s.amp, c);
-    s.coef_new[t] = R4<R>{(R)c[0], (R)c[1], (R)c[2], (R)c[3]};
-  }
+  if (tid == 0)
+    for (int m = rank; m < s.nmodes; m += ncta) {
+      double c[4];
+      stir_draw(s.seed, s.step_new, m, s.amp, c);
+      s.coef_new[m] = R4<R>{(R)c[0], (R)c[1], (R)c[2], (R)c[3]};
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -466,6 +470,62 @@ __device__ __forceinline__ R collide_class(const Coll<R> &c, int q, R h) {
   if (vx != 0.0 || vy != 0.0) acc = fma(t, fma(t, fma(t, c.p3, c.p2), c.p1), acc);
   const R k = (vx != 0.0 || vy != 0.0) ? fma(c.om, t, c.k0) : c.k0;
   return fma(h, k, acc);
+}
+
+// All classes of a cell.  For the paper's set the classes of a sign group
+// {(+a,+b), (-a,+b), (-a,-b), (+a,-b)} share a u-projection pair (a u^x, b u^y) and the
+// even part of the force polynomial; only signs differ between the four members.
+template <typename R, bool FORCE>
+__device__ __forceinline__ void collide_group(const Coll<R> &c, double a, double b, double vz2, R h0, R h1, R h2,
+                                              R h3, R &o0, R &o1, R &o2, R &o3) {
+  const R A = c.ux * R(a), B = c.uy * R(b);
+  R even = c.s0, X = R(0), Y = R(0), XY = R(0);
+  if (FORCE) {
+    even = fma(c.sxx, R(a * a), even);
+    if (b != 0.0) even = fma(c.syy, R(b * b), even);
+    if (vz2 != 0.0) even = fma(c.szz, R(vz2), even);
+    X = c.s1x * R(a);
+    if (b != 0.0) { Y = c.s1y * R(b); XY = c.sxy2 * R(a * b); }
+  }
+  auto one = [&](R t, R force, R hq) {
+    const R acc = fma(t, fma(t, fma(t, c.p3, c.p2), c.p1), force);
+    return fma(hq, fma(c.om, t, c.k0), acc);
+  };
+  if (b != 0.0) {  // diagonal group: (+a,+b), (-a,+b), (-a,-b), (+a,-b)
+    const R e0 = even + XY, e1 = even - XY;
+    o0 = one(A + B, e0 + (X + Y), h0);
+    o1 = one(B - A, e1 + (Y - X), h1);
+    o2 = one(-(A + B), e0 - (X + Y), h2);
+    o3 = one(A - B, e1 + (X - Y), h3);
+  } else {  // axis group: (+a,0), (0,+a), (-a,0), (0,-a)
+    R evx = even, evy = c.s0;
+    R Yv = R(0);
+    if (FORCE) {
+      evy = fma(c.syy, R(a * a), c.s0);
+      if (vz2 != 0.0) evy = fma(c.szz, R(vz2), evy);
+      Yv = c.s1y * R(a);
+    }
+    const R By = c.uy * R(a);
+    o0 = one(A, evx + X, h0);
+    o1 = one(By, evy + Yv, h1);
+    o2 = one(-A, evx - X, h2);
+    o3 = one(-By, evy - Yv, h3);
+  }
+}
+
+template <typename R, int VS, bool FORCE>
+__device__ __forceinline__ void collide_all(const Coll<R> &c, const R h[VSet<VS>::Q], R hn[VSet<VS>::Q]) {
+  if constexpr (VS == 3) {
+    // class 0: v = (0, 0), v_z^2 = 1
+    hn[0] = fma(h[0], c.k0, FORCE ? fma(c.szz, R(1), c.s0) : c.s0);
+    collide_group<R, FORCE>(c, 1.0, 0.0, 0.0, h[1], h[2], h[3], h[4], hn[1], hn[2], hn[3], hn[4]);
+    collide_group<R, FORCE>(c, RLBM_S2, RLBM_S2, 0.0, h[5], h[6], h[7], h[8], hn[5], hn[6], hn[7], hn[8]);
+    collide_group<R, FORCE>(c, RLBM_S2, 0.0, 0.5, h[9], h[10], h[11], h[12], hn[9], hn[10], hn[11], hn[12]);
+    collide_group<R, FORCE>(c, RLBM_S3, RLBM_S3, 1.0 / 3.0, h[13], h[14], h[15], h[16], hn[13], hn[14], hn[15], hn[16]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < VSet<VS>::Q; ++q) hn[q] = collide_class<R, VS, FORCE>(c, q, h[q]);
+  }
 }
 
 }  // namespace rlbm

@@ -26,8 +26,19 @@ template <typename S, int VS> struct Tile {
   static constexpr int OUT_BYTES = OUT_ELEMS * (int)sizeof(S);
   static constexpr int IN_STRIDE = (IN_BYTES + 127) / 128 * 128;
   static constexpr int OUT_STRIDE = (OUT_BYTES + 127) / 128 * 128;
+  // stirring tables of the tile (rows <= MAX_SROWS): G[row][TILE_X] (R4), EY[row][TILE_Y] (R2)
+  using R = typename RealOf<S>::type;
+  static constexpr int MAX_SROWS = 16;
+  static constexpr int G_BYTES = MAX_SROWS * TILE_X * 4 * (int)sizeof(R);
+  static constexpr int EY_BYTES = MAX_SROWS * TILE_Y * 2 * (int)sizeof(R);
+  static constexpr int G_OFF = IN_STRIDE;              // TMA destinations are 128-byte aligned
+  static constexpr int EY_OFF = G_OFF + G_BYTES;
+  static constexpr int STAGE = (EY_OFF + EY_BYTES + 127) / 128 * 128;
   static constexpr int NST = 2;                      // input stages
-  static constexpr int SMEM = NST * IN_STRIDE + 2 * OUT_STRIDE + 64;
+  static constexpr int SMEM = NST * STAGE + 2 * OUT_STRIDE + 64 + 128;  // + base alignment slack
+  static_assert(G_OFF % 128 == 0 && EY_OFF % 128 == 0 && STAGE % 128 == 0 && OUT_STRIDE % 128 == 0,
+                "every TMA shared-memory destination and source must be 128-byte aligned");
+  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
 // ---------------------------------------------------------------------------
@@ -44,6 +55,7 @@ template <typename S, int VS> struct Tile {
 template <typename S, int VS, bool MASK, bool FORCE>
 __global__ void __launch_bounds__(NTHREADS)
 step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+            const __grid_constant__ CUtensorMap tG, const __grid_constant__ CUtensorMap tEY,
             S *__restrict__ fout, const Geometry<typename RealOf<S>::type> g,
             const Physics<typename RealOf<S>::type> p, const Stir<typename RealOf<S>::type> st,
             unsigned *__restrict__ err) {
@@ -51,34 +63,45 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
   using V = VSet<VS>;
   using TL = Tile<S, VS>;
   constexpr int Q = V::Q;
-  extern __shared__ __align__(128) unsigned char smem[];
-  S *sin = reinterpret_cast<S *>(smem);
-  S *sout = reinterpret_cast<S *>(smem + TL::NST * TL::IN_STRIDE);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TL::NST * TL::IN_STRIDE + 2 * TL::OUT_STRIDE);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // every TMA box lands on a 128-byte boundary of this aligned base
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned char *stage0 = smem;
+  S *sout = reinterpret_cast<S *>(smem + TL::NST * TL::STAGE);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TL::NST * TL::STAGE + 2 * TL::OUT_STRIDE);
 
   const int tid = threadIdx.x;
   const int lx = tid % TILE_X, ly = tid / TILE_X;
   const int ntx = (g.nx + TILE_X - 1) / TILE_X, nty = (g.ny + TILE_Y - 1) / TILE_Y;
   const int ntiles = ntx * nty;
   const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // tile k of this CTA is blockIdx.x + k * gridDim.x; its (x, y) tile coordinates advance
+  // by (gridDim.x mod ntx, gridDim.x div ntx) with a carry
+  const int stx = gridDim.x % ntx, sty = gridDim.x / ntx;
+  const bool staged = FORCE && st.nrows > 0 && st.nrows <= TL::MAX_SROWS;
+  const uint32_t stage_bytes = TL::IN_BYTES + (staged ? st.nrows * (TILE_X * 4 + TILE_Y * 2) * (int)sizeof(R) : 0);
 
   if (tid == 0) {
     for (int s = 0; s < TL::NST; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
   }
   __syncthreads();
+  int itx = blockIdx.x % ntx, ity = blockIdx.x / ntx;  // next tile to stage (thread 0)
   auto issue = [&](int k) {  // stage the k-th tile of this CTA into stage k % NST
-    const int t = blockIdx.x + k * gridDim.x;
-    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    const int x0 = itx * TILE_X, y0 = ity * TILE_Y;
+    unsigned char *st0 = stage0 + (k % TL::NST) * TL::STAGE;
     uint64_t *b = &bar[k % TL::NST];
-    mbar_expect_tx(b, TL::IN_BYTES);
-    tma_load_3d(sin + (k % TL::NST) * (TL::IN_STRIDE / (int)sizeof(S)), &tin, b, x0 + TL::XOFF - TL::V, y0, 0);
+    mbar_expect_tx(b, stage_bytes);
+    tma_load_3d(st0, &tin, b, x0 + TL::XOFF - TL::V, y0, 0);
+    if (staged) {
+      tma_load_2d(st0 + TL::G_OFF, &tG, b, 4 * x0, 0);
+      tma_load_2d(st0 + TL::EY_OFF, &tEY, b, 2 * y0, 0);
+    }
+    itx += stx; ity += sty;
+    if (itx >= ntx) { itx -= ntx; ++ity; }
   };
   if (tid == 0)
     for (int k = 0; k < TL::NST && k < my_tiles; ++k) issue(k);
-
-  // preparation of the stirring table of step n+1 and the draws of step n+2
-  stir_prepare<R>(st, (long long)blockIdx.x * NTHREADS + tid, (long long)gridDim.x * NTHREADS, g.nx);
 
   // Every thread waits for the staged tile (bounded); the vote in the barrier makes the
   // whole CTA wind down together if a copy never lands.
@@ -87,12 +110,15 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
     const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
     if (__syncthreads_or(!ok)) alive = false;
   }
+  int ctx_ = blockIdx.x % ntx, cty = blockIdx.x / ntx;  // tile being computed
   for (int k = 0; alive && k < my_tiles; ++k) {
-    const int t = blockIdx.x + k * gridDim.x;
-    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    const int x0 = ctx_ * TILE_X, y0 = cty * TILE_Y;
+    ctx_ += stx; cty += sty;
+    if (ctx_ >= ntx) { ctx_ -= ntx; ++cty; }
     const int x = x0 + lx, y = y0 + ly;
     const int s = k % TL::NST;
-    const S *tile = sin + s * (TL::IN_STRIDE / (int)sizeof(S));
+    const unsigned char *stg = stage0 + s * TL::STAGE;
+    const S *tile = reinterpret_cast<const S *>(stg);
     S *otile = sout + (k & 1) * (TL::OUT_STRIDE / (int)sizeof(S));
     const bool inside = x < g.nx && y < g.ny;
     unsigned nb = 0;
@@ -131,16 +157,40 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
       if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
       R Fx = p.body_x, Fy = p.body_y;
       if (FORCE) {
-        for (int r = 0; r < st.nrows; ++r) {
-          const R4<R> G = st.G_cur[(long long)r * g.nx + x];
-          const R2<R> E = st.EY[(long long)r * g.ny + y];
-          Fx += G.x * E.x - G.y * E.y;
-          Fy += G.z * E.x - G.w * E.y;
+        if (staged) {
+          const R4<R> *Gs = reinterpret_cast<const R4<R> *>(stg + TL::G_OFF) + lx;
+          const R2<R> *Es = reinterpret_cast<const R2<R> *>(stg + TL::EY_OFF) + ly;
+          // F = sum_r Re[G_r(x) EY_r(y)], two rows per iteration
+          R Fx2 = R(0), Fy2 = R(0);
+          int r = 0;
+#pragma unroll 1
+          for (; r + 1 < st.nrows; r += 2) {
+            const R4<R> G0 = Gs[r * TILE_X], G1 = Gs[(r + 1) * TILE_X];
+            const R2<R> E0 = Es[r * TILE_Y], E1 = Es[(r + 1) * TILE_Y];
+            Fx = fma(G0.x, E0.x, fma(-G0.y, E0.y, Fx));
+            Fy = fma(G0.z, E0.x, fma(-G0.w, E0.y, Fy));
+            Fx2 = fma(G1.x, E1.x, fma(-G1.y, E1.y, Fx2));
+            Fy2 = fma(G1.z, E1.x, fma(-G1.w, E1.y, Fy2));
+          }
+          if (r < st.nrows) {
+            const R4<R> G0 = Gs[r * TILE_X];
+            const R2<R> E0 = Es[r * TILE_Y];
+            Fx = fma(G0.x, E0.x, fma(-G0.y, E0.y, Fx));
+            Fy = fma(G0.z, E0.x, fma(-G0.w, E0.y, Fy));
+          }
+          Fx += Fx2;
+          Fy += Fy2;
+        } else {
+          for (int r = 0; r < st.nrows; ++r) {
+            const R4<R> G = st.G_cur[(long long)r * g.nx + x];
+            const R2<R> E = st.EY[(long long)r * st.eyp + y];
+            Fx += G.x * E.x - G.y * E.y;
+            Fy += G.z * E.x - G.w * E.y;
+          }
         }
       }
       const Coll<R> cf = coll_coeffs<R, VS, FORCE>(M, m, p.omega0, p.fpref, Fx, Fy);
-#pragma unroll
-      for (int q = 0; q < Q; ++q) hn[q] = collide_class<R, VS, FORCE>(cf, q, h[q]);
+      collide_all<R, VS, FORCE>(cf, h, hn);
     } else {
 #pragma unroll
       for (int q = 0; q < Q; ++q) hn[q] = R(0);
@@ -174,6 +224,10 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
       if (k + TL::NST < my_tiles) issue(k + TL::NST);
     }
   }
+  // Preparation of the stirring table of step n+1 and the draws of step n+2, by the
+  // CTAs with the fewest tiles first (reverse order).
+  stir_prepare<R>(st, (long long)(gridDim.x - 1 - blockIdx.x) * NTHREADS + tid, (long long)gridDim.x * NTHREADS,
+                  gridDim.x - 1 - blockIdx.x, tid, gridDim.x, g.nx);
   if (!alive) {
     // a staged copy did not land in time: latch the error and wait (bounded) once more
     // for this CTA's copies still in flight before returning
@@ -340,13 +394,14 @@ template <typename R> static Stir<R> to_stir(const HostStir &h) {
   s.nrows = h.nrows; s.nmodes = h.nmodes;
   s.G_cur = (const R4<R> *)h.G_cur; s.EY = (const R2<R> *)h.EY; s.G_next = (R4<R> *)h.G_next;
   s.coef_next = (const R4<R> *)h.coef_next; s.coef_new = (R4<R> *)h.coef_new;
-  s.mode_kx = h.mode_kx; s.row_start = h.row_start; s.EX = (const R2<R> *)h.EX;
+  s.mode_kx = h.mode_kx; s.row_start = h.row_start; s.EX = (const R2<R> *)h.EX; s.eyp = h.eyp;
   s.seed = h.seed; s.step_new = h.step_new; s.amp = h.amp;
   return s;
 }
 
 template <typename S, int VS, bool MASK, bool FORCE>
-static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tout, void *fout, const Geometry<typename RealOf<S>::type> &g,
+static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tout, const CUtensorMap &tG,
+                                 const CUtensorMap &tEY, void *fout, const Geometry<typename RealOf<S>::type> &g,
                                  const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &s,
                                  unsigned *err, int grid_limit, cudaStream_t stream) {
   using TL = Tile<S, VS>;
@@ -368,12 +423,13 @@ static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tout
   if (grid_limit > 0 && grid_limit < grid) grid = grid_limit;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
-  kern<<<grid, NTHREADS, TL::SMEM, stream>>>(tin, tout, (S *)fout, g, p, s, err);
+  kern<<<grid, NTHREADS, TL::SMEM, stream>>>(tin, tout, tG, tEY, (S *)fout, g, p, s, err);
   return cudaGetLastError();
 }
 
 template <typename S>
-static cudaError_t launch_step_t(int vset, const void *tin, const void *tout, void *fout, const HostGeom &hg,
+static cudaError_t launch_step_t(int vset, const void *tin, const void *tout, const void *tg, const void *tey,
+                                 void *fout, const HostGeom &hg,
                                  const HostPhys &hp, const HostStir &hs, unsigned *err, int grid_limit,
                                  cudaStream_t stream) {
   using R = typename RealOf<S>::type;
@@ -383,17 +439,18 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tout, vo
   p.vmax2 = (R)hp.vmax2;
   const Stir<R> s = to_stir<R>(hs);
   const CUtensorMap &mi = *(const CUtensorMap *)tin, &mo = *(const CUtensorMap *)tout;
+  const CUtensorMap &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
   const bool mask = hg.nbmask != nullptr;
   if (vset == 3) {
     if (hp.has_force) {
-      if (mask) return launch_step_v<S, 3, true, true>(mi, mo, fout, g, p, s, err, grid_limit, stream);
-      return launch_step_v<S, 3, false, true>(mi, mo, fout, g, p, s, err, grid_limit, stream);
+      if (mask) return launch_step_v<S, 3, true, true>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
+      return launch_step_v<S, 3, false, true>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
     }
-    if (mask) return launch_step_v<S, 3, true, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
-    return launch_step_v<S, 3, false, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
+    if (mask) return launch_step_v<S, 3, true, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
+    return launch_step_v<S, 3, false, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
   }
-  if (mask) return launch_step_v<S, 2, true, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
-  return launch_step_v<S, 2, false, false>(mi, mo, fout, g, p, s, err, grid_limit, stream);
+  if (mask) return launch_step_v<S, 2, true, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
+  return launch_step_v<S, 2, false, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
 }
 
 template <typename S>
@@ -458,10 +515,10 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
 
 #define RLBM_DEFINE_LAUNCHERS(S, SUF)                                                                    \
   namespace rlbm {                                                                                       \
-  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, void *fout, const HostGeom &g, \
-                                const HostPhys &p, const HostStir &s, unsigned *err, int grid_limit,    \
-                                cudaStream_t st) {                                                       \
-    return launch_step_t<S>(vset, tin, tout, fout, g, p, s, err, grid_limit, st);                       \
+  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, const void *tg,             \
+                                const void *tey, void *fout, const HostGeom &g, const HostPhys &p,      \
+                                const HostStir &s, unsigned *err, int grid_limit, cudaStream_t st) {    \
+    return launch_step_t<S>(vset, tin, tout, tg, tey, fout, g, p, s, err, grid_limit, st);              \
   }                                                                                                      \
   cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
                                    double *ux, double *uy, double *part, unsigned *err, dim3 b,         \

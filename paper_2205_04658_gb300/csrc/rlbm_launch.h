@@ -23,6 +23,7 @@ struct HostPhys {
 struct HostStir {
   int nrows, nmodes;
   const void *G_cur, *EY;
+  int eyp;
   void *G_next;
   const void *coef_next;
   void *coef_new;
@@ -34,9 +35,9 @@ struct HostStir {
 };
 
 #define RLBM_DECLARE_LAUNCHERS(SUF)                                                                      \
-  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, void *fout, const HostGeom &g, \
-                                const HostPhys &p, const HostStir &s, unsigned *err, int grid_limit,    \
-                                cudaStream_t st);                                                        \
+  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, const void *tg,             \
+                                const void *tey, void *fout, const HostGeom &g, const HostPhys &p,      \
+                                const HostStir &s, unsigned *err, int grid_limit, cudaStream_t st);     \
   cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st);               \
   cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
                                    double *ux, double *uy, double *part, unsigned *err, dim3 b,         \

@@ -59,6 +59,7 @@ def lib():
             "rlbm_get_state": (c_i32, [P, dp, ctypes.POINTER(c_i64)]),
             "rlbm_set_state": (c_i32, [P, dp, c_i64]),
             "rlbm_num_planes": (c_i32, [P]),
+            "rlbm_set_grid": (c_i32, [P, c_i32]),
             "rlbm_sync": (c_i32, [P]),
             "rlbm_current_step": (c_i64, [P]),
             "rlbm_last_error": (ctypes.c_char_p, [P]),
@@ -150,6 +151,10 @@ def rlbm_num_planes(ctx):
     return lib().rlbm_num_planes(ctx)
 
 
+def rlbm_set_grid(ctx, ctas):
+    _check(lib().rlbm_set_grid(ctx, int(ctas)), ctx)
+
+
 def rlbm_sync(ctx):
     _check(lib().rlbm_sync(ctx), ctx)
 
@@ -216,6 +221,9 @@ class Lattice:
     @property
     def current_step(self):
         return rlbm_current_step(self.ctx)
+
+    def set_grid(self, ctas):
+        rlbm_set_grid(self.ctx, ctas)
 
     def sync(self):
         rlbm_sync(self.ctx)
