@@ -132,11 +132,19 @@ RLBM_API rlbm_status rlbm_get_state(rlbm_ctx *ctx, double *host, int64_t *step);
 RLBM_API rlbm_status rlbm_set_state(rlbm_ctx *ctx, const double *host, int64_t step);
 RLBM_API int32_t rlbm_num_planes(const rlbm_ctx *ctx);
 
-/* Launch shape of the fused step kernel: the number of persistent CTAs that walk the
- * lattice's 32 x 8 tiles (0 = as many as are resident at once, the default; values
- * above that are clamped).  A tuning control of this implementation: results do not
- * depend on it.  The paper has no counterpart. */
-RLBM_API rlbm_status rlbm_set_grid(rlbm_ctx *ctx, int32_t ctas);
+/* Launch shape of the fused step kernel: `ctas` persistent CTAs walk the lattice's
+ * 32 x 8 tiles (0 = as many as are resident at once, the default; larger values are
+ * clamped) and `stages` (1 or 2; 0 keeps the current value) tiles of shared memory rotate
+ * in its TMA pipeline (default 2).  A tuning control: results do not depend on it.
+ * The paper has no counterpart. */
+RLBM_API rlbm_status rlbm_set_launch(rlbm_ctx *ctx, int32_t ctas, int32_t stages);
+
+/* Autotuner: times every launch shape it knows (pipeline depth x CTA count), `reps`
+ * launches each, on the current state, and keeps the fastest.  The state and the step
+ * counter are left as they were (the launches rewrite the next buffer only).  *ms_out
+ * (may be NULL) receives the chosen shape's time per step in milliseconds.  Syncs.
+ * The paper has no counterpart. */
+RLBM_API rlbm_status rlbm_autotune(rlbm_ctx *ctx, int32_t reps, double *ms_out);
 
 /* Wait for queued work and report latched device errors. */
 RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);

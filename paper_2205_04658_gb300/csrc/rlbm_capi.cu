@@ -59,7 +59,7 @@ Modes shell_modes(int kmin, int kmax) {
 bool stirring_on(const rlbm_config &c) { return c.force_amp != 0.0; }
 
 struct Layout {
-  size_t pop[2], nbmask, err, EX, EY, G[2], coef[2], mode_kx, row_start;
+  size_t pop[2], nbmask, err, EY, G[2], coef[2], mode_kx, row_start;
   size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, total;
   long long plane;
   int pitch, xoff, Q, nrows, nmodes, max_bins, eyp;
@@ -88,7 +88,6 @@ Layout make_layout(const rlbm_config &c) {
   L.pop[1] = take(sb * L.Q * L.plane);
   L.nbmask = take((c.solid || c.walls_y) ? 2 * ncell : 0);
   L.err = take(16);
-  L.EX = take(2 * rb * c.nx);
   L.eyp = (c.ny + 7) / 8 * 8;  // EY rows padded to 8 entries (16-byte TMA strides)
   L.EY = take(2 * rb * (size_t)L.nrows * L.eyp);
   L.G[0] = take(4 * rb * (size_t)L.nrows * c.nx);
@@ -177,7 +176,8 @@ struct rlbm_ctx {
   HostPhys phys;
   dim3 block{32, 8, 1};       // moments kernel
   int grid_limit = 0;          // step kernel: 0 = one wave of resident CTAs
-  CUtensorMap tmap_in[2], tmap_out[2], tmap_G[2], tmap_EY;
+  int stages = 2;              // shared-memory pipeline depth of the step kernel (1 or 2)
+  CUtensorMap tmap_in[2], tmap_G[2], tmap_EY;
   std::vector<uint8_t> host_stage;
 
   template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
@@ -196,14 +196,14 @@ namespace {
 
 cudaError_t dispatch_step(rlbm_ctx *c, int src, const HostStir &s) {
   unsigned *err = c->at<unsigned>(c->L.err);
-  const void *ti = &c->tmap_in[src], *to = &c->tmap_out[src ^ 1];
+  const void *ti = &c->tmap_in[src];
   const void *tg = &c->tmap_G[c->step & 1], *te = &c->tmap_EY;
   void *fout = c->ws + c->L.pop[src ^ 1];
   switch (c->cfg.precision) {
-    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
-    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
-    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
-    default: return launch_step_bf16(c->cfg.vset, ti, to, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stream);
+    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
+    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
+    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
+    default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
   }
 }
 
@@ -217,10 +217,9 @@ cudaError_t dispatch_ghosts(rlbm_ctx *c, int b) {
   }
 }
 
-// Tensor maps of one population buffer: loads see the whole ghost-padded planes,
-// {pitch, ny + 2, Q}, in boxes of {32 + 2 V, 10, Q} (a 32 x 8 tile with its halo,
-// V = 16 bytes of elements); stores are clipped at the last interior column and row,
-// {xoff + nx, ny + 1, Q}, in boxes of {32, 8, Q}.
+// Tensor maps of one population buffer: the whole ghost-padded planes, {pitch, ny + 2,
+// Q}, read in boxes of {32 + 2 V, 10, Q} (a 32 x 8 tile with its halo, V = 16 bytes of
+// elements).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -250,11 +249,6 @@ std::string make_tensor_maps(rlbm_ctx *c) {
     CUresult r = encode(&c->tmap_in[b], dt, 3, base, din, strides, bin, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (load map) failed with " + std::to_string((int)r);
-    const cuuint64_t dout[3] = {(cuuint64_t)(c->L.xoff + c->cfg.nx), (cuuint64_t)c->cfg.ny + 1, (cuuint64_t)c->L.Q};
-    const cuuint32_t bout[3] = {32, 8, (cuuint32_t)c->L.Q};
-    r = encode(&c->tmap_out[b], dt, 3, base, dout, strides, bout, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (store map) failed with " + std::to_string((int)r);
   }
   // stirring tables of a tile: G rows {4 nx} (one R4 per column) in boxes {4 * 32, nrows},
   // EY rows {2 eyp} in boxes {2 * 8, nrows}; staged only for shells of <= 16 k_y rows
@@ -321,7 +315,6 @@ HostStir stir_for_step(rlbm_ctx *c, int64_t n) {
   s.coef_new = c->ws + L.coef[n & 1];
   s.EY = c->ws + L.EY;
   s.eyp = L.eyp;
-  s.EX = c->ws + L.EX;
   s.mode_kx = c->at<int>(L.mode_kx);
   s.row_start = c->at<int>(L.row_start);
   s.seed = c->cfg.seed;
@@ -505,11 +498,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   // stirring tables (library's own; FP64-built, stored in the compute type)
   if (L.nmodes) {
     const Modes m = shell_modes(cfg->kmin, cfg->kmax);
-    std::vector<double> ex_re(cfg->nx), ex_im(cfg->nx), ey_re((size_t)L.nrows * L.eyp, 0.0), ey_im((size_t)L.nrows * L.eyp, 0.0);
-    for (int j = 0; j < cfg->nx; ++j) {
-      ex_re[j] = std::cos(2.0 * M_PI * j / cfg->nx);
-      ex_im[j] = std::sin(2.0 * M_PI * j / cfg->nx);
-    }
+    std::vector<double> ey_re((size_t)L.nrows * L.eyp, 0.0), ey_im((size_t)L.nrows * L.eyp, 0.0);
     for (int r = 0; r < L.nrows; ++r)
       for (int y = 0; y < cfg->ny; ++y) {
         const long long j = ((long long)m.row_ky[r] * y) % cfg->ny;
@@ -517,11 +506,9 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
         ey_im[(size_t)r * L.eyp + y] = std::sin(2.0 * M_PI * j / cfg->ny);
       }
     keep.emplace_back();
-    keep.emplace_back();
-    if (cfg->precision == RLBM_F64) { put_pairs<double>(keep[keep.size() - 2], ex_re, ex_im); put_pairs<double>(keep.back(), ey_re, ey_im); }
-    else { put_pairs<float>(keep[keep.size() - 2], ex_re, ex_im); put_pairs<float>(keep.back(), ey_re, ey_im); }
-    if ((e = put(L.EX, keep[keep.size() - 2].data(), keep[keep.size() - 2].size())) != cudaSuccess ||
-        (e = put(L.EY, keep.back().data(), keep.back().size())) != cudaSuccess ||
+    if (cfg->precision == RLBM_F64) put_pairs<double>(keep.back(), ey_re, ey_im);
+    else put_pairs<float>(keep.back(), ey_re, ey_im);
+    if ((e = put(L.EY, keep.back().data(), keep.back().size())) != cudaSuccess ||
         (e = put(L.mode_kx, m.kx.data(), 4 * m.kx.size())) != cudaSuccess ||
         (e = put(L.row_start, m.row_start.data(), 4 * m.row_start.size())) != cudaSuccess) {
       c->cuda_fail(e, "upload of the stirring tables");
@@ -656,11 +643,54 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
 
 int32_t rlbm_num_planes(const rlbm_ctx *c) { return c ? c->L.Q : -1; }
 
-rlbm_status rlbm_set_grid(rlbm_ctx *c, int32_t ctas) {
+rlbm_status rlbm_set_launch(rlbm_ctx *c, int32_t ctas, int32_t stages) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
-  if (ctas < 0) return c->fail(RLBM_E_INVAL, "ctas must be >= 0");
+  if (ctas < 0 || stages < 0 || stages > 2) return c->fail(RLBM_E_INVAL, "ctas must be >= 0 and stages 0, 1 or 2");
   c->grid_limit = ctas;
+  if (stages) c->stages = stages;
   return RLBM_OK;
+}
+
+rlbm_status rlbm_autotune(rlbm_ctx *c, int32_t reps, double *ms_out) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (reps < 1) return c->fail(RLBM_E_INVAL, "reps must be >= 1");
+  Scoped dev(c->device);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  // candidate launch shapes: pipeline depth x persistent CTA count (0 = all resident)
+  const int stage_opts[2] = {2, 1};
+  const int grid_opts[4] = {0, 2 * sms, 3 * sms, 4 * sms};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return c->fail(RLBM_E_CUDA, "cudaEventCreate failed");
+  const int save_grid = c->grid_limit, save_stages = c->stages;
+  float best = 1e30f;
+  int best_grid = save_grid, best_stages = save_stages;
+  const HostStir st = stir_for_step(c, c->step);
+  cudaError_t e = cudaSuccess;
+  for (int si = 0; si < 2 && e == cudaSuccess; ++si)
+    for (int gi = 0; gi < 4 && e == cudaSuccess; ++gi) {
+      c->stages = stage_opts[si];
+      c->grid_limit = grid_opts[gi];
+      // the step kernel reads the current buffer and writes the other one; repeating it
+      // leaves the state (and the step counter) as it was
+      if ((e = dispatch_step(c, c->cur, st)) != cudaSuccess) break;  // warm-up
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch_step(c, c->cur, st);
+      cudaEventRecord(e1, c->stream);
+      if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_grid = c->grid_limit; best_stages = c->stages; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->grid_limit = best_grid;
+  c->stages = best_stages;
+  if (e != cudaSuccess) { c->grid_limit = save_grid; c->stages = save_stages; return c->cuda_fail(e, "autotune launch"); }
+  if (ms_out) *ms_out = best / reps;
+  return check_device(c);
 }
 
 rlbm_status rlbm_sync(rlbm_ctx *c) {

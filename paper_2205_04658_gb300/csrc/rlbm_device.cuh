@@ -17,6 +17,10 @@
 
 namespace rlbm {
 
+// keep the scalar math overloads visible next to the packed-pair ones defined below
+using ::fma;
+using ::fmax;
+
 enum : unsigned { ERR_UNSTABLE = 1u, ERR_UNPHYSICAL = 2u, ERR_TIMEOUT = 4u };
 
 // ---------------------------------------------------------------------------
@@ -150,7 +154,6 @@ template <typename R> struct Stir {
   R4<R> *coef_new;         // [nmodes] of step n+2 (written)
   const int *mode_kx;      // [nmodes]
   const int *row_start;    // [nrows+1] mode range of each row (modes sorted by k_y)
-  const R2<R> *EX;         // [nx]: exp(i 2 pi j / nx)
   unsigned long long seed;
   long long step_new;      // n + 2
   double amp;
@@ -186,40 +189,95 @@ __device__ inline void stir_draw(unsigned long long seed, long long n, int m, do
   out[2] = a * spsi * cphi; out[3] = a * spsi * sphi;
 }
 
+// exp(i pi a) for the stirring phases: FP64 in the FP64 path, FP32 (about 1 ulp) in the
+// others.
+template <typename R> __device__ __forceinline__ void sincospi_R(R a, R *s, R *c);
+template <> __device__ __forceinline__ void sincospi_R<double>(double a, double *s, double *c) { sincospi(a, s, c); }
+template <> __device__ __forceinline__ void sincospi_R<float>(float a, float *s, float *c) { sincospif(a, s, c); }
+
 // One entry of the per-row stirring table of a step:
-//   G_r(x) = sum_{m in row r} (cx_m, cy_m) exp(i 2 pi k_x,m x / nx).
+//   G_r(x) = sum_{m in row r} (cx_m, cy_m) exp(i 2 pi k_x,m x / nx),
+// the phase evaluated from the exact integer residue k_x,m x mod nx.  `coef`, `kx` and
+// `row_start` may live in shared memory.
 template <typename R>
-__device__ inline R4<R> stir_row_entry(const Stir<R> &s, const R4<R> *coef, int r, int x, int nx) {
+__device__ inline R4<R> stir_row_entry(const R4<R> *coef, const int *kx, const int *row_start, int r, int x, int nx) {
   R4<R> g{R(0), R(0), R(0), R(0)};
-  for (int m = s.row_start[r]; m < s.row_start[r + 1]; ++m) {
-    long long j = ((long long)s.mode_kx[m] * x) % nx;
+  const int m1 = row_start[r + 1];
+  for (int m = row_start[r]; m < m1; ++m) {
+    int j = (kx[m] * x) % nx;  // |k_x| < nx / 2 and x < nx <= 32768: no 32-bit overflow
     if (j < 0) j += nx;
-    const R2<R> e = s.EX[j];
+    R sn, cs;
+    sincospi_R<R>(R(2 * j) / R(nx), &sn, &cs);
     const R4<R> c = coef[m];
-    g.x += c.x * e.x - c.y * e.y;
-    g.y += c.x * e.y + c.y * e.x;
-    g.z += c.z * e.x - c.w * e.y;
-    g.w += c.z * e.y + c.w * e.x;
+    g.x += c.x * cs - c.y * sn;
+    g.y += c.x * sn + c.y * cs;
+    g.z += c.z * cs - c.w * sn;
+    g.w += c.z * sn + c.w * cs;
   }
   return g;
 }
 
-// Work a step launch does for the following steps: the table of step n+1 (grid-stride
-// over the threads t0, t0 + nthreads, ...) and the Philox draws of step n+2 (mode m by
-// thread 0 of the CTA of rank m, m + ncta, ...).
 template <typename R>
-__device__ inline void stir_prepare(const Stir<R> &s, long long t0, long long nthreads, int rank, int tid,
-                                    int ncta, int nx) {
+__device__ inline R4<R> stir_row_entry(const Stir<R> &s, const R4<R> *coef, int r, int x, int nx) {
+  return stir_row_entry<R>(coef, s.mode_kx, s.row_start, r, x, nx);
+}
+
+// The table of step n+1 by `ncta` CTAs of a launch (this one has rank `rank`), with the
+// mode coefficients, k_x and row ranges first copied to shared memory `sm` when they fit
+// in `sm_bytes`.  Entry e goes to CTA e mod ncta, thread (e div ncta) mod nthr.
+template <typename R>
+__device__ inline void stir_table_part(const Stir<R> &s, int rank, int ncta, int tid, int nthr, int nx,
+                                       unsigned char *sm, int sm_bytes) {
   if (s.nrows == 0) return;
+  const R4<R> *coef = s.coef_next;
+  const int *kx = s.mode_kx, *rs = s.row_start;
+  const int need = s.nmodes * (int)(sizeof(R4<R>) + sizeof(int)) + (s.nrows + 1) * (int)sizeof(int);
+  if (sm && need <= sm_bytes) {
+    R4<R> *c2 = reinterpret_cast<R4<R> *>(sm);
+    int *k2 = reinterpret_cast<int *>(c2 + s.nmodes);
+    int *r2 = k2 + s.nmodes;
+    for (int i = tid; i < s.nmodes; i += nthr) { c2[i] = coef[i]; k2[i] = kx[i]; }
+    for (int i = tid; i <= s.nrows; i += nthr) r2[i] = rs[i];
+    __syncthreads();
+    coef = c2; kx = k2; rs = r2;
+  }
   const long long entries = (long long)s.nrows * nx;
-  for (long long t = t0; t < entries; t += nthreads)
-    s.G_next[t] = stir_row_entry<R>(s, s.coef_next, (int)(t / nx), (int)(t % nx), nx);
-  if (tid == 0)
-    for (int m = rank; m < s.nmodes; m += ncta) {
+  for (long long e = rank + (long long)ncta * tid; e < entries; e += (long long)ncta * nthr)
+    s.G_next[e] = stir_row_entry<R>(coef, kx, rs, (int)(e / nx), (int)(e % nx), nx);
+}
+
+// Mode m of step n in FP32 (the draws of the FP32-compute paths; the uniform u_j and
+// the Box-Muller transform in single precision, about 1e-7 relative).
+__device__ inline void stir_draw_f32(unsigned long long seed, long long n, int m, float amp, float out[4]) {
+  uint32_t c[4] = {(uint32_t)(n & 0xffffffffll), (uint32_t)m, (uint32_t)((unsigned long long)n >> 32), 0u};
+  philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+  float u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) u[j] = ((float)c[j] + 0.5f) * 2.3283064365386962890625e-10f;
+  const float a = amp * sqrtf(-2.0f * logf(u[0])) * cospif(2.0f * u[1]);
+  float sphi, cphi, spsi, cpsi;
+  sincospif(2.0f * u[2], &sphi, &cphi);
+  sincospif(2.0f * u[3], &spsi, &cpsi);
+  out[0] = a * cpsi * cphi; out[1] = a * cpsi * sphi;
+  out[2] = a * spsi * cphi; out[3] = a * spsi * sphi;
+}
+
+// Philox draws of step n+2: mode m by one thread of the CTA of rank m, m + ncta, ...
+// (FP64 arithmetic in the FP64 path, FP32 in the others: GB300's FP64 rate is 1/64 of
+// FP32, and the draws sit on the critical path of the CTAs that make them).
+template <typename R>
+__device__ inline void stir_draws_part(const Stir<R> &s, int rank, int ncta) {
+  for (int m = rank; m < s.nmodes; m += ncta) {
+    if constexpr (sizeof(R) == 8) {
       double c[4];
       stir_draw(s.seed, s.step_new, m, s.amp, c);
       s.coef_new[m] = R4<R>{(R)c[0], (R)c[1], (R)c[2], (R)c[3]};
+    } else {
+      float c[4];
+      stir_draw_f32(s.seed, s.step_new, m, (float)s.amp, c);
+      s.coef_new[m] = R4<R>{c[0], c[1], c[2], c[3]};
     }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -239,6 +297,32 @@ template <> struct FM<float> {
   static __device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
   static __device__ __forceinline__ float qroot(float x) { return rsqrtf(rsqrtf(x)); }
   static __device__ __forceinline__ float croot(float x) { return cbrtf(x); }
+};
+
+// Two FP32 lanes (two lattice cells) in one register pair: Blackwell's packed FP32
+// add/multiply/FMA (__fadd2_rn, __fmul2_rn, __ffma2_rn) do both in one instruction.
+struct F2 {
+  float2 v;
+  __device__ __forceinline__ F2() : v(make_float2(0.0f, 0.0f)) {}
+  __device__ __forceinline__ explicit F2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ explicit F2(double s) : v(make_float2((float)s, (float)s)) {}
+  __device__ __forceinline__ explicit F2(int s) : v(make_float2((float)s, (float)s)) {}
+  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ explicit F2(float2 w) : v(w) {}
+  __device__ __forceinline__ F2 &operator+=(F2 o) { v = __fadd2_rn(v, o.v); return *this; }
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)); }
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2 fmax(F2 a, F2 b) { return F2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+template <> struct FM<F2> {
+  static __device__ __forceinline__ F2 rcp(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+  static __device__ __forceinline__ F2 rsqrt(F2 x) { return F2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
+  static __device__ __forceinline__ F2 sqrt_(F2 x) { return F2(FM<float>::sqrt_(x.v.x), FM<float>::sqrt_(x.v.y)); }
+  static __device__ __forceinline__ F2 qroot(F2 x) { return F2(FM<float>::qroot(x.v.x), FM<float>::qroot(x.v.y)); }
+  static __device__ __forceinline__ F2 croot(F2 x) { return F2(cbrtf(x.v.x), cbrtf(x.v.y)); }
 };
 
 // ---------------------------------------------------------------------------
@@ -399,6 +483,68 @@ __device__ __forceinline__ Macro<R> cell_macro(const R h[VSet<VS>::Q], const Mom
     }
     return m;
   }
+}
+
+// Landau matching of two cells at once (the Newton steps of `landau` on both lanes, until
+// both have converged); a lane that has not converged, or whose |v|^2 exceeds vmax2, is
+// re-solved in FP64 from the same populations.
+template <int VS>
+__device__ __forceinline__ Macro<F2> cell_macro_pair(const F2 h[VSet<VS>::Q], const Mom<F2> &M, float vmax2) {
+  constexpr float dinv = 1.0f / VSet<VS>::DP;
+  const float tol = 3e-4f;
+  const F2 one(1.0f);
+  const F2 T00 = one + M.e;
+  const F2 i00 = FM<F2>::rcp(T00);
+  const F2 ax = M.mx * i00, ay = M.my * i00, m2 = fma(ax, ax, ay * ay);
+  F2 c;
+  if (VS == 3) c = F2(3.0f) * FM<F2>::rcp(F2(2.0f) + FM<F2>::sqrt_(fmax(fma(F2(-3.0f), m2, F2(4.0f)), F2(0.0f))));
+  else c = F2(4.0f) * FM<F2>::rcp(F2(3.0f) + FM<F2>::sqrt_(fmax(fma(F2(-8.0f), m2, F2(9.0f)), F2(0.0f))));
+  F2 vx = c * ax, vy = c * ay;
+  const F2 Txx = F2(dinv) + M.txx, Txy = M.txy, Tyy = F2(dinv) + M.tyy;
+  bool convA = false, convB = false;
+  for (int it = 0; it < 4; ++it) {
+    const F2 E = T00 - fma(M.mx, vx, M.my * vy);
+    const F2 rx = M.mx - fma(Txx, vx, Txy * vy) - E * vx;
+    const F2 ry = M.my - fma(Txy, vx, Tyy * vy) - E * vy;
+    const F2 jxx = fma(vx, M.mx, -Txx) - E, jxy = fma(vx, M.my, -Txy);
+    const F2 jyx = fma(vy, M.mx, -Txy), jyy = fma(vy, M.my, -Tyy) - E;
+    const F2 idet = FM<F2>::rcp(jxx * jyy - jxy * jyx);
+    const F2 dx = (jxy * ry - jyy * rx) * idet;
+    const F2 dy = (jyx * rx - jxx * ry) * idet;
+    vx += dx;
+    vy += dy;
+    const F2 d2 = fma(dx, dx, dy * dy), lim = F2(tol * tol) * (F2(1e-6f) + fma(vx, vx, vy * vy));
+    convA = d2.v.x <= lim.v.x;
+    convB = d2.v.y <= lim.v.y;
+    if (convA && convB) break;
+  }
+  const F2 v2 = fma(vx, vx, vy * vy);
+  const F2 E = T00 - fma(M.mx, vx, M.my * vy);
+  const bool okA = convA && v2.v.x < vmax2 && E.v.x > 0.0f, okB = convB && v2.v.y < vmax2 && E.v.y > 0.0f;
+  Macro<F2> r;
+  const F2 gam = FM<F2>::rsqrt(one - v2);
+  r.eps_m1 = M.e - fma(M.mx, vx, M.my * vy);
+  r.u0 = gam; r.ux = gam * vx; r.uy = gam * vy; r.vx = vx; r.vy = vy;
+  r.ok = true;
+  if (!okA || !okB) {
+    for (int lane = 0; lane < 2; ++lane) {
+      if (lane == 0 ? okA : okB) continue;
+      float hl[VSet<VS>::Q];
+#pragma unroll
+      for (int q = 0; q < VSet<VS>::Q; ++q) hl[q] = lane == 0 ? h[q].v.x : h[q].v.y;
+      const Mom<double> Md = moments_of<double, float, VS, false>(hl);
+      const Macro<double> d = macro_from<double, VS>(Md, 40, 1e-12);
+      float *dst[6] = {lane ? &r.eps_m1.v.y : &r.eps_m1.v.x, lane ? &r.u0.v.y : &r.u0.v.x,
+                       lane ? &r.ux.v.y : &r.ux.v.x, lane ? &r.uy.v.y : &r.uy.v.x,
+                       lane ? &r.vx.v.y : &r.vx.v.x, lane ? &r.vy.v.y : &r.vy.v.x};
+      *dst[0] = (float)d.eps_m1; *dst[1] = (float)d.u0; *dst[2] = (float)d.ux;
+      *dst[3] = (float)d.uy; *dst[4] = (float)d.vx; *dst[5] = (float)d.vy;
+      r.ok = r.ok && d.ok;
+    }
+  }
+  r.ok = r.ok && isfinite(r.eps_m1.v.x) && isfinite(r.eps_m1.v.y) && (1.0f + r.eps_m1.v.x > 0.0f) &&
+         (1.0f + r.eps_m1.v.y > 0.0f);
+  return r;
 }
 
 // ---------------------------------------------------------------------------

@@ -8,6 +8,7 @@
 #include "rlbm_tma.cuh"
 
 #include <climits>
+#include <type_traits>
 
 namespace rlbm {
 
@@ -20,106 +21,34 @@ template <typename S, int VS> struct Tile {
   static constexpr int XOFF = PadLayout<S>::XOFF;
   static constexpr int TXB = TILE_X + 2 * V;         // staged columns (16-byte granules on both sides)
   static constexpr int TYB = TILE_Y + 2;             // staged rows (one halo row each side)
-  static constexpr int IN_ELEMS = Q * TYB * TXB;
-  static constexpr int OUT_ELEMS = Q * TILE_Y * TILE_X;
-  static constexpr int IN_BYTES = IN_ELEMS * (int)sizeof(S);
-  static constexpr int OUT_BYTES = OUT_ELEMS * (int)sizeof(S);
+  static constexpr int IN_BYTES = Q * TYB * TXB * (int)sizeof(S);
   static constexpr int IN_STRIDE = (IN_BYTES + 127) / 128 * 128;
-  static constexpr int OUT_STRIDE = (OUT_BYTES + 127) / 128 * 128;
-  // stirring tables of the tile (rows <= MAX_SROWS): G[row][TILE_X] (R4), EY[row][TILE_Y] (R2)
+  // stirring tables of the tile (at most MAX_SROWS k_y rows): G[row][TILE_X] (R4) and
+  // EY[row][TILE_Y] (R2) after the populations; their size follows the shell at run time
   using R = typename RealOf<S>::type;
   static constexpr int MAX_SROWS = 16;
-  static constexpr int G_BYTES = MAX_SROWS * TILE_X * 4 * (int)sizeof(R);
-  static constexpr int EY_BYTES = MAX_SROWS * TILE_Y * 2 * (int)sizeof(R);
-  static constexpr int G_OFF = IN_STRIDE;              // TMA destinations are 128-byte aligned
-  static constexpr int EY_OFF = G_OFF + G_BYTES;
-  static constexpr int STAGE = (EY_OFF + EY_BYTES + 127) / 128 * 128;
-  static constexpr int NST = 2;                      // input stages
-  static constexpr int SMEM = NST * STAGE + 2 * OUT_STRIDE + 64 + 128;  // + base alignment slack
-  static_assert(G_OFF % 128 == 0 && EY_OFF % 128 == 0 && STAGE % 128 == 0 && OUT_STRIDE % 128 == 0,
-                "every TMA shared-memory destination and source must be 128-byte aligned");
-  static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+  static constexpr int G_ROW = TILE_X * 4 * (int)sizeof(R);
+  static constexpr int EY_ROW = TILE_Y * 2 * (int)sizeof(R);
+  static_assert(IN_STRIDE % 128 == 0 && G_ROW % 128 == 0, "TMA shared-memory destinations are 128-byte aligned");
+  __host__ __device__ static constexpr int g_bytes(int rows) { return (rows * G_ROW + 127) / 128 * 128; }
+  __host__ __device__ static constexpr int ey_bytes(int rows) { return (rows * EY_ROW + 127) / 128 * 128; }
+  __host__ __device__ static constexpr int stage(int rows) { return IN_STRIDE + g_bytes(rows) + ey_bytes(rows); }
+  __host__ __device__ static constexpr int smem(int nst, int rows) { return nst * stage(rows) + 64 + 128; }
 };
 
-// ---------------------------------------------------------------------------
-// The fused step (procedure items 2-5 of Sec. "The Standard/Classical LBM", with the
-// driving term of Sec. "The Driving Term").  Persistent CTAs walk the 32 x 8 tiles of
-// the lattice.  Per tile, one 3-D TMA copy stages all Q planes of the tile plus a
-// one-cell halo (ghost rows/columns carry the periodic wrap) into shared memory,
-// double-buffered on mbarriers; each thread pull-streams its cell from shared memory
-// (bilinear weights, bounce-back substitution from the mask), takes the moments,
-// Landau-matches, relaxes and adds the force, writes the Q results into a shared
-// output tile that one TMA store writes back, and refreshes the ghost copies of
-// boundary cells with plain stores.
-// ---------------------------------------------------------------------------
-template <typename S, int VS, bool MASK, bool FORCE>
-__global__ void __launch_bounds__(NTHREADS)
-step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
-            const __grid_constant__ CUtensorMap tG, const __grid_constant__ CUtensorMap tEY,
-            S *__restrict__ fout, const Geometry<typename RealOf<S>::type> g,
-            const Physics<typename RealOf<S>::type> p, const Stir<typename RealOf<S>::type> st,
-            unsigned *__restrict__ err) {
+// One cell per thread (256 threads): the FP64 path.
+template <typename S, int VS, bool MASK, bool FORCE, int CPT>
+__device__ __forceinline__ typename std::enable_if<CPT == 1>::type
+tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid,
+           const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,
+           const Stir<typename RealOf<S>::type> &st, bool staged, unsigned *err) {
   using R = typename RealOf<S>::type;
   using V = VSet<VS>;
   using TL = Tile<S, VS>;
   constexpr int Q = V::Q;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  // every TMA box lands on a 128-byte boundary of this aligned base
-  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned char *stage0 = smem;
-  S *sout = reinterpret_cast<S *>(smem + TL::NST * TL::STAGE);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TL::NST * TL::STAGE + 2 * TL::OUT_STRIDE);
-
-  const int tid = threadIdx.x;
-  const int lx = tid % TILE_X, ly = tid / TILE_X;
-  const int ntx = (g.nx + TILE_X - 1) / TILE_X, nty = (g.ny + TILE_Y - 1) / TILE_Y;
-  const int ntiles = ntx * nty;
-  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  // tile k of this CTA is blockIdx.x + k * gridDim.x; its (x, y) tile coordinates advance
-  // by (gridDim.x mod ntx, gridDim.x div ntx) with a carry
-  const int stx = gridDim.x % ntx, sty = gridDim.x / ntx;
-  const bool staged = FORCE && st.nrows > 0 && st.nrows <= TL::MAX_SROWS;
-  const uint32_t stage_bytes = TL::IN_BYTES + (staged ? st.nrows * (TILE_X * 4 + TILE_Y * 2) * (int)sizeof(R) : 0);
-
-  if (tid == 0) {
-    for (int s = 0; s < TL::NST; ++s) mbar_init(&bar[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  int itx = blockIdx.x % ntx, ity = blockIdx.x / ntx;  // next tile to stage (thread 0)
-  auto issue = [&](int k) {  // stage the k-th tile of this CTA into stage k % NST
-    const int x0 = itx * TILE_X, y0 = ity * TILE_Y;
-    unsigned char *st0 = stage0 + (k % TL::NST) * TL::STAGE;
-    uint64_t *b = &bar[k % TL::NST];
-    mbar_expect_tx(b, stage_bytes);
-    tma_load_3d(st0, &tin, b, x0 + TL::XOFF - TL::V, y0, 0);
-    if (staged) {
-      tma_load_2d(st0 + TL::G_OFF, &tG, b, 4 * x0, 0);
-      tma_load_2d(st0 + TL::EY_OFF, &tEY, b, 2 * y0, 0);
-    }
-    itx += stx; ity += sty;
-    if (itx >= ntx) { itx -= ntx; ++ity; }
-  };
-  if (tid == 0)
-    for (int k = 0; k < TL::NST && k < my_tiles; ++k) issue(k);
-
-  // Every thread waits for the staged tile (bounded); the vote in the barrier makes the
-  // whole CTA wind down together if a copy never lands.
-  bool alive = true;
-  {
-    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
-    if (__syncthreads_or(!ok)) alive = false;
-  }
-  int ctx_ = blockIdx.x % ntx, cty = blockIdx.x / ntx;  // tile being computed
-  for (int k = 0; alive && k < my_tiles; ++k) {
-    const int x0 = ctx_ * TILE_X, y0 = cty * TILE_Y;
-    ctx_ += stx; cty += sty;
-    if (ctx_ >= ntx) { ctx_ -= ntx; ++cty; }
+    const int lx = tid % TILE_X, ly = tid / TILE_X;
     const int x = x0 + lx, y = y0 + ly;
-    const int s = k % TL::NST;
-    const unsigned char *stg = stage0 + s * TL::STAGE;
     const S *tile = reinterpret_cast<const S *>(stg);
-    S *otile = sout + (k & 1) * (TL::OUT_STRIDE / (int)sizeof(S));
     const bool inside = x < g.nx && y < g.ny;
     unsigned nb = 0;
     if (MASK && inside) nb = g.nbmask[(long long)y * g.nx + x];
@@ -158,8 +87,8 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
       R Fx = p.body_x, Fy = p.body_y;
       if (FORCE) {
         if (staged) {
-          const R4<R> *Gs = reinterpret_cast<const R4<R> *>(stg + TL::G_OFF) + lx;
-          const R2<R> *Es = reinterpret_cast<const R2<R> *>(stg + TL::EY_OFF) + ly;
+          const R4<R> *Gs = reinterpret_cast<const R4<R> *>(stg + TL::IN_STRIDE) + lx;
+          const R2<R> *Es = reinterpret_cast<const R2<R> *>(stg + ey_off) + ly;
           // F = sum_r Re[G_r(x) EY_r(y)], two rows per iteration
           R Fx2 = R(0), Fy2 = R(0);
           int r = 0;
@@ -195,8 +124,11 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
 #pragma unroll
       for (int q = 0; q < Q; ++q) hn[q] = R(0);
     }
+    if (inside) {  // coalesced stores straight from registers (one 128-byte line per warp and plane)
+      S *o = fout + (long long)(y + 1) * g.pitch + x + TL::XOFF;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) otile[(q * TILE_Y + ly) * TILE_X + lx] = store_h<S, R>(hn[q]);
+      for (int q = 0; q < Q; ++q) o[q * g.plane] = store_h<S, R>(hn[q]);
+    }
     // ghost copies of the periodic neighbours (boundary cells only)
     if (inside) {
       const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
@@ -211,32 +143,222 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
         }
       }
     }
-    fence_proxy_async_smem();
-    if (tid == 0) bulk_wait_read_all();  // the store of the previous tile has read its buffer
-    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % TL::NST], ((k + 1) / TL::NST) & 1, WAIT_CYCLES);
-    if (__syncthreads_or(!ok)) {  // also the barrier after which stage s and buffer k&1 are free
+}
+
+// Two cells per thread (128 threads): cells (x, y) and (x, y + 4) of the 32 x 8 tile, all
+// per-cell arithmetic on packed FP32 pairs.  The FP32, FP16 and BF16 paths.
+template <typename S, int VS, bool MASK, bool FORCE, int CPT>
+__device__ __forceinline__ typename std::enable_if<CPT == 2>::type
+tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid,
+           const Geometry<float> &g, const Physics<float> &p, const Stir<float> &st, bool staged,
+           unsigned *err) {
+  using V = VSet<VS>;
+  using TL = Tile<S, VS>;
+  using T = F2;
+  constexpr int Q = V::Q;
+  constexpr int DB = (TILE_Y / 2) * TL::TXB;  // smem offset of the second cell
+  const int lx = tid % TILE_X, ly = tid / TILE_X;
+  const int x = x0 + lx, yA = y0 + ly, yB = yA + TILE_Y / 2;
+  const S *tile = reinterpret_cast<const S *>(stg);
+  const bool inA = x < g.nx && yA < g.ny, inB = x < g.nx && yB < g.ny;
+  unsigned nbA = 0, nbB = 0;
+  if (MASK) {
+    if (inA) nbA = g.nbmask[(long long)yA * g.nx + x];
+    if (inB) nbB = g.nbmask[(long long)yB * g.nx + x];
+  }
+  const bool flA = inA && !(MASK && (nbA & 16u)), flB = inB && !(MASK && (nbB & 16u));
+  T hn[Q];
+  if (flA || flB) {
+    const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
+    T h[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const S *pl = tile + q * TL::TYB * TL::TXB + b0;
+      const S *own = tile + V::opp(q) * TL::TYB * TL::TXB + b0;
+      const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
+      T acc = T(g.beta[q][0]) * T(load_h_s<S, float>(pl), load_h_s<S, float>(pl + DB));
+      if (sx != 0) {
+        float vA = load_h_s<S, float>(pl - sx), vB = load_h_s<S, float>(pl + DB - sx);
+        if (MASK && ((nbA >> (4 - sx)) & 1u)) vA = load_h_s<S, float>(own);
+        if (MASK && ((nbB >> (4 - sx)) & 1u)) vB = load_h_s<S, float>(own + DB);
+        acc = fma(T(g.beta[q][1]), T(vA, vB), acc);
+      }
+      if (sy != 0) {
+        float vA = load_h_s<S, float>(pl - sy * TL::TXB), vB = load_h_s<S, float>(pl + DB - sy * TL::TXB);
+        if (MASK && ((nbA >> (4 - 3 * sy)) & 1u)) vA = load_h_s<S, float>(own);
+        if (MASK && ((nbB >> (4 - 3 * sy)) & 1u)) vB = load_h_s<S, float>(own + DB);
+        acc = fma(T(g.beta[q][2]), T(vA, vB), acc);
+      }
+      if (sx != 0 && sy != 0) {
+        float vA = load_h_s<S, float>(pl - sy * TL::TXB - sx), vB = load_h_s<S, float>(pl + DB - sy * TL::TXB - sx);
+        if (MASK && ((nbA >> (4 - 3 * sy - sx)) & 1u)) vA = load_h_s<S, float>(own);
+        if (MASK && ((nbB >> (4 - 3 * sy - sx)) & 1u)) vB = load_h_s<S, float>(own + DB);
+        acc = fma(T(g.beta[q][3]), T(vA, vB), acc);
+      }
+      // a lane without fluid (outside the lattice or solid) computes the rest state
+      h[q] = T(flA ? acc.v.x : 0.0f, flB ? acc.v.y : 0.0f);
+    }
+    const Mom<T> M = moments_of<T, T, VS, FORCE>(h);
+    const Macro<T> m = cell_macro_pair<VS>(h, M, p.vmax2);
+    if (!m.ok) atomicOr(err, (isfinite(m.eps_m1.v.x) && isfinite(m.eps_m1.v.y)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+    T Fx(p.body_x), Fy(p.body_y);
+    if (FORCE) {
+      if (staged) {
+        const R4<float> *Gs = reinterpret_cast<const R4<float> *>(stg + TL::IN_STRIDE) + lx;
+        const R2<float> *Es = reinterpret_cast<const R2<float> *>(stg + ey_off) + ly;
+#pragma unroll 1
+        for (int r = 0; r < st.nrows; ++r) {
+          const R4<float> G = Gs[r * TILE_X];
+          const R2<float> EA = Es[r * TILE_Y], EB = Es[r * TILE_Y + TILE_Y / 2];
+          const T Ere(EA.x, EB.x), Eim(EA.y, EB.y);
+          Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
+          Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
+        }
+      } else {
+        for (int r = 0; r < st.nrows; ++r) {
+          const R4<float> G = st.G_cur[(long long)r * g.nx + x];
+          const R2<float> EA = st.EY[(long long)r * st.eyp + yA];
+          const R2<float> EB = st.EY[(long long)r * st.eyp + (yB < g.ny ? yB : yA)];
+          const T Ere(EA.x, EB.x), Eim(EA.y, EB.y);
+          Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
+          Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
+        }
+      }
+    }
+    const Coll<T> cf = coll_coeffs<T, VS, FORCE>(M, m, T(p.omega0), T(p.fpref), Fx, Fy);
+    collide_all<T, VS, FORCE>(cf, h, hn);
+  }
+  {  // coalesced stores straight from registers (one 128-byte line per warp and plane)
+    S *oA = fout + (long long)(yA + 1) * g.pitch + x + TL::XOFF;
+    S *oB = oA + (long long)(TILE_Y / 2) * g.pitch;
+    if (inA) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) oA[q * g.plane] = store_h<S, float>(flA ? hn[q].v.x : 0.0f);
+    }
+    if (inB) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) oB[q * g.plane] = store_h<S, float>(flB ? hn[q].v.y : 0.0f);
+    }
+  }
+  // ghost copies of the periodic neighbours (boundary cells only)
+#pragma unroll
+  for (int lane = 0; lane < 2; ++lane) {
+    const int y = lane ? yB : yA;
+    if (!(lane ? inB : inA)) continue;
+    const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
+    const int gyv = g.walls ? INT_MIN : (y == 0 ? g.ny : (y == g.ny - 1 ? -1 : INT_MIN));
+    if (gxv == INT_MIN && gyv == INT_MIN) continue;
+    const bool fl = lane ? flB : flA;
+    const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
+    for (int a = 0; a < 3; ++a) {
+      if (px[a] == INT_MIN || py[a] == INT_MIN) continue;
+      S *o = fout + (long long)(py[a] + 1) * g.pitch + px[a] + TL::XOFF;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) o[q * g.plane] = store_h<S, float>(fl ? (lane ? hn[q].v.y : hn[q].v.x) : 0.0f);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The fused step (procedure items 2-5 of Sec. "The Standard/Classical LBM", with the
+// driving term of Sec. "The Driving Term").  Persistent CTAs walk the 32 x 8 tiles of
+// the lattice.  Per tile, one 3-D TMA copy stages all Q planes of the tile plus a
+// one-cell halo (ghost rows/columns carry the periodic wrap) into shared memory, with
+// the tile's stirring rows; NST stages rotate on mbarriers (NST = 2: the next tile is
+// in flight while this one is computed; NST = 1: more CTAs per SM hide the copy
+// instead).  Each thread pull-streams its cell(s) from shared memory (bilinear
+// weights, bounce-back substitution from the mask), takes the moments, Landau-matches,
+// relaxes, adds the force and stores the Q results with coalesced stores, refreshing
+// the ghost copies of boundary cells.
+// ---------------------------------------------------------------------------
+template <typename S, int VS, bool MASK, bool FORCE, int CPT, int NST>
+__global__ void __launch_bounds__(NTHREADS / CPT)
+step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tG,
+            const __grid_constant__ CUtensorMap tEY, S *__restrict__ fout,
+            const Geometry<typename RealOf<S>::type> g, const Physics<typename RealOf<S>::type> p,
+            const Stir<typename RealOf<S>::type> st, int prep_bytes, unsigned *__restrict__ err) {
+  using R = typename RealOf<S>::type;
+  using TL = Tile<S, VS>;
+  constexpr int NT = NTHREADS / CPT;
+  const int wid = blockIdx.x, nworkers = gridDim.x;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // every TMA box lands on a 128-byte boundary of this aligned base
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const bool staged = FORCE && st.nrows > 0 && st.nrows <= TL::MAX_SROWS;
+  const int srows = staged ? st.nrows : 0;
+  const int stage_stride = TL::stage(srows), ey_off = TL::IN_STRIDE + TL::g_bytes(srows);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * stage_stride);
+
+  const int tid = threadIdx.x;
+  const int ntx = (g.nx + TILE_X - 1) / TILE_X, nty = (g.ny + TILE_Y - 1) / TILE_Y;
+  const int ntiles = ntx * nty;
+  const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
+  // tile k of this CTA is wid + k * nworkers; its (x, y) tile coordinates advance by
+  // (nworkers mod ntx, nworkers div ntx) with a carry
+  const int stx = nworkers % ntx, sty = nworkers / ntx;
+  const uint32_t stage_bytes = TL::IN_BYTES + srows * (TL::G_ROW + TL::EY_ROW);
+
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int itx = wid % ntx, ity = wid / ntx;  // next tile to stage (thread 0)
+  auto issue = [&](int k) {  // stage the k-th tile of this CTA into stage k % NST
+    const int x0 = itx * TILE_X, y0 = ity * TILE_Y;
+    unsigned char *st0 = smem + (k % NST) * stage_stride;
+    uint64_t *b = &bar[k % NST];
+    mbar_expect_tx(b, stage_bytes);
+    tma_load_3d(st0, &tin, b, x0 + TL::XOFF - TL::V, y0, 0);
+    if (staged) {
+      tma_load_2d(st0 + TL::IN_STRIDE, &tG, b, 4 * x0, 0);
+      tma_load_2d(st0 + ey_off, &tEY, b, 2 * y0, 0);
+    }
+    itx += stx; ity += sty;
+    if (itx >= ntx) { itx -= ntx; ++ity; }
+  };
+  if (tid == 0)
+    for (int k = 0; k < NST && k < my_tiles; ++k) issue(k);
+
+  // While the first tiles are in flight: this CTA's share of the stirring table of step
+  // n+1 (mode data staged in shared memory past the barriers) and, for the CTAs of
+  // highest index, one Philox draw of step n+2.
+  if (FORCE && st.nrows) {
+    stir_table_part<R>(st, wid, nworkers, tid, NT, g.nx, smem + NST * stage_stride + 64, prep_bytes);
+    if (tid == 32) stir_draws_part<R>(st, nworkers - 1 - wid, nworkers);  // modes m = rank, rank + nworkers, ...
+  }
+
+  // Every thread waits for its staged tile (bounded); the vote in the barrier makes the
+  // whole CTA wind down together if a copy never lands.
+  bool alive = true;
+  {
+    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) alive = false;
+  }
+  int ctx_ = wid % ntx, cty = wid / ntx;  // tile being computed
+  for (int k = 0; alive && k < my_tiles; ++k) {
+    const int x0 = ctx_ * TILE_X, y0 = cty * TILE_Y;
+    ctx_ += stx; cty += sty;
+    if (ctx_ >= ntx) { ctx_ -= ntx; ++cty; }
+    tile_cells<S, VS, MASK, FORCE, CPT>(smem + (k % NST) * stage_stride, ey_off, fout, x0, y0, tid, g, p, st,
+                                        staged, err);
+    if (NST == 1) {  // the only stage is free once every thread is done with it
+      __syncthreads();
+      if (tid == 0 && k + 1 < my_tiles) issue(k + 1);
+    }
+    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % NST], ((k + 1) / NST) & 1, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {  // (NST = 2: also the barrier after which stage k % 2 is free)
       alive = false;
       break;
     }
-    if (tid == 0) {
-      tma_store_3d(&tout, otile, x0 + TL::XOFF, y0 + 1, 0);
-      bulk_commit();
-      if (k + TL::NST < my_tiles) issue(k + TL::NST);
-    }
+    if (NST >= 2 && tid == 0 && k + NST < my_tiles) issue(k + NST);
   }
-  // Preparation of the stirring table of step n+1 and the draws of step n+2, by the
-  // CTAs with the fewest tiles first (reverse order).
-  stir_prepare<R>(st, (long long)(gridDim.x - 1 - blockIdx.x) * NTHREADS + tid, (long long)gridDim.x * NTHREADS,
-                  gridDim.x - 1 - blockIdx.x, tid, gridDim.x, g.nx);
-  if (!alive) {
+  if (!alive && tid == 0) {
     // a staged copy did not land in time: latch the error and wait (bounded) once more
     // for this CTA's copies still in flight before returning
-    if (tid == 0) {
-      atomicOr(err, ERR_TIMEOUT);
-      for (int s2 = 0; s2 < TL::NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
-    }
+    atomicOr(err, ERR_TIMEOUT);
+    for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
   }
-  if (tid == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -366,9 +488,16 @@ __global__ void stir_draw_kernel(R4<R> *coef_a, R4<R> *coef_b, int nmodes, unsig
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * nmodes) return;
   const int m = t % nmodes;
-  double c[4];
-  stir_draw(seed, n + t / nmodes, m, amp, c);
-  (t < nmodes ? coef_a : coef_b)[m] = R4<R>{(R)c[0], (R)c[1], (R)c[2], (R)c[3]};
+  // same arithmetic as the draws a step launch makes for later steps
+  if constexpr (sizeof(R) == 8) {
+    double c[4];
+    stir_draw(seed, n + t / nmodes, m, amp, c);
+    (t < nmodes ? coef_a : coef_b)[m] = R4<R>{(R)c[0], (R)c[1], (R)c[2], (R)c[3]};
+  } else {
+    float c[4];
+    stir_draw_f32(seed, n + t / nmodes, m, (float)amp, c);
+    (t < nmodes ? coef_a : coef_b)[m] = R4<R>{c[0], c[1], c[2], c[3]};
+  }
 }
 
 template <typename R>
@@ -394,63 +523,79 @@ template <typename R> static Stir<R> to_stir(const HostStir &h) {
   s.nrows = h.nrows; s.nmodes = h.nmodes;
   s.G_cur = (const R4<R> *)h.G_cur; s.EY = (const R2<R> *)h.EY; s.G_next = (R4<R> *)h.G_next;
   s.coef_next = (const R4<R> *)h.coef_next; s.coef_new = (R4<R> *)h.coef_new;
-  s.mode_kx = h.mode_kx; s.row_start = h.row_start; s.EX = (const R2<R> *)h.EX; s.eyp = h.eyp;
+  s.mode_kx = h.mode_kx; s.row_start = h.row_start; s.eyp = h.eyp;
   s.seed = h.seed; s.step_new = h.step_new; s.amp = h.amp;
   return s;
 }
 
-template <typename S, int VS, bool MASK, bool FORCE>
-static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tout, const CUtensorMap &tG,
-                                 const CUtensorMap &tEY, void *fout, const Geometry<typename RealOf<S>::type> &g,
-                                 const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &s,
-                                 unsigned *err, int grid_limit, cudaStream_t stream) {
+template <typename S, int VS, bool MASK, bool FORCE, int NST>
+static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, const CUtensorMap &tEY, void *fout,
+                                 const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,
+                                 const Stir<typename RealOf<S>::type> &s, unsigned *err, int grid_limit,
+                                 cudaStream_t stream) {
   using TL = Tile<S, VS>;
-  auto kern = step_kernel<S, VS, MASK, FORCE>;
-  static int configured_dev = -1, max_blocks = 0, sms = 0;
+  constexpr int CPT = sizeof(S) == 8 ? 1 : 2;
+  constexpr int NT = NTHREADS / CPT;
+  auto kern = step_kernel<S, VS, MASK, FORCE, CPT, NST>;
+  const int srows = (FORCE && s.nrows > 0 && s.nrows <= TL::MAX_SROWS) ? s.nrows : 0;
+  // room to stage the stirring modes of the next step (coefficients, k_x, row ranges)
+  const int prep_bytes = (FORCE && s.nrows && s.nmodes <= 1024)
+                             ? (s.nmodes * (int)(sizeof(R4<typename RealOf<S>::type>) + sizeof(int)) + (s.nrows + 1) * 4 + 127) / 128 * 128
+                             : 0;
+  const int smem = TL::smem(NST, srows) + prep_bytes;
+  static int configured_dev = -1, configured_smem = -1, max_blocks = 0, sms = 0;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_dev != dev) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM);
+  if (configured_dev != dev || configured_smem != smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, kern, NTHREADS, TL::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, kern, NT, smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     configured_dev = dev;
+    configured_smem = smem;
   }
   const int ntiles = ((g.nx + TILE_X - 1) / TILE_X) * ((g.ny + TILE_Y - 1) / TILE_Y);
-  int grid = max_blocks * sms;
-  if (grid_limit > 0 && grid_limit < grid) grid = grid_limit;
-  if (grid > ntiles) grid = ntiles;
-  if (grid < 1) grid = 1;
-  kern<<<grid, NTHREADS, TL::SMEM, stream>>>(tin, tout, tG, tEY, (S *)fout, g, p, s, err);
+  int workers = max_blocks * sms;
+  if (grid_limit > 0 && grid_limit < workers) workers = grid_limit;
+  if (workers > ntiles) workers = ntiles;
+  if (workers < 1) workers = 1;
+  kern<<<workers, NT, smem, stream>>>(tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, err);
   return cudaGetLastError();
 }
 
+template <typename S, int NST>
+static cudaError_t launch_step_n(int vset, const CUtensorMap &mi, const CUtensorMap &mg, const CUtensorMap &me,
+                                 void *fout, const Geometry<typename RealOf<S>::type> &g,
+                                 const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &s,
+                                 bool mask, bool force, unsigned *err, int grid_limit, cudaStream_t stream) {
+  if (vset == 3) {
+    if (force) {
+      if (mask) return launch_step_v<S, 3, true, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+      return launch_step_v<S, 3, false, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+    }
+    if (mask) return launch_step_v<S, 3, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+    return launch_step_v<S, 3, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+  }
+  if (mask) return launch_step_v<S, 2, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+  return launch_step_v<S, 2, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+}
+
 template <typename S>
-static cudaError_t launch_step_t(int vset, const void *tin, const void *tout, const void *tg, const void *tey,
-                                 void *fout, const HostGeom &hg,
-                                 const HostPhys &hp, const HostStir &hs, unsigned *err, int grid_limit,
-                                 cudaStream_t stream) {
+static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, const void *tey, void *fout,
+                                 const HostGeom &hg, const HostPhys &hp, const HostStir &hs, unsigned *err,
+                                 int grid_limit, int stages, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
   const Geometry<R> g = to_geom<R>(hg);
   Physics<R> p;
   p.omega0 = (R)hp.omega0; p.fpref = (R)hp.fpref; p.body_x = (R)hp.body_x; p.body_y = (R)hp.body_y;
   p.vmax2 = (R)hp.vmax2;
   const Stir<R> s = to_stir<R>(hs);
-  const CUtensorMap &mi = *(const CUtensorMap *)tin, &mo = *(const CUtensorMap *)tout;
-  const CUtensorMap &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
-  const bool mask = hg.nbmask != nullptr;
-  if (vset == 3) {
-    if (hp.has_force) {
-      if (mask) return launch_step_v<S, 3, true, true>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
-      return launch_step_v<S, 3, false, true>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
-    }
-    if (mask) return launch_step_v<S, 3, true, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
-    return launch_step_v<S, 3, false, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
-  }
-  if (mask) return launch_step_v<S, 2, true, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
-  return launch_step_v<S, 2, false, false>(mi, mo, mg, me, fout, g, p, s, err, grid_limit, stream);
+  const CUtensorMap &mi = *(const CUtensorMap *)tin, &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
+  const bool mask = hg.nbmask != nullptr, force = hp.has_force != 0;
+  if (stages == 1) return launch_step_n<S, 1>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stream);
+  return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stream);
 }
 
 template <typename S>
@@ -515,10 +660,10 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
 
 #define RLBM_DEFINE_LAUNCHERS(S, SUF)                                                                    \
   namespace rlbm {                                                                                       \
-  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, const void *tg,             \
-                                const void *tey, void *fout, const HostGeom &g, const HostPhys &p,      \
-                                const HostStir &s, unsigned *err, int grid_limit, cudaStream_t st) {    \
-    return launch_step_t<S>(vset, tin, tout, tg, tey, fout, g, p, s, err, grid_limit, st);              \
+  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
+                                const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
+                                int grid_limit, int stages, cudaStream_t st) {                           \
+    return launch_step_t<S>(vset, tin, tg, tey, fout, g, p, s, err, grid_limit, stages, st);            \
   }                                                                                                      \
   cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
                                    double *ux, double *uy, double *part, unsigned *err, dim3 b,         \

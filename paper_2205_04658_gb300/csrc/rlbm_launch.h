@@ -28,16 +28,15 @@ struct HostStir {
   const void *coef_next;
   void *coef_new;
   const int *mode_kx, *row_start;
-  const void *EX;
   unsigned long long seed;
   long long step_new;
   double amp;
 };
 
 #define RLBM_DECLARE_LAUNCHERS(SUF)                                                                      \
-  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tout, const void *tg,             \
-                                const void *tey, void *fout, const HostGeom &g, const HostPhys &p,      \
-                                const HostStir &s, unsigned *err, int grid_limit, cudaStream_t st);     \
+  cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
+                                const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
+                                int grid_limit, int stages, cudaStream_t st);                            \
   cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st);               \
   cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
                                    double *ux, double *uy, double *part, unsigned *err, dim3 b,         \

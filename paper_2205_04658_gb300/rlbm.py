@@ -59,7 +59,8 @@ def lib():
             "rlbm_get_state": (c_i32, [P, dp, ctypes.POINTER(c_i64)]),
             "rlbm_set_state": (c_i32, [P, dp, c_i64]),
             "rlbm_num_planes": (c_i32, [P]),
-            "rlbm_set_grid": (c_i32, [P, c_i32]),
+            "rlbm_set_launch": (c_i32, [P, c_i32, c_i32]),
+            "rlbm_autotune": (c_i32, [P, c_i32, dp]),
             "rlbm_sync": (c_i32, [P]),
             "rlbm_current_step": (c_i64, [P]),
             "rlbm_last_error": (ctypes.c_char_p, [P]),
@@ -151,8 +152,14 @@ def rlbm_num_planes(ctx):
     return lib().rlbm_num_planes(ctx)
 
 
-def rlbm_set_grid(ctx, ctas):
-    _check(lib().rlbm_set_grid(ctx, int(ctas)), ctx)
+def rlbm_set_launch(ctx, ctas, stages=0):
+    _check(lib().rlbm_set_launch(ctx, int(ctas), int(stages)), ctx)
+
+
+def rlbm_autotune(ctx, reps=10):
+    ms = ctypes.c_double(0.0)
+    _check(lib().rlbm_autotune(ctx, int(reps), ctypes.byref(ms)), ctx)
+    return ms.value
 
 
 def rlbm_sync(ctx):
@@ -222,8 +229,11 @@ class Lattice:
     def current_step(self):
         return rlbm_current_step(self.ctx)
 
-    def set_grid(self, ctas):
-        rlbm_set_grid(self.ctx, ctas)
+    def set_launch(self, ctas, stages=0):
+        rlbm_set_launch(self.ctx, ctas, stages)
+
+    def autotune(self, reps=10):
+        return rlbm_autotune(self.ctx, reps)
 
     def sync(self):
         rlbm_sync(self.ctx)

@@ -208,3 +208,25 @@ def test_full_size_1024_fp32_sampled(R):
 
 def test_maximum_size_4096_fp32_sampled(R):
     _sampled_check(R, 4096, 4096, 2, "f32", 12, 2)
+
+
+def test_launch_shapes_give_identical_results(R):
+    """The launch shape (pipeline depth, CTA count) and the autotuner change nothing in
+    the results: every cell is computed by the same arithmetic wherever it runs."""
+    nx, ny = 160, 72
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=21, u_amp=0.03)
+    kw = dict(eta_over_s=0.05, kmin=3, kmax=6, force_amp=1e-3, seed=8, init_eps=e, init_ux=ux, init_uy=uy)
+    outs = []
+    for shape in ((0, 2), (0, 1), (7, 2), (3, 1), None):
+        lat = R.Lattice(nx, ny, precision="f32", **kw)
+        if shape is None:
+            assert lat.autotune(3) > 0
+        else:
+            lat.set_launch(*shape)
+        lat.step(25)
+        outs.append(lat.moments())
+        assert lat.current_step == 25
+        lat.close()
+    for o in outs[1:]:
+        for k in range(3):
+            assert np.array_equal(o[k], outs[0][k])
