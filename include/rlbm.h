@@ -146,6 +146,29 @@ RLBM_API rlbm_status rlbm_set_launch(rlbm_ctx *ctx, int32_t ctas, int32_t stages
  * The paper has no counterpart. */
 RLBM_API rlbm_status rlbm_autotune(rlbm_ctx *ctx, int32_t reps, double *ms_out);
 
+/* Energy spectrum of device velocity fields, allocating nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc, such as
+ * code that owns all device memory through its own allocator or a fixed budget, or code
+ * in a loop where cudaMalloc's implicit device-wide synchronisation would stall other
+ * streams.  (rlbm_spectrum needs a context, whose workspace the caller allocates.)
+ *
+ * d_ux, d_uy: device arrays of nx * ny doubles (u^x, u^y, row-major, x fastest; the
+ * result uses v = u^i / u^0); d_E: device array receiving nbins doubles,
+ * E[n] = 1/2 sum_{round|k| = n} |v^(k)|^2 / (nx ny)^2 exactly as rlbm_spectrum.  Queued
+ * on cuda_stream (NULL = default stream); no synchronisation.
+ *
+ * Limits: 8 <= nx, ny <= 16384, nx * ny <= 131072 (2^17) cells, 1 <= nbins <= 8200;
+ * larger requests return RLBM_E_INVAL with a message in rlbm_last_error(NULL).  The
+ * work buffers are one fixed array of about 4.3 MB in the library's own device memory
+ * (every GPU that loads the library holds it until the process exits).  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call on a device before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (the bins are cleared at the start of each call):
+ * calls that overlap on the GPU, from several streams or threads, race and must be
+ * serialised by the caller. */
+RLBM_API rlbm_status rlbm_spectrum_noalloc(const double *d_ux, const double *d_uy, int32_t nx, int32_t ny,
+                                           int32_t nbins, double *d_E, void *cuda_stream);
+
 /* Wait for queued work and report latched device errors. */
 RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);
 

@@ -395,6 +395,11 @@ template <typename S> void pack_state(const rlbm_ctx *c, const double *src, uint
 
 }  // namespace
 
+namespace rlbm {
+// Lets the allocation-free entry point (rlbm_noalloc.cu) report through rlbm_last_error(NULL).
+void set_thread_error(const std::string &msg) { g_thread_error = msg; }
+}  // namespace rlbm
+
 extern "C" {
 
 rlbm_status rlbm_query_workspace(const rlbm_config *cfg, size_t *bytes) {

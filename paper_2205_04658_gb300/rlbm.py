@@ -61,6 +61,7 @@ def lib():
             "rlbm_num_planes": (c_i32, [P]),
             "rlbm_set_launch": (c_i32, [P, c_i32, c_i32]),
             "rlbm_autotune": (c_i32, [P, c_i32, dp]),
+            "rlbm_spectrum_noalloc": (c_i32, [P, P, c_i32, c_i32, c_i32, P, P]),
             "rlbm_sync": (c_i32, [P]),
             "rlbm_current_step": (c_i64, [P]),
             "rlbm_last_error": (ctypes.c_char_p, [P]),
@@ -160,6 +161,12 @@ def rlbm_autotune(ctx, reps=10):
     ms = ctypes.c_double(0.0)
     _check(lib().rlbm_autotune(ctx, int(reps), ctypes.byref(ms)), ctx)
     return ms.value
+
+
+def rlbm_spectrum_noalloc(d_ux, d_uy, nx, ny, nbins, d_E, cuda_stream):
+    """Spectrum of device velocity fields (device pointers as integers), allocating nothing."""
+    _check(lib().rlbm_spectrum_noalloc(ctypes.c_void_p(d_ux), ctypes.c_void_p(d_uy), int(nx), int(ny), int(nbins),
+                                       ctypes.c_void_p(d_E), ctypes.c_void_p(cuda_stream)))
 
 
 def rlbm_sync(ctx):
