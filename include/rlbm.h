@@ -77,7 +77,9 @@ typedef struct {
   int32_t vset;            /* 3: the paper's 26-direction spherical set (P = eps/3);
                               2: 8 directions on the unit circle (P = eps/2, no force) */
   int32_t precision;       /* rlbm_precision */
-  int32_t reserved0;       /* must be 0 */
+  int32_t rounding;        /* F16/BF16 storage: 0 = stochastic rounding (default; unbiased,
+                              counter-based per seed, step and cell, so runs repeat
+                              exactly), 1 = round to nearest.  Ignored for F64/F32. */
   double a, dt;            /* lattice spacing and time step; requires 0 < dt/a <= 1 */
   double eta_over_s;       /* > 0; tau_R = 5 (eta/s) / T (4 (eta/s) / T for vset 2) */
   double eps0;             /* > 0; reference energy density, T0 = T(eps0) */
@@ -168,6 +170,13 @@ RLBM_API rlbm_status rlbm_autotune(rlbm_ctx *ctx, int32_t reps, double *ms_out);
  * serialised by the caller. */
 RLBM_API rlbm_status rlbm_spectrum_noalloc(const double *d_ux, const double *d_uy, int32_t nx, int32_t ny,
                                            int32_t nbins, double *d_E, void *cuda_stream);
+
+/* The folded velocity classes behind the planes of rlbm_get_state / rlbm_set_state:
+ * for vset 3 (17 classes) or 2 (8 classes), out[4*q + 0..3] = (v_x, v_y, v_z^2, w) of
+ * class q, where w is the summed weight of the 3-D directions the class stands for.
+ * Returns the class count (and writes nothing when out is NULL), or -1 for a bad vset.
+ * The paper has no counterpart (a layout query). */
+RLBM_API int32_t rlbm_velocity_classes(int32_t vset, double *out);
 
 /* Wait for queued work and report latched device errors. */
 RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);

@@ -116,7 +116,7 @@ std::string validate(const rlbm_config *c) {
   if (c->walls_y != 0 && c->walls_y != 1) return "walls_y must be 0 or 1";
   if (c->vset != 2 && c->vset != 3) return "vset must be 2 or 3";
   if (c->precision < RLBM_F64 || c->precision > RLBM_BF16) return "precision must be one of RLBM_F64..RLBM_BF16";
-  if (c->reserved0 != 0) return "reserved0 must be 0";
+  if (c->rounding != 0 && c->rounding != 1) return "rounding must be 0 (stochastic) or 1 (to nearest)";
   if (!(c->a > 0.0) || !(c->dt > 0.0) || !std::isfinite(c->a) || !std::isfinite(c->dt))
     return "a and dt must be positive and finite";
   if (c->dt / c->a > 1.0) return "dt / a must not exceed 1 (the streaming displacement stays within one cell)";
@@ -468,6 +468,8 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   c->phys.body_y = cfg->body_force[1];
   c->phys.vmax2 = c->cfg.fp64_landau_vmax * c->cfg.fp64_landau_vmax;
   c->phys.has_force = (stirring_on(*cfg) || cfg->body_force[0] != 0.0 || cfg->body_force[1] != 0.0) ? 1 : 0;
+  c->phys.stochastic = cfg->rounding == 0 ? 1 : 0;
+  c->phys.round_key = (unsigned)(cfg->seed ^ (cfg->seed >> 32)) ^ 0x5bd1e995u;
 
   // Host staging buffers; copies from pageable memory have consumed their source when
   // cudaMemcpyAsync returns, and init synchronises the stream before it returns.
@@ -563,6 +565,7 @@ rlbm_status rlbm_step(rlbm_ctx *c, int64_t nsteps) {
   Scoped dev(c->device);
   for (int64_t i = 0; i < nsteps; ++i) {
     const HostStir s = stir_for_step(c, c->step);
+    c->phys.step = c->step;
     cudaError_t e = dispatch_step(c, c->cur, s);
     if (e != cudaSuccess) return c->cuda_fail(e, "step kernel launch");
     c->cur ^= 1;
@@ -647,6 +650,18 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
 }
 
 int32_t rlbm_num_planes(const rlbm_ctx *c) { return c ? c->L.Q : -1; }
+
+int32_t rlbm_velocity_classes(int32_t vset, double *out) {
+  if (vset != 2 && vset != 3) return -1;
+  const int Q = num_classes(vset);
+  for (int q = 0; out && q < Q; ++q) {
+    out[4 * q + 0] = vset == 3 ? VSet<3>::vx(q) : VSet<2>::vx(q);
+    out[4 * q + 1] = vset == 3 ? VSet<3>::vy(q) : VSet<2>::vy(q);
+    out[4 * q + 2] = vset == 3 ? VSet<3>::vz2(q) : VSet<2>::vz2(q);
+    out[4 * q + 3] = vset == 3 ? VSet<3>::w(q) : VSet<2>::w(q);
+  }
+  return Q;
+}
 
 rlbm_status rlbm_set_launch(rlbm_ctx *c, int32_t ctas, int32_t stages) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }

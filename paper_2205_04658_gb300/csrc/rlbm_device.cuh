@@ -140,7 +140,40 @@ template <typename R> struct Physics {
   R fpref;         // -6 dt / T0: force prefactor including dt
   R body_x, body_y;
   R vmax2;         // FP32 path: |v|^2 above which Landau runs in FP64
+  int stochastic;  // 16-bit storage: stochastic rounding
+  unsigned round_key;
+  unsigned step;   // low 32 bits of the step index (rounding bits)
 };
+
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the 16-bit stores: unbiased (E[round(v)] = v), so the rounding
+// errors of successive steps do not add up coherently.  The random bits are a
+// counter-based hash of (cell, step, key) stepped by a linear congruential generator per
+// value, so a run repeats exactly.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cell_hash(uint32_t x, uint32_t y, uint32_t step, uint32_t key) {
+  uint32_t h = (x * 0x9E3779B1u) ^ ((y + 0x7F4A7C15u) * 0x85EBCA77u) ^ ((step ^ key) * 0xC2B2AE3Du);
+  h ^= h >> 16; h *= 0x7FEB352Du; h ^= h >> 15; h *= 0x846CA68Bu; h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t lcg_next(uint32_t r) { return r * 1664525u + 1013904223u; }
+
+// v rounded to storage type S: to nearest, or stochastically with the random bits r.
+// FP16: adding 13 random bits below the kept mantissa and truncating (round toward zero)
+// rounds the magnitude up with probability equal to the dropped fraction; below the
+// FP16 normal range (|v| < 2^-14) the value is rounded to nearest.  BF16: the same with
+// 16 bits on the FP32 pattern.
+template <typename S> __device__ __forceinline__ S store_round(float v, bool sr, uint32_t r) {
+  return store_h<S, float>(v);
+}
+template <> __device__ __forceinline__ __half store_round<__half>(float v, bool sr, uint32_t r) {
+  if (!sr || fabsf(v) < 6.103515625e-05f) return __float2half_rn(v);
+  return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 store_round<__nv_bfloat16>(float v, bool sr, uint32_t r) {
+  if (!sr) return __float2bfloat16_rn(v);
+  return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
+}
 
 template <typename R> struct Stir {
   int nrows;               // distinct k_y of the shell (0 = no stirring)

@@ -228,16 +228,30 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     const Coll<T> cf = coll_coeffs<T, VS, FORCE>(M, m, T(p.omega0), T(p.fpref), Fx, Fy);
     collide_all<T, VS, FORCE>(cf, h, hn);
   }
+  // round once to the storage type (the ghost images below repeat the same values)
+  S sA[Q], sB[Q];
+  {
+    const bool sr = sizeof(S) == 2 && p.stochastic;
+    uint32_t rA = sr ? cell_hash(x, yA, p.step, p.round_key) : 0u;
+    uint32_t rB = sr ? cell_hash(x, yB, p.step, p.round_key) : 0u;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      rA = lcg_next(rA);
+      rB = lcg_next(rB);
+      sA[q] = store_round<S>(flA ? hn[q].v.x : 0.0f, sr, rA);
+      sB[q] = store_round<S>(flB ? hn[q].v.y : 0.0f, sr, rB);
+    }
+  }
   {  // coalesced stores straight from registers (one 128-byte line per warp and plane)
     S *oA = fout + (long long)(yA + 1) * g.pitch + x + TL::XOFF;
     S *oB = oA + (long long)(TILE_Y / 2) * g.pitch;
     if (inA) {
 #pragma unroll
-      for (int q = 0; q < Q; ++q) oA[q * g.plane] = store_h<S, float>(flA ? hn[q].v.x : 0.0f);
+      for (int q = 0; q < Q; ++q) oA[q * g.plane] = sA[q];
     }
     if (inB) {
 #pragma unroll
-      for (int q = 0; q < Q; ++q) oB[q * g.plane] = store_h<S, float>(flB ? hn[q].v.y : 0.0f);
+      for (int q = 0; q < Q; ++q) oB[q * g.plane] = sB[q];
     }
   }
   // ghost copies of the periodic neighbours (boundary cells only)
@@ -248,13 +262,12 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
     const int gyv = g.walls ? INT_MIN : (y == 0 ? g.ny : (y == g.ny - 1 ? -1 : INT_MIN));
     if (gxv == INT_MIN && gyv == INT_MIN) continue;
-    const bool fl = lane ? flB : flA;
     const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
     for (int a = 0; a < 3; ++a) {
       if (px[a] == INT_MIN || py[a] == INT_MIN) continue;
       S *o = fout + (long long)(py[a] + 1) * g.pitch + px[a] + TL::XOFF;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) o[q * g.plane] = store_h<S, float>(fl ? (lane ? hn[q].v.y : hn[q].v.x) : 0.0f);
+      for (int q = 0; q < Q; ++q) o[q * g.plane] = lane ? sB[q] : sA[q];
     }
   }
 }
@@ -591,6 +604,9 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, cons
   Physics<R> p;
   p.omega0 = (R)hp.omega0; p.fpref = (R)hp.fpref; p.body_x = (R)hp.body_x; p.body_y = (R)hp.body_y;
   p.vmax2 = (R)hp.vmax2;
+  p.stochastic = hp.stochastic;
+  p.round_key = hp.round_key;
+  p.step = (unsigned)(hp.step & 0xffffffffll);
   const Stir<R> s = to_stir<R>(hs);
   const CUtensorMap &mi = *(const CUtensorMap *)tin, &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
   const bool mask = hg.nbmask != nullptr, force = hp.has_force != 0;

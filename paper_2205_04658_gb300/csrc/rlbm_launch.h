@@ -18,6 +18,9 @@ struct HostGeom {
 struct HostPhys {
   double omega0, fpref, body_x, body_y, vmax2;
   int has_force;
+  int stochastic;          // 16-bit storage: stochastic rounding
+  unsigned round_key;      // key of the rounding bits
+  long long step;          // index n of the step being launched
 };
 
 struct HostStir {

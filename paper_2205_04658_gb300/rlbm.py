@@ -28,7 +28,7 @@ class RlbmError(RuntimeError):
 class rlbm_config(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("walls_y", ctypes.c_int32),
-        ("vset", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("vset", ctypes.c_int32), ("precision", ctypes.c_int32), ("rounding", ctypes.c_int32),
         ("a", ctypes.c_double), ("dt", ctypes.c_double), ("eta_over_s", ctypes.c_double),
         ("eps0", ctypes.c_double), ("body_force", ctypes.c_double * 2),
         ("kmin", ctypes.c_int32), ("kmax", ctypes.c_int32), ("force_amp", ctypes.c_double),
@@ -61,6 +61,7 @@ def lib():
             "rlbm_num_planes": (c_i32, [P]),
             "rlbm_set_launch": (c_i32, [P, c_i32, c_i32]),
             "rlbm_autotune": (c_i32, [P, c_i32, dp]),
+            "rlbm_velocity_classes": (c_i32, [c_i32, dp]),
             "rlbm_spectrum_noalloc": (c_i32, [P, P, c_i32, c_i32, c_i32, P, P]),
             "rlbm_sync": (c_i32, [P]),
             "rlbm_current_step": (c_i64, [P]),
@@ -86,7 +87,7 @@ def _dptr(a):
 
 def make_config(nx, ny, precision="f32", walls_y=0, vset=3, a=0.1, dt=0.05, eta_over_s=0.1, eps0=1.0,
                 body_force=(0.0, 0.0), kmin=0, kmax=0, force_amp=0.0, seed=0, solid=None,
-                init_eps=None, init_ux=None, init_uy=None, fp64_landau_vmax=0.0):
+                init_eps=None, init_ux=None, init_uy=None, fp64_landau_vmax=0.0, rounding="stochastic"):
     """An rlbm_config and the host arrays it points to (keep both alive until rlbm_init
     returns)."""
     keep = {}
@@ -101,7 +102,7 @@ def make_config(nx, ny, precision="f32", walls_y=0, vset=3, a=0.1, dt=0.05, eta_
     c = rlbm_config()
     c.nx, c.ny, c.walls_y, c.vset = nx, ny, int(walls_y), int(vset)
     c.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
-    c.reserved0 = 0
+    c.rounding = {"stochastic": 0, "nearest": 1}[rounding] if isinstance(rounding, str) else int(rounding)
     c.a, c.dt, c.eta_over_s, c.eps0 = a, dt, eta_over_s, eps0
     c.body_force[0], c.body_force[1] = body_force
     c.kmin, c.kmax, c.force_amp, c.seed = int(kmin), int(kmax), float(force_amp), int(seed)
@@ -167,6 +168,14 @@ def rlbm_spectrum_noalloc(d_ux, d_uy, nx, ny, nbins, d_E, cuda_stream):
     """Spectrum of device velocity fields (device pointers as integers), allocating nothing."""
     _check(lib().rlbm_spectrum_noalloc(ctypes.c_void_p(d_ux), ctypes.c_void_p(d_uy), int(nx), int(ny), int(nbins),
                                        ctypes.c_void_p(d_E), ctypes.c_void_p(cuda_stream)))
+
+
+def rlbm_velocity_classes(vset=3):
+    """(Q, 4) array of (v_x, v_y, v_z^2, w) of the folded classes (plane order of get/set_state)."""
+    q = lib().rlbm_velocity_classes(int(vset), None)
+    out = np.empty(4 * q)
+    lib().rlbm_velocity_classes(int(vset), _dptr(out))
+    return out.reshape(q, 4)
 
 
 def rlbm_sync(ctx):
