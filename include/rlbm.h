@@ -178,6 +178,42 @@ RLBM_API rlbm_status rlbm_spectrum_noalloc(const double *d_ux, const double *d_u
  * The paper has no counterpart (a layout query). */
 RLBM_API int32_t rlbm_velocity_classes(int32_t vset, double *out);
 
+/* ---- Batches: many lattices advanced by one persistent launch per step -------------
+ * An ensemble (stirred realisations, impurity samples) of uneven sizes steps as one job:
+ * each step is a single launch of the fused kernel over the tiles of all members
+ * (north-star "batching" form), and whole chunks of steps replay a captured CUDA graph.
+ * Members are ordinary contexts (rlbm_init) that share the velocity set, storage type,
+ * a, dt, eta/s, eps0, body force, stirring shell and amplitude, rounding and
+ * fp64_landau_vmax; they may differ in size, walls, solids, seeds and initial fields,
+ * and in their current step.  After rlbm_batch_step every member has advanced by nsteps
+ * (rlbm_current_step, rlbm_moments ... work on it as usual); work of the batch is queued
+ * on the batch's stream, so give the members the same stream or synchronise.  Graphs are
+ * used on a non-default stream only.  The paper has no counterpart (its runs were one
+ * lattice per process). */
+typedef struct rlbm_batch rlbm_batch;
+
+/* Device bytes of a batch workspace for nmembers members (member descriptors, tile and
+ * work prefixes, the step counter). */
+RLBM_API rlbm_status rlbm_batch_query_workspace(int32_t nmembers, size_t *bytes);
+
+/* Create a batch over members[0 .. nmembers-1] (the contexts stay owned by the caller and
+ * must outlive the batch).  dev_workspace: 256-byte aligned, caller-owned. */
+RLBM_API rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers, void *dev_workspace,
+                                     size_t bytes, void *cuda_stream, rlbm_batch **out);
+
+/* Launch shape of the batched step kernel (as rlbm_set_launch). */
+RLBM_API rlbm_status rlbm_batch_set_launch(rlbm_batch *b, int32_t ctas, int32_t stages);
+
+/* Advance every member by nsteps >= 0 steps.  Async. */
+RLBM_API rlbm_status rlbm_batch_step(rlbm_batch *b, int64_t nsteps);
+
+/* Message of the last failing call on b (or of the last failing batch call on this thread
+ * when b is NULL). */
+RLBM_API const char *rlbm_batch_last_error(const rlbm_batch *b);
+
+/* Release the batch (not its workspace, not the members). */
+RLBM_API void rlbm_batch_free(rlbm_batch *b);
+
 /* Wait for queued work and report latched device errors. */
 RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);
 

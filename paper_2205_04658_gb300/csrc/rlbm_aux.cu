@@ -30,6 +30,14 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partials, long
   }
 }
 
+__global__ void counter_inc_kernel(long long *c) { *c += 1; }
+
+// Advances the batch step counter between two batched step launches (stream order).
+cudaError_t launch_counter_inc(long long *counter, cudaStream_t st) {
+  counter_inc_kernel<<<1, 1, 0, st>>>(counter);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st) {
   reduce_partials_kernel<<<1, 256, 0, st>>>(partials, nblocks, totals);
   return cudaGetLastError();

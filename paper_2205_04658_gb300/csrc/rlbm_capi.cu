@@ -733,4 +733,209 @@ void rlbm_free(rlbm_ctx *c) {
   delete c;
 }
 
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct rlbm_batch {
+  std::vector<rlbm_ctx *> members;
+  char *ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  MemberDesc *d_mem = nullptr;
+  int *d_tile0 = nullptr, *d_draw0 = nullptr;
+  long long *d_entry0 = nullptr, *d_bstep = nullptr;
+  std::vector<MemberDesc> h_mem;
+  int ntiles = 0, srows = 0, stages = 2, grid_limit = 0;
+  bool mask = false;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  std::string msg;
+  rlbm_status fail(rlbm_status s, const std::string &m) { msg = m; return s; }
+  rlbm_status cuda_fail(cudaError_t e, const char *what) { msg = std::string(what) + ": " + cudaGetErrorString(e); return RLBM_E_CUDA; }
+};
+
+namespace {
+
+struct BatchLayout { size_t mem, tile0, entry0, draw0, bstep, total; };
+
+BatchLayout batch_layout(int n) {
+  BatchLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t b) { size_t o = off; off += align_up(std::max<size_t>(b, 1)); return o; };
+  L.mem = take(sizeof(MemberDesc) * (size_t)n);
+  L.tile0 = take(sizeof(int) * (size_t)(n + 1));
+  L.entry0 = take(sizeof(long long) * (size_t)(n + 1));
+  L.draw0 = take(sizeof(int) * (size_t)(n + 1));
+  L.bstep = take(sizeof(long long));
+  L.total = off;
+  return L;
+}
+
+bool same_physics(const rlbm_config &a, const rlbm_config &b) {
+  return a.vset == b.vset && a.precision == b.precision && a.a == b.a && a.dt == b.dt &&
+         a.eta_over_s == b.eta_over_s && a.eps0 == b.eps0 && a.body_force[0] == b.body_force[0] &&
+         a.body_force[1] == b.body_force[1] && a.kmin == b.kmin && a.kmax == b.kmax && a.force_amp == b.force_amp &&
+         a.rounding == b.rounding && a.fp64_landau_vmax == b.fp64_landau_vmax;
+}
+
+cudaError_t batch_launch_one(rlbm_batch *b) {
+  rlbm_ctx *c0 = b->members[0];
+  BatchTables bt{b->d_mem, b->d_tile0, b->d_entry0, b->d_draw0, (int)b->members.size()};
+  cudaError_t e;
+  const double amp = c0->cfg.force_amp;
+  switch (c0->cfg.precision) {
+    case RLBM_F64: e = launch_batch_step_f64(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream); break;
+    case RLBM_F32: e = launch_batch_step_f32(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream); break;
+    case RLBM_F16: e = launch_batch_step_f16(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream); break;
+    default: e = launch_batch_step_bf16(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream); break;
+  }
+  if (e != cudaSuccess) return e;
+  return launch_counter_inc(b->d_bstep, b->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+rlbm_status rlbm_batch_query_workspace(int32_t nmembers, size_t *bytes) {
+  if (nmembers < 1 || !bytes) { g_thread_error = "nmembers must be >= 1 and bytes non-NULL"; return RLBM_E_INVAL; }
+  *bytes = batch_layout(nmembers).total;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers, void *dev_workspace, size_t bytes,
+                            void *cuda_stream, rlbm_batch **out) {
+  if (!out) { g_thread_error = "out is NULL"; return RLBM_E_INVAL; }
+  *out = nullptr;
+  if (!members || nmembers < 1) { g_thread_error = "members must hold nmembers >= 1 contexts"; return RLBM_E_INVAL; }
+  const BatchLayout L = batch_layout(nmembers);
+  if (!dev_workspace || reinterpret_cast<uintptr_t>(dev_workspace) % kAlign) { g_thread_error = "dev_workspace must be a 256-byte aligned device pointer"; return RLBM_E_INVAL; }
+  if (bytes < L.total) { g_thread_error = "batch workspace too small"; return RLBM_E_NOMEM; }
+  for (int i = 0; i < nmembers; ++i) {
+    if (!members[i]) { g_thread_error = "member " + std::to_string(i) + " is NULL"; return RLBM_E_INVAL; }
+    if (members[i]->latched != RLBM_OK) { g_thread_error = "member " + std::to_string(i) + " is in an error state"; return RLBM_E_STATE; }
+    if (!same_physics(members[0]->cfg, members[i]->cfg))
+      { g_thread_error = "member " + std::to_string(i) + " differs from member 0 in velocity set, storage type, a, dt, eta/s, eps0, force or rounding"; return RLBM_E_INVAL; }
+    if (members[i]->device != members[0]->device) { g_thread_error = "members live on different devices"; return RLBM_E_INVAL; }
+  }
+  rlbm_batch *b = new (std::nothrow) rlbm_batch();
+  if (!b) { g_thread_error = "host allocation failed"; return RLBM_E_NOMEM; }
+  b->members.assign(members, members + nmembers);
+  b->ws = static_cast<char *>(dev_workspace);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->device = members[0]->device;
+  b->d_mem = reinterpret_cast<MemberDesc *>(b->ws + L.mem);
+  b->d_tile0 = reinterpret_cast<int *>(b->ws + L.tile0);
+  b->d_entry0 = reinterpret_cast<long long *>(b->ws + L.entry0);
+  b->d_draw0 = reinterpret_cast<int *>(b->ws + L.draw0);
+  b->d_bstep = reinterpret_cast<long long *>(b->ws + L.bstep);
+  b->stages = members[0]->stages;
+  const int nrows = members[0]->L.nrows;
+  b->srows = (nrows > 0 && nrows <= 16) ? nrows : 0;
+  std::vector<int> tile0(nmembers + 1, 0), draw0(nmembers + 1, 0);
+  std::vector<long long> entry0(nmembers + 1, 0);
+  b->h_mem.resize(nmembers);
+  for (int i = 0; i < nmembers; ++i) {
+    rlbm_ctx *c = members[i];
+    MemberDesc &d = b->h_mem[i];
+    std::memset(&d, 0, sizeof(d));
+    d.tin[0] = c->tmap_in[0]; d.tin[1] = c->tmap_in[1];
+    d.tG[0] = c->tmap_G[0]; d.tG[1] = c->tmap_G[1]; d.tEY = c->tmap_EY;
+    d.f[0] = c->ws + c->L.pop[0]; d.f[1] = c->ws + c->L.pop[1];
+    d.nbmask = c->geom.nbmask;
+    d.nx = c->cfg.nx; d.ny = c->cfg.ny; d.pitch = c->L.pitch; d.walls = c->cfg.walls_y; d.plane = c->L.plane;
+    d.nrows = c->L.nrows; d.nmodes = c->L.nmodes; d.eyp = c->L.eyp;
+    d.G[0] = c->ws + c->L.G[0]; d.G[1] = c->ws + c->L.G[1]; d.EY = c->ws + c->L.EY;
+    d.coef[0] = c->ws + c->L.coef[0]; d.coef[1] = c->ws + c->L.coef[1];
+    d.mode_kx = c->at<int>(c->L.mode_kx); d.row_start = c->at<int>(c->L.row_start);
+    d.seed = c->cfg.seed; d.round_key = c->phys.round_key; d.err = c->at<unsigned>(c->L.err);
+    d.ntx = (c->cfg.nx + 31) / 32;
+    const int nt = d.ntx * ((c->cfg.ny + 7) / 8);
+    tile0[i + 1] = tile0[i] + nt;
+    entry0[i + 1] = entry0[i] + (c->L.nmodes ? (long long)c->L.nrows * c->cfg.nx : 0);
+    draw0[i + 1] = draw0[i] + c->L.nmodes;
+    if (c->geom.nbmask) b->mask = true;
+  }
+  b->ntiles = tile0[nmembers];
+  Scoped dev(b->device);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b->d_tile0, tile0.data(), sizeof(int) * (nmembers + 1), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->d_entry0, entry0.data(), sizeof(long long) * (nmembers + 1), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->d_draw0, draw0.data(), sizeof(int) * (nmembers + 1), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(b->stream)) != cudaSuccess) {
+    g_thread_error = std::string("batch tables upload: ") + cudaGetErrorString(e);
+    delete b;
+    return RLBM_E_CUDA;
+  }
+  *out = b;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_set_launch(rlbm_batch *b, int32_t ctas, int32_t stages) {
+  if (!b) { g_thread_error = "batch is NULL"; return RLBM_E_INVAL; }
+  if (ctas < 0 || stages < 0 || stages > 2) return b->fail(RLBM_E_INVAL, "ctas must be >= 0 and stages 0, 1 or 2");
+  b->grid_limit = ctas;
+  if (stages) b->stages = stages;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_batch_step(rlbm_batch *b, int64_t nsteps) {
+  if (!b) { g_thread_error = "batch is NULL"; return RLBM_E_INVAL; }
+  if (nsteps < 0) return b->fail(RLBM_E_INVAL, "nsteps must be >= 0");
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (b->members[i]->latched != RLBM_OK) return b->fail(RLBM_E_STATE, "member " + std::to_string(i) + " is in an error state");
+  if (nsteps == 0) return RLBM_OK;
+  Scoped dev(b->device);
+  // the members' current buffers and steps (they may have been stepped on their own)
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    b->h_mem[i].cur0 = b->members[i]->cur;
+    b->h_mem[i].step0 = b->members[i]->step;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(MemberDesc) * b->h_mem.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bstep, 0, sizeof(long long), b->stream);
+  if (e != cudaSuccess) return b->cuda_fail(e, "batch descriptor upload");
+  // Whole chunks of steps replay one captured CUDA graph (kernel + counter advance per
+  // step); the remainder, and any run on the legacy default stream (which cannot be
+  // captured), launch directly.
+  const int chunk = 64;
+  int64_t done = 0;
+  if (b->stream != nullptr && nsteps >= chunk) {
+    if (!b->graph) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      for (int i = 0; e == cudaSuccess && i < chunk; ++i) e = batch_launch_one(b);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return b->cuda_fail(e, "batch graph capture");
+      b->graph_steps = chunk;
+    }
+    for (; done + chunk <= nsteps; done += chunk)
+      if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return b->cuda_fail(e, "batch graph launch");
+  }
+  for (; done < nsteps; ++done)
+    if ((e = batch_launch_one(b)) != cudaSuccess) return b->cuda_fail(e, "batch step launch");
+  for (rlbm_ctx *c : b->members) {
+    c->step += nsteps;
+    c->cur ^= (int)(nsteps & 1);
+  }
+  return RLBM_OK;
+}
+
+const char *rlbm_batch_last_error(const rlbm_batch *b) { return b ? b->msg.c_str() : g_thread_error.c_str(); }
+
+void rlbm_batch_free(rlbm_batch *b) {
+  if (!b) return;
+  {
+    Scoped dev(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+  }
+  delete b;
+}
+
 }  // extern "C"

@@ -133,6 +133,7 @@ template <typename R> struct Geometry {
   int walls;                // y ghost rows are solid (never written)
   const uint16_t *nbmask;   // bit 4: cell solid; bit (dy+1)*3+(dx+1): neighbour (x+dx, y+dy) solid
   R beta[17][4];            // bilinear weights of corners (0,0), (s_x,0), (0,s_y), (s_x,s_y)
+  float2 beta2[17][4];      // the same duplicated into pairs (packed two-cell arithmetic)
 };
 
 template <typename R> struct Physics {

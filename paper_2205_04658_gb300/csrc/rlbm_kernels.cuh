@@ -37,11 +37,11 @@ template <typename S, int VS> struct Tile {
 };
 
 // One cell per thread (256 threads): the FP64 path.
-template <typename S, int VS, bool MASK, bool FORCE, int CPT>
+template <typename S, int VS, bool MASK, bool FORCE, int CPT, class G, class W>
 __device__ __forceinline__ typename std::enable_if<CPT == 1>::type
-tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid,
-           const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,
-           const Stir<typename RealOf<S>::type> &st, bool staged, unsigned *err) {
+tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid, const G &g, const W &wts,
+           const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &st, bool staged,
+           unsigned *err) {
   using R = typename RealOf<S>::type;
   using V = VSet<VS>;
   using TL = Tile<S, VS>;
@@ -51,7 +51,7 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     const S *tile = reinterpret_cast<const S *>(stg);
     const bool inside = x < g.nx && y < g.ny;
     unsigned nb = 0;
-    if (MASK && inside) nb = g.nbmask[(long long)y * g.nx + x];
+    if (MASK && g.nbmask && inside) nb = g.nbmask[(long long)y * g.nx + x];
     const bool fluid = inside && !(MASK && (nb & 16u));
     R hn[Q];
     if (fluid) {
@@ -63,21 +63,21 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         const S *pl = tile + q * TL::TYB * TL::TXB + b0;
         const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
         const R c = load_h_s<S, R>(pl);
-        R acc = g.beta[q][0] * c;
+        R acc = wts.beta[q][0] * c;
         if (sx != 0) {
           R v = load_h_s<S, R>(pl - sx);
           if (MASK && ((nb >> (4 - sx)) & 1u)) v = load_h_s<S, R>(tile + V::opp(q) * TL::TYB * TL::TXB + b0);
-          acc = fma(g.beta[q][1], v, acc);
+          acc = fma(wts.beta[q][1], v, acc);
         }
         if (sy != 0) {
           R v = load_h_s<S, R>(pl - sy * TL::TXB);
           if (MASK && ((nb >> (4 - 3 * sy)) & 1u)) v = load_h_s<S, R>(tile + V::opp(q) * TL::TYB * TL::TXB + b0);
-          acc = fma(g.beta[q][2], v, acc);
+          acc = fma(wts.beta[q][2], v, acc);
         }
         if (sx != 0 && sy != 0) {
           R v = load_h_s<S, R>(pl - sy * TL::TXB - sx);
           if (MASK && ((nb >> (4 - 3 * sy - sx)) & 1u)) v = load_h_s<S, R>(tile + V::opp(q) * TL::TYB * TL::TXB + b0);
-          acc = fma(g.beta[q][3], v, acc);
+          acc = fma(wts.beta[q][3], v, acc);
         }
         h[q] = acc;
       }
@@ -147,11 +147,10 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
 
 // Two cells per thread (128 threads): cells (x, y) and (x, y + 4) of the 32 x 8 tile, all
 // per-cell arithmetic on packed FP32 pairs.  The FP32, FP16 and BF16 paths.
-template <typename S, int VS, bool MASK, bool FORCE, int CPT>
+template <typename S, int VS, bool MASK, bool FORCE, int CPT, class G, class W>
 __device__ __forceinline__ typename std::enable_if<CPT == 2>::type
-tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid,
-           const Geometry<float> &g, const Physics<float> &p, const Stir<float> &st, bool staged,
-           unsigned *err) {
+tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid, const G &g, const W &wts,
+           const Physics<float> &p, const Stir<float> &st, bool staged, unsigned *err) {
   using V = VSet<VS>;
   using TL = Tile<S, VS>;
   using T = F2;
@@ -162,11 +161,12 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
   const S *tile = reinterpret_cast<const S *>(stg);
   const bool inA = x < g.nx && yA < g.ny, inB = x < g.nx && yB < g.ny;
   unsigned nbA = 0, nbB = 0;
-  if (MASK) {
+  if (MASK && g.nbmask) {
     if (inA) nbA = g.nbmask[(long long)yA * g.nx + x];
     if (inB) nbB = g.nbmask[(long long)yB * g.nx + x];
   }
   const bool flA = inA && !(MASK && (nbA & 16u)), flB = inB && !(MASK && (nbB & 16u));
+  const bool both = flA && flB;
   T hn[Q];
   if (flA || flB) {
     const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
@@ -176,27 +176,27 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
       const S *pl = tile + q * TL::TYB * TL::TXB + b0;
       const S *own = tile + V::opp(q) * TL::TYB * TL::TXB + b0;
       const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
-      T acc = T(g.beta[q][0]) * T(load_h_s<S, float>(pl), load_h_s<S, float>(pl + DB));
+      T acc = T(wts.beta2[q][0]) * T(load_h_s<S, float>(pl), load_h_s<S, float>(pl + DB));
       if (sx != 0) {
         float vA = load_h_s<S, float>(pl - sx), vB = load_h_s<S, float>(pl + DB - sx);
         if (MASK && ((nbA >> (4 - sx)) & 1u)) vA = load_h_s<S, float>(own);
         if (MASK && ((nbB >> (4 - sx)) & 1u)) vB = load_h_s<S, float>(own + DB);
-        acc = fma(T(g.beta[q][1]), T(vA, vB), acc);
+        acc = fma(T(wts.beta2[q][1]), T(vA, vB), acc);
       }
       if (sy != 0) {
         float vA = load_h_s<S, float>(pl - sy * TL::TXB), vB = load_h_s<S, float>(pl + DB - sy * TL::TXB);
         if (MASK && ((nbA >> (4 - 3 * sy)) & 1u)) vA = load_h_s<S, float>(own);
         if (MASK && ((nbB >> (4 - 3 * sy)) & 1u)) vB = load_h_s<S, float>(own + DB);
-        acc = fma(T(g.beta[q][2]), T(vA, vB), acc);
+        acc = fma(T(wts.beta2[q][2]), T(vA, vB), acc);
       }
       if (sx != 0 && sy != 0) {
         float vA = load_h_s<S, float>(pl - sy * TL::TXB - sx), vB = load_h_s<S, float>(pl + DB - sy * TL::TXB - sx);
         if (MASK && ((nbA >> (4 - 3 * sy - sx)) & 1u)) vA = load_h_s<S, float>(own);
         if (MASK && ((nbB >> (4 - 3 * sy - sx)) & 1u)) vB = load_h_s<S, float>(own + DB);
-        acc = fma(T(g.beta[q][3]), T(vA, vB), acc);
+        acc = fma(T(wts.beta2[q][3]), T(vA, vB), acc);
       }
       // a lane without fluid (outside the lattice or solid) computes the rest state
-      h[q] = T(flA ? acc.v.x : 0.0f, flB ? acc.v.y : 0.0f);
+      h[q] = both ? acc : T(flA ? acc.v.x : 0.0f, flB ? acc.v.y : 0.0f);
     }
     const Mom<T> M = moments_of<T, T, VS, FORCE>(h);
     const Macro<T> m = cell_macro_pair<VS>(h, M, p.vmax2);
@@ -238,8 +238,8 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     for (int q = 0; q < Q; ++q) {
       rA = lcg_next(rA);
       rB = lcg_next(rB);
-      sA[q] = store_round<S>(flA ? hn[q].v.x : 0.0f, sr, rA);
-      sB[q] = store_round<S>(flB ? hn[q].v.y : 0.0f, sr, rB);
+      sA[q] = store_round<S>(both || flA ? hn[q].v.x : 0.0f, sr, rA);
+      sB[q] = store_round<S>(both || flB ? hn[q].v.y : 0.0f, sr, rB);
     }
   }
   {  // coalesced stores straight from registers (one 128-byte line per warp and plane)
@@ -353,7 +353,7 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
     const int x0 = ctx_ * TILE_X, y0 = cty * TILE_Y;
     ctx_ += stx; cty += sty;
     if (ctx_ >= ntx) { ctx_ -= ntx; ++cty; }
-    tile_cells<S, VS, MASK, FORCE, CPT>(smem + (k % NST) * stage_stride, ey_off, fout, x0, y0, tid, g, p, st,
+    tile_cells<S, VS, MASK, FORCE, CPT>(smem + (k % NST) * stage_stride, ey_off, fout, x0, y0, tid, g, g, p, st,
                                         staged, err);
     if (NST == 1) {  // the only stage is free once every thread is done with it
       __syncthreads();
@@ -371,6 +371,148 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
     // for this CTA's copies still in flight before returning
     atomicOr(err, ERR_TIMEOUT);
     for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The batched step: one persistent launch advances every lattice of a batch (an
+// ensemble of stirred realisations or impurity samples, uneven sizes) by one step.
+// The tiles of all members form one list (member m owns tiles tile0[m] .. tile0[m+1]);
+// CTAs walk it exactly as the single-lattice kernel walks one lattice, and take each
+// tile's member (binary search), buffers and TMA descriptors from the member table.
+// The per-member step is step0 + *bstep, so a captured CUDA graph of launches can
+// replay with the counter advanced by a one-thread kernel between launches.  All members
+// share the velocity set, storage type, dt/a, eta/s, eps0, the force shell and the
+// rounding mode; they differ in size, walls, solids, seeds and initial fields.
+// ---------------------------------------------------------------------------
+struct BatchDims {
+  int nx, ny, pitch, walls;
+  long long plane;
+  const uint16_t *nbmask;
+};
+
+__device__ __forceinline__ int find_member(const int *prefix, int n, int t) {
+  int lo = 0, hi = n;  // prefix[lo] <= t < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <typename R> __device__ __forceinline__ Stir<R> member_stir(const MemberDesc &d, long long n) {
+  Stir<R> s;
+  s.nrows = d.nrows; s.nmodes = d.nmodes; s.eyp = d.eyp;
+  s.G_cur = (const R4<R> *)d.G[n & 1];
+  s.EY = (const R2<R> *)d.EY;
+  s.G_next = (R4<R> *)d.G[(n + 1) & 1];
+  s.coef_next = (const R4<R> *)d.coef[(n + 1) & 1];
+  s.coef_new = (R4<R> *)d.coef[n & 1];
+  s.mode_kx = d.mode_kx; s.row_start = d.row_start;
+  s.seed = d.seed; s.step_new = n + 2; s.amp = 0.0;
+  return s;
+}
+
+template <typename S, int VS, bool MASK, bool FORCE, int CPT, int NST>
+__global__ void __launch_bounds__(NTHREADS / CPT)
+batch_step_kernel(const BatchTables bt, const Geometry<typename RealOf<S>::type> wts,
+                  const Physics<typename RealOf<S>::type> p0, const int srows_in, const double amp,
+                  const long long *__restrict__ bstep_ptr) {
+  using R = typename RealOf<S>::type;
+  using TL = Tile<S, VS>;
+  constexpr int NT = NTHREADS / CPT;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const bool staged = FORCE && srows_in > 0;
+  const int srows = staged ? srows_in : 0;
+  const int stage_stride = TL::stage(srows), ey_off = TL::IN_STRIDE + TL::g_bytes(srows);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * stage_stride);
+  const uint32_t stage_bytes = TL::IN_BYTES + srows * (TL::G_ROW + TL::EY_ROW);
+  const long long bstep = *bstep_ptr;
+
+  const int tid = threadIdx.x, wid = blockIdx.x, nworkers = gridDim.x;
+  const int ntiles = bt.tile0[bt.n];
+  const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int k) {  // stage the k-th tile of this CTA into stage k % NST
+    const int t = wid + k * nworkers;
+    const int m = find_member(bt.tile0, bt.n, t);
+    const MemberDesc &d = bt.mem[m];
+    const int lt = t - bt.tile0[m];
+    const int x0 = (lt % d.ntx) * TILE_X, y0 = (lt / d.ntx) * TILE_Y;
+    const long long n = d.step0 + bstep;
+    const int cur = (d.cur0 + (int)(bstep & 1)) & 1;
+    unsigned char *st0 = smem + (k % NST) * stage_stride;
+    uint64_t *b = &bar[k % NST];
+    mbar_expect_tx(b, stage_bytes);
+    tma_load_3d(st0, &d.tin[cur], b, x0 + TL::XOFF - TL::V, y0, 0);
+    if (staged) {
+      tma_load_2d(st0 + TL::IN_STRIDE, &d.tG[n & 1], b, 4 * x0, 0);
+      tma_load_2d(st0 + ey_off, &d.tEY, b, 2 * y0, 0);
+    }
+  };
+  if (tid == 0)
+    for (int k = 0; k < NST && k < my_tiles; ++k) issue(k);
+  bool alive = true;
+  {
+    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) alive = false;
+  }
+  for (int k = 0; alive && k < my_tiles; ++k) {
+    const int t = wid + k * nworkers;
+    const int m = find_member(bt.tile0, bt.n, t);
+    const MemberDesc &d = bt.mem[m];
+    const int lt = t - bt.tile0[m];
+    const int x0 = (lt % d.ntx) * TILE_X, y0 = (lt / d.ntx) * TILE_Y;
+    const long long n = d.step0 + bstep;
+    const int cur = (d.cur0 + (int)(bstep & 1)) & 1;
+    const BatchDims dims{d.nx, d.ny, d.pitch, d.walls, d.plane, d.nbmask};
+    Physics<R> p = p0;
+    p.round_key = d.round_key;
+    p.step = (unsigned)(n & 0xffffffffll);
+    const Stir<R> st = member_stir<R>(d, n);
+    tile_cells<S, VS, MASK, FORCE, CPT>(smem + (k % NST) * stage_stride, ey_off, (S *)d.f[cur ^ 1], x0, y0, tid,
+                                        dims, wts, p, st, staged, d.err);
+    if (NST == 1) {
+      __syncthreads();
+      if (tid == 0 && k + 1 < my_tiles) issue(k + 1);
+    }
+    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % NST], ((k + 1) / NST) & 1, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {
+      alive = false;
+      break;
+    }
+    if (NST >= 2 && tid == 0 && k + NST < my_tiles) issue(k + NST);
+  }
+  if (!alive && tid == 0) {
+    atomicOr(bt.mem[0].err, ERR_TIMEOUT);
+    for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
+  }
+  // The stirring work of the following steps, spread over all CTAs after their tiles:
+  // table entries of step n+1 and draws of step n+2 of every member.
+  if (FORCE && srows_in >= 0 && bt.mem[0].nrows) {
+    const long long entries = bt.entry0[bt.n];
+    for (long long e = wid + (long long)nworkers * tid; e < entries; e += (long long)nworkers * NT) {
+      int lo = 0, hi = bt.n;
+      while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (bt.entry0[mid] <= e) lo = mid; else hi = mid; }
+      const MemberDesc &d = bt.mem[lo];
+      const long long n = d.step0 + bstep;
+      const Stir<R> st = member_stir<R>(d, n);
+      const long long le = e - bt.entry0[lo];
+      st.G_next[le] = stir_row_entry<R>(st, st.coef_next, (int)(le / d.nx), (int)(le % d.nx), d.nx);
+    }
+    const int draws = bt.draw0[bt.n];
+    for (int e = wid + nworkers * tid; e < draws; e += nworkers * NT) {
+      const int m = find_member(bt.draw0, bt.n, e);
+      const MemberDesc &d = bt.mem[m];
+      Stir<R> st = member_stir<R>(d, d.step0 + bstep);
+      st.amp = amp;
+      stir_draws_part<R>(st, e - bt.draw0[m], st.nmodes);
+    }
   }
 }
 
@@ -527,7 +669,10 @@ template <typename R> static Geometry<R> to_geom(const HostGeom &h) {
   Geometry<R> g;
   g.nx = h.nx; g.ny = h.ny; g.pitch = h.pitch; g.plane = h.plane; g.walls = h.walls; g.nbmask = h.nbmask;
   for (int q = 0; q < 17; ++q)
-    for (int k = 0; k < 4; ++k) g.beta[q][k] = (R)h.beta[q][k];
+    for (int k = 0; k < 4; ++k) {
+      g.beta[q][k] = (R)h.beta[q][k];
+      g.beta2[q][k] = make_float2((float)h.beta[q][k], (float)h.beta[q][k]);
+    }
   return g;
 }
 
@@ -614,6 +759,71 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, cons
   return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stream);
 }
 
+template <typename S, int VS, bool MASK, bool FORCE, int NST>
+static cudaError_t launch_batch_v(const BatchTables &bt, const Geometry<typename RealOf<S>::type> &w,
+                                  const Physics<typename RealOf<S>::type> &p, int srows, double amp,
+                                  const long long *bstep, int grid_limit, int ntiles, cudaStream_t stream) {
+  using TL = Tile<S, VS>;
+  constexpr int CPT = sizeof(S) == 8 ? 1 : 2;
+  constexpr int NT = NTHREADS / CPT;
+  auto kern = batch_step_kernel<S, VS, MASK, FORCE, CPT, NST>;
+  const int smem = TL::smem(NST, FORCE ? srows : 0);
+  static int configured_dev = -1, configured_smem = -1, max_blocks = 0, sms = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev || configured_smem != smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+    configured_smem = smem;
+  }
+  int workers = max_blocks * sms;
+  if (grid_limit > 0 && grid_limit < workers) workers = grid_limit;
+  if (workers > ntiles) workers = ntiles;
+  if (workers < 1) workers = 1;
+  kern<<<workers, NT, smem, stream>>>(bt, w, p, FORCE ? srows : 0, amp, bstep);
+  return cudaGetLastError();
+}
+
+template <typename S, int NST>
+static cudaError_t launch_batch_n(int vset, const BatchTables &bt, const Geometry<typename RealOf<S>::type> &w,
+                                  const Physics<typename RealOf<S>::type> &p, int srows, double amp,
+                                  const long long *bstep, bool mask, bool force, int grid_limit, int ntiles,
+                                  cudaStream_t st) {
+  if (vset == 3) {
+    if (force) {
+      if (mask) return launch_batch_v<S, 3, true, true, NST>(bt, w, p, srows, amp, bstep, grid_limit, ntiles, st);
+      return launch_batch_v<S, 3, false, true, NST>(bt, w, p, srows, amp, bstep, grid_limit, ntiles, st);
+    }
+    if (mask) return launch_batch_v<S, 3, true, false, NST>(bt, w, p, srows, amp, bstep, grid_limit, ntiles, st);
+    return launch_batch_v<S, 3, false, false, NST>(bt, w, p, srows, amp, bstep, grid_limit, ntiles, st);
+  }
+  if (mask) return launch_batch_v<S, 2, true, false, NST>(bt, w, p, srows, amp, bstep, grid_limit, ntiles, st);
+  return launch_batch_v<S, 2, false, false, NST>(bt, w, p, srows, amp, bstep, grid_limit, ntiles, st);
+}
+
+template <typename S>
+static cudaError_t launch_batch_t(int vset, const BatchTables &bt, const HostGeom &hw, const HostPhys &hp, int srows,
+                                  double amp, const long long *bstep, bool mask, int stages, int grid_limit,
+                                  int ntiles, cudaStream_t stream) {
+  using R = typename RealOf<S>::type;
+  const Geometry<R> w = to_geom<R>(hw);
+  Physics<R> p;
+  p.omega0 = (R)hp.omega0; p.fpref = (R)hp.fpref; p.body_x = (R)hp.body_x; p.body_y = (R)hp.body_y;
+  p.vmax2 = (R)hp.vmax2;
+  p.stochastic = hp.stochastic;
+  p.round_key = 0;
+  p.step = 0;
+  const bool force = hp.has_force != 0;
+  if (stages == 1)
+    return launch_batch_n<S, 1>(vset, bt, w, p, srows, amp, bstep, mask, force, grid_limit, ntiles, stream);
+  return launch_batch_n<S, 2>(vset, bt, w, p, srows, amp, bstep, mask, force, grid_limit, ntiles, stream);
+}
+
 template <typename S>
 static cudaError_t launch_moments_t(int vset, const void *fin, const HostGeom &hg, double eps0, double *eps,
                                     double *ux, double *uy, double *partials, unsigned *err, dim3 block,
@@ -680,6 +890,11 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
                                 int grid_limit, int stages, cudaStream_t st) {                           \
     return launch_step_t<S>(vset, tin, tg, tey, fout, g, p, s, err, grid_limit, stages, st);            \
+  }                                                                                                      \
+  cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
+                                      int srows, double amp, const long long *bstep, bool mask, int stages, \
+                                      int grid_limit, int ntiles, cudaStream_t st) {                        \
+    return launch_batch_t<S>(vset, bt, w, p, srows, amp, bstep, mask, stages, grid_limit, ntiles, st);    \
   }                                                                                                      \
   cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
                                    double *ux, double *uy, double *part, unsigned *err, dim3 b,         \

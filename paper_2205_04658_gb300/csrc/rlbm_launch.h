@@ -2,6 +2,7 @@
 // each storage type (rlbm_kernels_*.cu).  Plain structs, no templates.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -36,11 +37,44 @@ struct HostStir {
   double amp;
 };
 
+// One lattice of a batch, as the batched step kernel sees it (device memory, written by
+// the host before the launches; 128-byte aligned so its tensor maps are 64-byte aligned).
+struct alignas(128) MemberDesc {
+  CUtensorMap tin[2];      // loads of population buffer 0 / 1
+  CUtensorMap tG[2];       // stirring rows of step parity 0 / 1
+  CUtensorMap tEY;
+  void *f[2];              // population buffers
+  const uint16_t *nbmask;  // NULL = no solid cells and no walls
+  int nx, ny, pitch, walls;
+  long long plane;
+  int cur0;                // buffer holding f*_n at batch step 0
+  int nrows, nmodes, eyp;
+  long long step0;         // the member's step index at batch step 0
+  const void *G[2], *EY, *coef[2];
+  const int *mode_kx, *row_start;
+  unsigned long long seed;
+  unsigned round_key;
+  unsigned *err;
+  int ntx;                 // tiles per row
+};
+
+// Prefix tables of a batch (device): tiles, stirring-table entries and draws per member.
+struct BatchTables {
+  const MemberDesc *mem;
+  const int *tile0;        // [n + 1]
+  const long long *entry0; // [n + 1]
+  const int *draw0;        // [n + 1]
+  int n;
+};
+
 #define RLBM_DECLARE_LAUNCHERS(SUF)                                                                      \
   cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
                                 int grid_limit, int stages, cudaStream_t st);                            \
   cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st);               \
+  cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
+                                      int srows, double amp, const long long *bstep, bool mask, int stages, \
+                                      int grid_limit, int ntiles, cudaStream_t st);                       \
   cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
                                    double *ux, double *uy, double *part, unsigned *err, dim3 b,         \
                                    cudaStream_t st);                                                     \
@@ -55,6 +89,7 @@ RLBM_DECLARE_LAUNCHERS(f16)
 RLBM_DECLARE_LAUNCHERS(bf16)
 
 // Reductions and spectrum (rlbm_aux.cu)
+cudaError_t launch_counter_inc(long long *counter, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st);
 cudaError_t launch_spectrum(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
                             const double2 *twy, double2 *z0, double2 *z1, double *bins, int nbins,

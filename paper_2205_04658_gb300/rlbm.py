@@ -62,6 +62,12 @@ def lib():
             "rlbm_set_launch": (c_i32, [P, c_i32, c_i32]),
             "rlbm_autotune": (c_i32, [P, c_i32, dp]),
             "rlbm_velocity_classes": (c_i32, [c_i32, dp]),
+            "rlbm_batch_query_workspace": (c_i32, [c_i32, ctypes.POINTER(c_sz)]),
+            "rlbm_batch_init": (c_i32, [ctypes.POINTER(P), c_i32, P, c_sz, P, ctypes.POINTER(P)]),
+            "rlbm_batch_set_launch": (c_i32, [P, c_i32, c_i32]),
+            "rlbm_batch_step": (c_i32, [P, c_i64]),
+            "rlbm_batch_last_error": (ctypes.c_char_p, [P]),
+            "rlbm_batch_free": (None, [P]),
             "rlbm_spectrum_noalloc": (c_i32, [P, P, c_i32, c_i32, c_i32, P, P]),
             "rlbm_sync": (c_i32, [P]),
             "rlbm_current_step": (c_i64, [P]),
@@ -258,6 +264,69 @@ class Lattice:
         if getattr(self, "ctx", None) is not None:
             rlbm_free(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----- batches -----------------------------------------------------------------
+def _bcheck(status, b=None):
+    if status != RLBM_OK:
+        raise RlbmError(status, lib().rlbm_batch_last_error(b).decode())
+
+
+def rlbm_batch_query_workspace(nmembers):
+    n = ctypes.c_size_t(0)
+    _bcheck(lib().rlbm_batch_query_workspace(int(nmembers), ctypes.byref(n)))
+    return n.value
+
+
+def rlbm_batch_init(ctxs, dev_workspace, nbytes, cuda_stream):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    b = ctypes.c_void_p()
+    _bcheck(lib().rlbm_batch_init(arr, len(ctxs), ctypes.c_void_p(dev_workspace), nbytes,
+                                  ctypes.c_void_p(cuda_stream), ctypes.byref(b)))
+    return b
+
+
+def rlbm_batch_set_launch(b, ctas, stages=0):
+    _bcheck(lib().rlbm_batch_set_launch(b, int(ctas), int(stages)), b)
+
+
+def rlbm_batch_step(b, nsteps):
+    _bcheck(lib().rlbm_batch_step(b, int(nsteps)), b)
+
+
+def rlbm_batch_free(b):
+    lib().rlbm_batch_free(b)
+
+
+class Batch:
+    """Lattices advanced together, one persistent launch per step.  The lattices should
+    live on the batch's stream (a non-default stream enables CUDA-graph replay)."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+        self.lattices = list(lattices)
+        self.stream = stream if stream is not None else self.lattices[0].stream
+        self.nbytes = rlbm_batch_query_workspace(len(self.lattices))
+        self._ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.b = rlbm_batch_init([l.ctx for l in self.lattices], ptr, self.nbytes, self.stream.cuda_stream)
+
+    def step(self, n=1):
+        rlbm_batch_step(self.b, n)
+
+    def set_launch(self, ctas, stages=0):
+        rlbm_batch_set_launch(self.b, ctas, stages)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            rlbm_batch_free(self.b)
+            self.b = None
 
     def __del__(self):
         try:

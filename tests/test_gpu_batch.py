@@ -1,0 +1,79 @@
+"""The batched form: many lattices of uneven sizes advanced by one persistent launch
+per step (CUDA-graph replay for whole chunks) must give exactly the results of
+stepping each lattice on its own."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2205_04658_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_04658_gb300 import build as B
+    from paper_2205_04658_gb300 import rlbm
+    if not os.path.exists(rlbm.LIB_PATH):
+        B.build()
+    return rlbm
+
+
+MEMBERS = [  # (nx, ny, seed, walls/discs)
+    (64, 48, 11, False), (96, 80, 12, False), (40, 40, 13, False), (128, 64, 14, True), (72, 56, 15, False),
+]
+
+
+def make(R, precision, stream, nx, ny, seed, solid):
+    kw = dict(precision=precision, eta_over_s=0.05, kmin=2, kmax=5, force_amp=1e-3, seed=seed)
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=seed, eps_amp=0.02, u_amp=0.02)
+    kw.update(init_eps=e, init_ux=ux, init_uy=uy)
+    if solid:
+        mask, _ = inputs.disc_mask(nx, ny, radius=3, fraction=0.05, seed=seed, walls_y=True)
+        kw.update(walls_y=1, solid=mask)
+    return R.Lattice(nx, ny, stream=stream, **kw)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16", "f64"])
+def test_batch_equals_members_stepped_alone(R, precision):
+    import torch
+    stream = torch.cuda.Stream()
+    alone, batched = [], []
+    for (nx, ny, seed, solid) in MEMBERS:
+        alone.append(make(R, precision, stream, nx, ny, seed, solid))
+        batched.append(make(R, precision, stream, nx, ny, seed, solid))
+    # members need not be at the same step: advance one of them first, in both sets
+    alone[2].step(5)
+    batched[2].step(5)
+    nsteps = 70  # one captured chunk of 64 steps + 6 direct launches
+    for lat in alone:
+        lat.step(nsteps)
+    b = R.Batch(batched, stream=stream)
+    b.step(nsteps)
+    b.step(3)
+    for lat in alone:
+        lat.step(3)
+    for a, c in zip(alone, batched):
+        assert a.current_step == c.current_step
+        ma, mc = a.moments(), c.moments()
+        for k in range(3):
+            assert np.array_equal(ma[k], mc[k])
+    b.close()
+    for lat in alone + batched:
+        lat.close()
+
+
+def test_batch_rejects_mismatched_physics(R):
+    import torch
+    stream = torch.cuda.Stream()
+    a = R.Lattice(32, 32, stream=stream, precision="f32", eta_over_s=0.05)
+    c = R.Lattice(32, 32, stream=stream, precision="f32", eta_over_s=0.06)
+    with pytest.raises(R.RlbmError) as e:
+        R.Batch([a, c], stream=stream)
+    assert e.value.status == R.RLBM_E_INVAL
+    a.close()
+    c.close()
