@@ -365,7 +365,7 @@ def spectrum(ux, uy, nbins, solid=None):
 # --------------------------------------------------------------------------
 DEFAULTS = dict(walls_y=0, vset=3, a=0.1, dt=0.05, eta_over_s=0.1, eps0=1.0,
                 body_force=(0.0, 0.0), kmin=0, kmax=0, force_amp=0.0, seed=0,
-                solid=None, init_eps=None, init_ux=None, init_uy=None)
+                solid=None, init_eps=None, init_ux=None, init_uy=None, mode_scale=None)
 
 
 class Window:
@@ -433,6 +433,8 @@ class Oracle:
         F[..., 1] += c["body_force"][1]
         if self.modes:
             a, phi, psi = mode_draws(c["seed"], n, len(self.modes), c["force_amp"])
+            if c["mode_scale"] is not None:  # amplitude multipliers sigma_m (parameters of the adjoint)
+                a = a * np.asarray(c["mode_scale"], np.float64)
             F += stirring_force(self.win.X, self.win.Y, c["nx"], c["ny"], self.modes, a, phi, psi)
         return F
 
