@@ -180,8 +180,8 @@ RLBM_API int32_t rlbm_velocity_classes(int32_t vset, double *out);
 
 /* ---- Batches: many lattices advanced by one persistent launch per step -------------
  * An ensemble (stirred realisations, impurity samples) of uneven sizes steps as one job:
- * each step is a single launch of the fused kernel over the tiles of all members
- * (north-star "batching" form), and whole chunks of steps replay a captured CUDA graph.
+ * each step is a single launch of the fused kernel over the tiles of all members, and
+ * whole chunks of steps replay a captured CUDA graph.
  * Members are ordinary contexts (rlbm_init) that share the velocity set, storage type,
  * a, dt, eta/s, eps0, body force, stirring shell and amplitude, rounding and
  * fp64_landau_vmax; they may differ in size, walls, solids, seeds and initial fields,
@@ -213,6 +213,40 @@ RLBM_API const char *rlbm_batch_last_error(const rlbm_batch *b);
 
 /* Release the batch (not its workspace, not the members). */
 RLBM_API void rlbm_batch_free(rlbm_batch *b);
+
+/* ---- Stirring multipliers and the adjoint ------------------------------------------
+ * The stirring of Sec. "The Driving Term" draws, at every step n, a Gaussian amplitude a_m
+ * for each mode m of the shell.  Multipliers sigma_m (default 1) scale those amplitudes:
+ * the force becomes sum_m sigma_m a_m (cos psi_m, sin psi_m) cos(k_m.x + phi_m).
+ * The paper has no counterpart; they are the parameters of the gradient below. */
+
+/* Number of stirring modes of the context's shell (0 without stirring); -1 if ctx is NULL. */
+RLBM_API int32_t rlbm_num_modes(const rlbm_ctx *ctx);
+
+/* Set sigma_m (host array of rlbm_num_modes(ctx) finite values, copied) for the current
+ * and all later steps.  Syncs.  E_INVAL on a wrong count or a non-finite value. */
+RLBM_API rlbm_status rlbm_set_mode_scale(rlbm_ctx *ctx, const double *sigma, int32_t nmodes);
+
+/* Objective (no counterpart in the paper): the time average over the states after steps
+ * s0+1 .. s0+nsteps (s0 = rlbm_current_step on entry) of the fluid-cell mean of
+ * |v|^2 / 2, v = u^i / u^0 from Landau matching,
+ *     J = (1 / nsteps) sum_n (1 / N_fluid) sum_x |v_n(x)|^2 / 2.
+ * rlbm_gradient runs the nsteps forward steps (the context ends at s0 + nsteps, exactly as
+ * after rlbm_step(ctx, nsteps)), keeping the post-collision state every `segment` steps
+ * (0: ceil(sqrt(nsteps))), then the hand-written adjoint backwards, recomputing each
+ * segment from its checkpoint: about 2 sqrt(nsteps) states of memory and one extra
+ * forward pass.  It returns J and dJ/dsigma_m (host, rlbm_num_modes values; may be NULL),
+ * dJ/d(eta/s) (host, 1; may be NULL) and dJ/dF_body (host, 2; may be NULL; zero for the
+ * eight-direction set, which has no force term), evaluated at
+ * the current sigma, eta/s and body force.  FP64 and FP32 storage only (E_INVAL for the
+ * 16-bit forms).  Syncs.
+ * Workspace: rlbm_gradient_query_workspace bytes of caller-owned device memory, 256-byte
+ * aligned, used only during the call.  Device errors of the run are latched as usual. */
+RLBM_API rlbm_status rlbm_gradient_query_workspace(const rlbm_ctx *ctx, int64_t nsteps, int32_t segment,
+                                                   size_t *bytes);
+RLBM_API rlbm_status rlbm_gradient(rlbm_ctx *ctx, int64_t nsteps, int32_t segment, void *dev_workspace,
+                                   size_t bytes, double *J, double *grad_sigma, double *grad_eta_over_s,
+                                   double *grad_body_force);
 
 /* Wait for queued work and report latched device errors. */
 RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);

@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 SOURCES = ["rlbm_kernels_f64.cu", "rlbm_kernels_f32.cu", "rlbm_kernels_f16.cu", "rlbm_kernels_bf16.cu",
-           "rlbm_aux.cu", "rlbm_capi.cu", "rlbm_noalloc.cu"]
+           "rlbm_aux.cu", "rlbm_capi.cu", "rlbm_noalloc.cu", "rlbm_adjoint.cu"]
 
 
 def nvcc():

@@ -1,0 +1,427 @@
+// Adjoint of the fused step: the gradient of a kinetic-energy objective of a stirred
+// run with respect to the per-mode stirring multipliers sigma_m, eta/s and the body
+// force, by reverse-mode differentiation written out by hand.
+//
+// With the post-collision buffer B_{n-1} of the forward run, S_n = P B_{n-1} (pull
+// streaming) and B_n = C_n(S_n) (moments, Landau matching, equilibrium, Anderson-Witting
+// relaxation and projected force of one cell), the adjoint kappa_n = dJ/dS_n obeys
+//
+//   kappa_n = dj_n/dS_n + (dC_n/dS)^T (P^T kappa_{n+1}),
+//
+// and every step adds (dC_n/dtheta)^T (P^T kappa_{n+1}) to the parameter gradients.
+// One launch per step gathers S_n (forward pull of B_{n-1}) and P^T kappa_{n+1} (the
+// transposed pull: reversed offsets, same bilinear weights, and at a solid corner the
+// cell's own reversed plane, so it has the form of the forward pull), runs the cell's
+// reverse and writes kappa_n.  Landau matching R(v) = m - T v - (T^00 - m.v) v = 0 is
+// differentiated implicitly: the adjoint w solves (dR/dv)^T w = vbar and the moments
+// receive -(dR/dp)^T w.
+#include "rlbm_kernels.cuh"
+
+namespace rlbm {
+
+template <typename R> struct AdjStir {
+  int nrows;
+  const R4<R> *G;    // [nrows][nx] table of the step (Gx.re, Gx.im, Gy.re, Gy.im)
+  const R2<R> *EY;   // [nrows][eyp] exp(i 2 pi k_y y / ny)
+  int eyp;
+};
+
+// lam_q(x) = sum_c beta_{q,c} kappa_q(x + o_c), o_c in {(0,0), (sx,0), (0,sy), (sx,sy)}:
+// the transpose of `pull_global`; a solid source corner of the forward pull (the
+// neighbour x + o_c here) takes kappa_{opp(q)}(x) instead.
+template <typename T, int VS, bool MASK>
+__device__ __forceinline__ void pull_transpose(const T *__restrict__ kin, const Geometry<T> &g, int x, int y,
+                                               unsigned nb, T lam[VSet<VS>::Q]) {
+  constexpr int Q = VSet<VS>::Q;
+  const long long o = (long long)(y + 1) * g.pitch + x + PadLayout<T>::XOFF;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const T *pl = kin + q * g.plane + o;
+    const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
+    T acc = g.beta[q][0] * __ldg(pl);
+    const T own = __ldg(kin + VSet<VS>::opp(q) * g.plane + o);
+    if (sx != 0) acc += g.beta[q][1] * ((MASK && ((nb >> (4 + sx)) & 1u)) ? own : __ldg(pl + sx));
+    if (sy != 0) acc += g.beta[q][2] * ((MASK && ((nb >> (4 + 3 * sy)) & 1u)) ? own : __ldg(pl + (long long)sy * g.pitch));
+    if (sx != 0 && sy != 0)
+      acc += g.beta[q][3] * ((MASK && ((nb >> (4 + 3 * sy + sx)) & 1u)) ? own : __ldg(pl + (long long)sy * g.pitch + sx));
+    lam[q] = acc;
+  }
+}
+
+// Reverse of one cell's collision and force (coll_coeffs / collide_all) and of its
+// objective term cj |v|^2 / 2, given the cell's post-streaming deviations h, their
+// moments M and Landau solution m, and the adjoint lam of the cell's output.  Returns
+// the adjoint of h in kap, d/d(ln omega0) in gom and the adjoint of F in gFx, gFy.
+template <typename R, int VS, bool FORCE>
+__device__ __forceinline__ void cell_adjoint(const R h[VSet<VS>::Q], const R lam[VSet<VS>::Q], const Mom<R> &M,
+                                             const Macro<R> &m, R omega0, R fpref, R Fx, R Fy, R cj,
+                                             R kap[VSet<VS>::Q], R &gom, R &gFx, R &gFy) {
+  using V = VSet<VS>;
+  constexpr int Q = V::Q;
+  const R epsh = R(1) + m.eps_m1;
+  const R om = VS == 3 ? omega0 * FM<R>::qroot(epsh) : omega0 * FM<R>::croot(epsh);
+  const R u0 = m.u0, ux = m.ux, uy = m.uy;
+  const R u2 = ux * ux + uy * uy;
+  const R ca = R(V::CA) * epsh * u0, cb = R(V::CB) * epsh, cc = m.eps_m1 - R(V::CC) * epsh * u2;
+  const R p1 = om * (u0 * ca - cc), p2 = om * (u0 * cb - ca), p3 = -om * cb;
+  const R k0 = R(1) - om * u0;
+
+  // h*_q = h_q (k0 + om t_q) + p0 + p1 t + p2 t^2 + p3 t^3 + S_q,  t_q = u . v_q
+  R om_b = R(0), u0_b = R(0), ux_b = R(0), uy_b = R(0);
+  R P0 = R(0), P1 = R(0), P2 = R(0), P3 = R(0);
+  R S1x = R(0), S1y = R(0), Sxx = R(0), Sxy = R(0), Syy = R(0), Szz = R(0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const R vx = R(V::vx(q)), vy = R(V::vy(q));
+    const R t = ux * vx + uy * vy;
+    const R lq = lam[q];
+    kap[q] = lq * (k0 + om * t);
+    const R lh = lq * h[q];
+    om_b += lh * (t - u0);
+    u0_b -= om * lh;
+    const R tb = om * lh + lq * (p1 + t * (R(2) * p2 + R(3) * p3 * t));
+    ux_b += tb * vx;
+    uy_b += tb * vy;
+    P0 += lq;
+    P1 += lq * t;
+    P2 += lq * t * t;
+    P3 += lq * t * t * t;
+    if (FORCE) {
+      S1x += lq * vx;
+      S1y += lq * vy;
+      Sxx += lq * vx * vx;
+      Sxy += lq * vx * vy;
+      Syy += lq * vy * vy;
+      Szz += lq * R(V::vz2(q));
+    }
+  }
+  // p0 = om u0 cc, p1 = om (u0 ca - cc), p2 = om (u0 cb - ca), p3 = -om cb
+  om_b += P0 * u0 * cc + P1 * (u0 * ca - cc) + P2 * (u0 * cb - ca) - P3 * cb;
+  u0_b += om * (P0 * cc + P1 * ca + P2 * cb);
+  const R cc_b = om * (P0 * u0 - P1);
+  const R ca_b = om * (P1 * u0 - P2);
+  const R cb_b = om * (P2 * u0 - P3);
+  // ca = CA eps^ u0, cb = CB eps^, cc = (eps^ - 1) - CC eps^ |u|^2
+  R epsh_b = ca_b * R(V::CA) * u0 + cb_b * R(V::CB) + cc_b * (R(1) - R(V::CC) * u2);
+  u0_b += ca_b * R(V::CA) * epsh;
+  ux_b -= cc_b * R(2 * V::CC) * epsh * ux;
+  uy_b -= cc_b * R(2 * V::CC) * epsh * uy;
+  // om = omega0 eps^(1/4) (D_p = 3) or omega0 eps^(1/3) (D_p = 2)
+  epsh_b += om_b * om / (R(VS == 3 ? 4 : 3) * epsh);
+  gom = om_b * om;
+
+  R e_b = R(0), mx_b = R(0), my_b = R(0), txx_b = R(0), txy_b = R(0), tyy_b = R(0);
+  R wxxx_b = R(0), wxxy_b = R(0), wxyy_b = R(0), wyyy_b = R(0);
+  gFx = R(0);
+  gFy = R(0);
+  if (FORCE) {
+    // s0 = fpref F.m / 4;  s1 = -fpref (1 + e) F / 2;  quadratic form with B and F m^T
+    const R M0 = R(1) + M.e;
+    const R f54 = R(1.25) * fpref;
+    R FM1_b = R(0.25) * fpref * P0;
+    e_b += R(-0.5) * fpref * (Fx * S1x + Fy * S1y);
+    gFx += R(-0.5) * fpref * M0 * S1x;
+    gFy += R(-0.5) * fpref * M0 * S1y;
+    R Bxx_b = f54 * Sxx, Bxy_b = R(2) * f54 * Sxy, Byy_b = f54 * Syy;
+    gFx -= R(2) * f54 * (M.mx * Sxx + M.my * Sxy);
+    gFy -= R(2) * f54 * (M.mx * Sxy + M.my * Syy);
+    mx_b -= R(2) * f54 * (Fx * Sxx + Fy * Sxy);
+    my_b -= R(2) * f54 * (Fx * Sxy + Fy * Syy);
+    // szz = f54 Bzz, Bzz = F.m - Bxx - Byy
+    const R Bzz_b = f54 * Szz;
+    FM1_b += Bzz_b;
+    Bxx_b -= Bzz_b;
+    Byy_b -= Bzz_b;
+    // Bxx = Fx wxxx + Fy wxxy, Bxy = Fx wxxy + Fy wxyy, Byy = Fx wxyy + Fy wyyy
+    gFx += Bxx_b * M.wxxx + Bxy_b * M.wxxy + Byy_b * M.wxyy;
+    gFy += Bxx_b * M.wxxy + Bxy_b * M.wxyy + Byy_b * M.wyyy;
+    wxxx_b += Bxx_b * Fx;
+    wxxy_b += Bxx_b * Fy + Bxy_b * Fx;
+    wxyy_b += Bxy_b * Fy + Byy_b * Fx;
+    wyyy_b += Byy_b * Fy;
+    gFx += FM1_b * M.mx;
+    gFy += FM1_b * M.my;
+    mx_b += FM1_b * Fx;
+    my_b += FM1_b * Fy;
+  }
+
+  // objective and the macroscopic map: u0 = gamma, u = gamma v, eps^ = 1 + e - m.v
+  const R vx = m.vx, vy = m.vy;
+  R vx_b = cj * vx, vy_b = cj * vy;
+  const R gam = u0;
+  const R gam_b = u0_b + ux_b * vx + uy_b * vy;
+  vx_b += ux_b * gam;
+  vy_b += uy_b * gam;
+  const R g3 = gam * gam * gam;
+  vx_b += gam_b * g3 * vx;
+  vy_b += gam_b * g3 * vy;
+  e_b += epsh_b;
+  mx_b -= epsh_b * vx;
+  my_b -= epsh_b * vy;
+  vx_b -= epsh_b * M.mx;
+  vy_b -= epsh_b * M.my;
+
+  // Landau: J = dR/dv = -T + v m^T - eps^ I;  J^T w = vbar;  pbar -= (dR/dp)^T w
+  constexpr R dinv = R(1.0 / V::DP);
+  const R Txx = dinv + M.txx, Txy = M.txy, Tyy = dinv + M.tyy;
+  const R jxx = -Txx + vx * M.mx - epsh, jxy = -Txy + vx * M.my;
+  const R jyx = -Txy + vy * M.mx, jyy = -Tyy + vy * M.my - epsh;
+  const R idet = R(1) / (jxx * jyy - jxy * jyx);
+  const R wx = (jyy * vx_b - jyx * vy_b) * idet;
+  const R wy = (jxx * vy_b - jxy * vx_b) * idet;
+  const R wv = wx * vx + wy * vy;
+  e_b += wv;
+  mx_b -= wx + vx * wv;
+  my_b -= wy + vy * wv;
+  txx_b += wx * vx;
+  tyy_b += wy * vy;
+  txy_b += wx * vy + wy * vx;
+
+  // moments: e = sum w h, m = sum w h v, t = sum w h v v, third moments sum w h v v v
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const double qx = V::vx(q), qy = V::vy(q);
+    R a = e_b;
+    if (qx != 0.0) a += mx_b * R(qx) + txx_b * R(qx * qx);
+    if (qy != 0.0) a += my_b * R(qy) + tyy_b * R(qy * qy);
+    if (qx != 0.0 && qy != 0.0) a += txy_b * R(qx * qy);
+    if (FORCE) {
+      if (qx != 0.0) a += wxxx_b * R(qx * qx * qx);
+      if (qx != 0.0 && qy != 0.0) a += wxxy_b * R(qx * qx * qy) + wxyy_b * R(qx * qy * qy);
+      if (qy != 0.0) a += wyyy_b * R(qy * qy * qy);
+    }
+    kap[q] += R(V::w(q)) * a;
+  }
+}
+
+// One adjoint step over the lattice: 32 x 8 cells per block, one cell per thread.
+//   B     post-collision buffer B_{n-1} of the forward run (storage type S)
+//   kin   kappa_{n+1} (unused when LAM is false: the last state, objective only)
+//   kout  kappa_n; ghost cells are written like the forward's (periodic copies)
+//   cj    objective weight of S_n (1 / (N N_fluid), or 0 for the first state)
+//   acc   per-block FP64 sums, accumulated over steps: d/d(ln omega0), F adjoint x, y, J
+//   zpart per block row and k_y row r: sum over the block's 8 rows of gF(x, y) EY_r(y)
+template <typename S, int VS, bool MASK, bool FORCE, bool LAM>
+__global__ void __launch_bounds__(256)
+adjoint_kernel(const S *__restrict__ B, const typename RealOf<S>::type *__restrict__ kin,
+               typename RealOf<S>::type *__restrict__ kout, const Geometry<typename RealOf<S>::type> g,
+               const Physics<typename RealOf<S>::type> p, const AdjStir<typename RealOf<S>::type> st,
+               const typename RealOf<S>::type cj, double *__restrict__ acc, R4<typename RealOf<S>::type> *__restrict__ zpart,
+               unsigned *__restrict__ err) {
+  using R = typename RealOf<S>::type;
+  constexpr int Q = VSet<VS>::Q;
+  const int lx = threadIdx.x, ly = threadIdx.y;
+  const int x = blockIdx.x * 32 + lx, y = blockIdx.y * 8 + ly;
+  const bool inside = x < g.nx && y < g.ny;
+  unsigned nb = 0;
+  if (MASK && inside) nb = g.nbmask[(long long)y * g.nx + x];
+  const bool fluid = inside && !(MASK && (nb & 16u));
+  R kap[Q];
+  R gom = R(0), gFx = R(0), gFy = R(0), jv = R(0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) kap[q] = R(0);
+  if (fluid) {
+    R h[Q], lam[Q];
+    pull_global<S, R, VS, MASK>(B, g, x, y, nb, h);
+    if (LAM) {
+      pull_transpose<R, VS, MASK>(kin, g, x, y, nb, lam);
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) lam[q] = R(0);
+    }
+    const Mom<R> M = moments_of<R, R, VS, FORCE>(h);
+    const Macro<R> m = cell_macro<R, VS>(h, M, p.vmax2);
+    if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+    R Fx = p.body_x, Fy = p.body_y;
+    if (FORCE) {
+      for (int r = 0; r < st.nrows; ++r) {
+        const R4<R> G = st.G[(long long)r * g.nx + x];
+        const R2<R> E = st.EY[(long long)r * st.eyp + y];
+        Fx = fma(G.x, E.x, fma(-G.y, E.y, Fx));
+        Fy = fma(G.z, E.x, fma(-G.w, E.y, Fy));
+      }
+    }
+    cell_adjoint<R, VS, FORCE>(h, lam, M, m, p.omega0, p.fpref, Fx, Fy, cj, kap, gom, gFx, gFy);
+    jv = cj * R(0.5) * (m.vx * m.vx + m.vy * m.vy);
+  }
+  if (inside) {
+    R *o = kout + (long long)(y + 1) * g.pitch + x + PadLayout<R>::XOFF;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) o[q * g.plane] = kap[q];
+    const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
+    const int gyv = g.walls ? INT_MIN : (y == 0 ? g.ny : (y == g.ny - 1 ? -1 : INT_MIN));
+    if (gxv != INT_MIN || gyv != INT_MIN) {
+      const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
+      for (int a = 0; a < 3; ++a) {
+        if (px[a] == INT_MIN || py[a] == INT_MIN) continue;
+        R *d = kout + (long long)(py[a] + 1) * g.pitch + px[a] + PadLayout<R>::XOFF;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) d[q * g.plane] = kap[q];
+      }
+    }
+  }
+  // projections of the force adjoint on the k_y rows of the stirring tables
+  if (FORCE && st.nrows > 0) {
+    __shared__ R2<R> sF[8][32];
+    sF[ly][lx] = R2<R>{gFx, gFy};
+    __syncthreads();
+    for (int r = ly; r < st.nrows; r += 8) {
+      R4<R> z{R(0), R(0), R(0), R(0)};
+      for (int j = 0; j < 8; ++j) {
+        const int yy = blockIdx.y * 8 + j;
+        if (yy >= g.ny) break;
+        const R2<R> E = st.EY[(long long)r * st.eyp + yy];
+        const R2<R> F = sF[j][lx];
+        z.x += F.x * E.x;
+        z.y += F.x * E.y;
+        z.z += F.y * E.x;
+        z.w += F.y * E.y;
+      }
+      if (x < g.nx) zpart[((long long)blockIdx.y * st.nrows + r) * g.nx + x] = z;
+    }
+  }
+  // block sums (fixed order) added to this block's accumulators
+  double v[4] = {(double)gom, (double)gFx, (double)gFy, (double)jv};
+  __shared__ double red[8][4];
+  const int tid = ly * 32 + lx, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (tid < 4) {
+    double s = 0.0;
+    for (int w8 = 0; w8 < 8; ++w8) s += red[w8][tid];
+    acc[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] += s;
+  }
+}
+
+// zsum[r][x] = sum over block rows of zpart (FP64), the k_y-row transform of the force
+// adjoint at column x.
+template <typename R>
+__global__ void zsum_kernel(const R4<R> *__restrict__ zpart, int nby, int nrows, int nx, R4<double> *__restrict__ zsum) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (x >= nx) return;
+  R4<double> s{0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < nby; ++b) {
+    const R4<R> z = zpart[((long long)b * nrows + r) * nx + x];
+    s.x += (double)z.x; s.y += (double)z.y; s.z += (double)z.z; s.w += (double)z.w;
+  }
+  zsum[(long long)r * nx + x] = s;
+}
+
+// gsig[m] += d/d sigma_m of sum_x gF(x) . F(x) for the draws of step n:
+//   F(x, y) = sum_m sigma_m Re[(cx_m, cy_m) exp(i 2 pi (k_x x / nx + k_y y / ny))],
+// so the derivative is Re[cx_m W_x] + Re[cy_m W_y] with W = sum_x exp(i 2 pi k_x x / nx) zsum_r(x).
+template <typename R>
+__global__ void mode_grad_kernel(const R4<double> *__restrict__ zsum, const double2 *__restrict__ tw, const int *__restrict__ mode_kx,
+                                 const int *__restrict__ row_start, int nx, unsigned long long seed, long long n,
+                                 double amp, double *__restrict__ gsig) {
+  const int mo = blockIdx.x;
+  int r = 0;
+  while (row_start[r + 1] <= mo) ++r;
+  const int kx = mode_kx[mo];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    int j = (kx * x) % nx;
+    if (j < 0) j += nx;
+    const double2 t = tw[j];
+    const R4<double> z = zsum[(long long)r * nx + x];
+    a[0] += t.x * z.x - t.y * z.y;
+    a[1] += t.x * z.y + t.y * z.x;
+    a[2] += t.x * z.z - t.y * z.w;
+    a[3] += t.x * z.w + t.y * z.z;
+  }
+  __shared__ double red[8][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    for (int off = 16; off > 0; off >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], off);
+    if (lane == 0) red[warp][k] = a[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double W[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8)
+      for (int k = 0; k < 4; ++k) W[k] += red[w8][k];
+    double c[4];
+    if constexpr (sizeof(R) == 8) {
+      stir_draw(seed, n, mo, amp, c);
+    } else {
+      float cf[4];
+      stir_draw_f32(seed, n, mo, (float)amp, cf);
+      for (int k = 0; k < 4; ++k) c[k] = (double)cf[k];
+    }
+    gsig[mo] += c[0] * W[0] - c[1] * W[1] + c[2] * W[2] - c[3] * W[3];
+  }
+}
+
+// exp(+2 pi i t / n) for t < n
+__global__ void adj_twiddle_kernel(double2 *tw, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double s, c;
+  sincospi(2.0 * t / n, &s, &c);
+  tw[t] = make_double2(c, s);
+}
+
+template <typename S, int VS, bool MASK, bool FORCE>
+static cudaError_t launch_adjoint_v(const AdjointArgs &a, const Geometry<typename RealOf<S>::type> &g,
+                                    const Physics<typename RealOf<S>::type> &p, cudaStream_t st) {
+  using R = typename RealOf<S>::type;
+  AdjStir<R> s;
+  s.nrows = FORCE ? a.nrows : 0;
+  s.G = (const R4<R> *)a.G;
+  s.EY = (const R2<R> *)a.EY;
+  s.eyp = a.eyp;
+  const dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8);
+  if (a.kin)
+    adjoint_kernel<S, VS, MASK, FORCE, true><<<grid, block, 0, st>>>((const S *)a.B, (const R *)a.kin, (R *)a.kout, g, p, s,
+                                                                    (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
+  else
+    adjoint_kernel<S, VS, MASK, FORCE, false><<<grid, block, 0, st>>>((const S *)a.B, nullptr, (R *)a.kout, g, p, s,
+                                                                     (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !FORCE || a.nrows == 0 || !a.kin) return e;
+  zsum_kernel<R><<<dim3((g.nx + 255) / 256, a.nrows), 256, 0, st>>>((const R4<R> *)a.zpart, (int)grid.y, a.nrows, g.nx,
+                                                                   (R4<double> *)a.zsum);
+  mode_grad_kernel<R><<<a.nmodes, 256, 0, st>>>((const R4<double> *)a.zsum, (const double2 *)a.tw, a.mode_kx, a.row_start,
+                                                g.nx, a.seed, a.step, a.amp, a.gsig);
+  return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t launch_adjoint_t(int vset, const AdjointArgs &a, const HostGeom &hg, const HostPhys &hp,
+                                    cudaStream_t st) {
+  using R = typename RealOf<S>::type;
+  const Geometry<R> g = to_geom<R>(hg);
+  Physics<R> p{};
+  p.omega0 = (R)hp.omega0; p.fpref = (R)hp.fpref; p.body_x = (R)hp.body_x; p.body_y = (R)hp.body_y;
+  p.vmax2 = (R)hp.vmax2;
+  const bool mask = hg.nbmask != nullptr, force = hp.has_force != 0;
+  if (vset == 3) {
+    if (force) {
+      if (mask) return launch_adjoint_v<S, 3, true, true>(a, g, p, st);
+      return launch_adjoint_v<S, 3, false, true>(a, g, p, st);
+    }
+    if (mask) return launch_adjoint_v<S, 3, true, false>(a, g, p, st);
+    return launch_adjoint_v<S, 3, false, false>(a, g, p, st);
+  }
+  if (mask) return launch_adjoint_v<S, 2, true, false>(a, g, p, st);
+  return launch_adjoint_v<S, 2, false, false>(a, g, p, st);
+}
+
+cudaError_t launch_adjoint_f64(int vset, const AdjointArgs &a, const HostGeom &g, const HostPhys &p, cudaStream_t st) {
+  return launch_adjoint_t<double>(vset, a, g, p, st);
+}
+cudaError_t launch_adjoint_f32(int vset, const AdjointArgs &a, const HostGeom &g, const HostPhys &p, cudaStream_t st) {
+  return launch_adjoint_t<float>(vset, a, g, p, st);
+}
+cudaError_t launch_adj_twiddles(double2 *tw, int n, cudaStream_t st) {
+  adj_twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(tw, n);
+  return cudaGetLastError();
+}
+
+}  // namespace rlbm

@@ -59,7 +59,7 @@ Modes shell_modes(int kmin, int kmax) {
 bool stirring_on(const rlbm_config &c) { return c.force_amp != 0.0; }
 
 struct Layout {
-  size_t pop[2], nbmask, err, EY, G[2], coef[2], mode_kx, row_start;
+  size_t pop[2], nbmask, err, EY, G[2], coef[2], mode_kx, row_start, mode_scale;
   size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, total;
   long long plane;
   int pitch, xoff, Q, nrows, nmodes, max_bins, eyp;
@@ -96,6 +96,7 @@ Layout make_layout(const rlbm_config &c) {
   L.coef[1] = take(4 * rb * L.nmodes);
   L.mode_kx = take(4 * L.nmodes);
   L.row_start = take(4 * (L.nrows + 1));
+  L.mode_scale = take(8 * L.nmodes);
   L.eps = take(8 * ncell);
   L.ux = take(8 * ncell);
   L.uy = take(8 * ncell);
@@ -170,6 +171,7 @@ struct rlbm_ctx {
   char *ws = nullptr;
   int cur = 0;           // population buffer holding f*_n
   int64_t step = 0;
+  long long nfluid = 0;  // cells that are not solid
   rlbm_status latched = RLBM_OK;
   std::string msg;
   HostGeom geom;
@@ -194,17 +196,20 @@ struct rlbm_ctx {
 
 namespace {
 
-cudaError_t dispatch_step(rlbm_ctx *c, int src, const HostStir &s) {
+// Step `s` (its tables: s.G_cur of step n) from the buffer behind `ti` into `fout`.
+cudaError_t dispatch_step_raw(rlbm_ctx *c, const CUtensorMap *ti, void *fout, int64_t n, const HostStir &s) {
   unsigned *err = c->at<unsigned>(c->L.err);
-  const void *ti = &c->tmap_in[src];
-  const void *tg = &c->tmap_G[c->step & 1], *te = &c->tmap_EY;
-  void *fout = c->ws + c->L.pop[src ^ 1];
+  const void *tg = &c->tmap_G[n & 1], *te = &c->tmap_EY;
   switch (c->cfg.precision) {
     case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
     case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
     case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
     default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
   }
+}
+
+cudaError_t dispatch_step(rlbm_ctx *c, int src, const HostStir &s) {
+  return dispatch_step_raw(c, &c->tmap_in[src], c->ws + c->L.pop[src ^ 1], c->step, s);
 }
 
 cudaError_t dispatch_ghosts(rlbm_ctx *c, int b) {
@@ -224,15 +229,21 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-std::string make_tensor_maps(rlbm_ctx *c) {
+EncodeTiledFn tensor_map_encoder() {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return "cuTensorMapEncodeTiled is not available";
-    encode = reinterpret_cast<EncodeTiledFn>(fn);
+    if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn) encode = reinterpret_cast<EncodeTiledFn>(fn);
   }
+  return encode;
+}
+
+// Load map of a population buffer at `base` (the layout of the context's own buffers).
+std::string encode_state_map(const rlbm_ctx *c, void *base, CUtensorMap *out) {
+  EncodeTiledFn encode = tensor_map_encoder();
+  if (!encode) return "cuTensorMapEncodeTiled is not available";
   const int prec = c->cfg.precision;
   const size_t eb = store_bytes(prec);
   const CUtensorMapDataType dt = prec == RLBM_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -242,13 +253,21 @@ std::string make_tensor_maps(rlbm_ctx *c) {
   const cuuint32_t V = (cuuint32_t)(16 / eb);
   const cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * eb, (cuuint64_t)c->L.plane * eb};
   const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint64_t din[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->cfg.ny + 2, (cuuint64_t)c->L.Q};
+  const cuuint32_t bin[3] = {32 + 2 * V, 10, (cuuint32_t)c->L.Q};
+  CUresult r = encode(out, dt, 3, base, din, strides, bin, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (load map) failed with " + std::to_string((int)r);
+  return "";
+}
+
+std::string make_tensor_maps(rlbm_ctx *c) {
+  EncodeTiledFn encode = tensor_map_encoder();
+  if (!encode) return "cuTensorMapEncodeTiled is not available";
+  const int prec = c->cfg.precision;
   for (int b = 0; b < 2; ++b) {
-    void *base = c->ws + c->L.pop[b];
-    const cuuint64_t din[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->cfg.ny + 2, (cuuint64_t)c->L.Q};
-    const cuuint32_t bin[3] = {32 + 2 * V, 10, (cuuint32_t)c->L.Q};
-    CUresult r = encode(&c->tmap_in[b], dt, 3, base, din, strides, bin, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (load map) failed with " + std::to_string((int)r);
+    const std::string m = encode_state_map(c, c->ws + c->L.pop[b], &c->tmap_in[b]);
+    if (!m.empty()) return m;
   }
   // stirring tables of a tile: G rows {4 nx} (one R4 per column) in boxes {4 * 32, nrows},
   // EY rows {2 eyp} in boxes {2 * 8, nrows}; staged only for shells of <= 16 k_y rows
@@ -320,6 +339,7 @@ HostStir stir_for_step(rlbm_ctx *c, int64_t n) {
   s.seed = c->cfg.seed;
   s.step_new = n + 2;
   s.amp = c->cfg.force_amp;
+  s.mode_scale = c->at<double>(L.mode_scale);
   return s;
 }
 
@@ -476,6 +496,10 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   std::vector<std::vector<uint8_t>> keep;
   cudaError_t e = cudaSuccess;
 
+  c->nfluid = (long long)ncell;
+  for (size_t i = 0; cfg->solid && i < ncell; ++i)
+    if (cfg->solid[i] != 0) --c->nfluid;
+
   // solid-neighbour masks: bit 4 = the cell, bit (dy+1)*3+(dx+1) = neighbour (x+dx, y+dy);
   // rows y = -1 and y = ny are solid when walls_y is set.
   if (cfg->solid || cfg->walls_y) {
@@ -515,7 +539,10 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
     keep.emplace_back();
     if (cfg->precision == RLBM_F64) put_pairs<double>(keep.back(), ey_re, ey_im);
     else put_pairs<float>(keep.back(), ey_re, ey_im);
-    if ((e = put(L.EY, keep.back().data(), keep.back().size())) != cudaSuccess ||
+    const std::vector<double> ones(L.nmodes, 1.0);
+    keep.emplace_back(reinterpret_cast<const uint8_t *>(ones.data()), reinterpret_cast<const uint8_t *>(ones.data()) + 8 * ones.size());
+    if ((e = put(L.mode_scale, keep.back().data(), keep.back().size())) != cudaSuccess ||
+        (e = put(L.EY, keep[keep.size() - 2].data(), keep[keep.size() - 2].size())) != cudaSuccess ||
         (e = put(L.mode_kx, m.kx.data(), 4 * m.kx.size())) != cudaSuccess ||
         (e = put(L.row_start, m.row_start.data(), 4 * m.row_start.size())) != cudaSuccess) {
       c->cuda_fail(e, "upload of the stirring tables");
@@ -936,6 +963,219 @@ void rlbm_batch_free(rlbm_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
   }
   delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Stirring multipliers and the adjoint (gradient of the kinetic-energy objective)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GradLayout {
+  int64_t N;
+  int seg, K, nslots;
+  size_t state_bytes, kap_bytes;
+  size_t ckpt, slots, kap[2], acc, zpart, zsum, tw, gsig, out, total;
+  long long nblocks;
+  int nby;
+};
+
+GradLayout grad_layout(const rlbm_ctx *c, int64_t N, int32_t segment) {
+  GradLayout G{};
+  G.N = N;
+  G.seg = segment > 0 ? segment : std::max(1, (int)std::ceil(std::sqrt((double)N)));
+  if (G.seg > N) G.seg = (int)N;
+  G.K = (int)((N + G.seg - 1) / G.seg);
+  G.nslots = G.seg - 1;
+  const int prec = c->cfg.precision;
+  G.state_bytes = align_up(store_bytes(prec) * c->L.Q * c->L.plane);
+  G.kap_bytes = align_up(real_bytes(prec) * c->L.Q * c->L.plane);
+  G.nby = (c->cfg.ny + 7) / 8;
+  G.nblocks = (long long)((c->cfg.nx + 31) / 32) * G.nby;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1)); return o; };
+  G.ckpt = take(G.state_bytes * G.K);
+  G.slots = take(G.state_bytes * G.nslots);
+  G.kap[0] = take(G.kap_bytes);
+  G.kap[1] = take(G.kap_bytes);
+  G.acc = take(32 * (size_t)G.nblocks);
+  G.zpart = take(4 * real_bytes(prec) * (size_t)G.nby * c->L.nrows * c->cfg.nx);
+  G.zsum = take(32 * (size_t)c->L.nrows * c->cfg.nx);
+  G.tw = take(16 * (size_t)c->cfg.nx);
+  G.gsig = take(8 * (size_t)c->L.nmodes);
+  G.out = take(64);
+  G.total = off;
+  return G;
+}
+
+std::string grad_check(const rlbm_ctx *c, int64_t nsteps, int32_t segment) {
+  if (c->cfg.precision != RLBM_F64 && c->cfg.precision != RLBM_F32)
+    return "the adjoint runs on FP64 and FP32 storage (the 16-bit forms round stochastically)";
+  if (nsteps < 1) return "nsteps must be >= 1";
+  if (segment < 0) return "segment must be >= 0 (0 = ceil(sqrt(nsteps)))";
+  return "";
+}
+
+// The adjoint always takes the force path on the paper's set, so that dJ/dF_body is the
+// derivative at F = 0 too (the forward with F = 0 is the same either way).
+cudaError_t dispatch_adjoint(rlbm_ctx *c, const AdjointArgs &a) {
+  HostPhys ph = c->phys;
+  ph.has_force = c->cfg.vset == 3 ? 1 : 0;
+  if (c->cfg.precision == RLBM_F64) return launch_adjoint_f64(c->cfg.vset, a, c->geom, ph, c->stream);
+  return launch_adjoint_f32(c->cfg.vset, a, c->geom, ph, c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t rlbm_num_modes(const rlbm_ctx *c) { return c ? c->L.nmodes : -1; }
+
+rlbm_status rlbm_set_mode_scale(rlbm_ctx *c, const double *sigma, int32_t nmodes) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (nmodes != c->L.nmodes) return c->fail(RLBM_E_INVAL, "nmodes must equal rlbm_num_modes(ctx) = " + std::to_string(c->L.nmodes));
+  if (nmodes == 0) return RLBM_OK;
+  if (!sigma) return c->fail(RLBM_E_INVAL, "sigma is NULL");
+  for (int m = 0; m < nmodes; ++m)
+    if (!std::isfinite(sigma[m])) return c->fail(RLBM_E_INVAL, "sigma must be finite");
+  Scoped dev(c->device);
+  cudaError_t e = cudaMemcpyAsync(c->ws + c->L.mode_scale, sigma, 8 * (size_t)nmodes, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "copy of the mode multipliers");
+  // the coefficients and table of the current and next step are redrawn with them
+  if ((e = stir_prime(c, c->step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
+  return check_device(c);
+}
+
+rlbm_status rlbm_gradient_query_workspace(const rlbm_ctx *c, int64_t nsteps, int32_t segment, size_t *bytes) {
+  if (!c || !bytes) { g_thread_error = "ctx and bytes must be non-NULL"; return RLBM_E_INVAL; }
+  const std::string m = grad_check(c, nsteps, segment);
+  if (!m.empty()) { g_thread_error = m; return RLBM_E_INVAL; }
+  *bytes = grad_layout(c, nsteps, segment).total;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *dev_workspace, size_t bytes, double *J,
+                          double *grad_sigma, double *grad_eta_over_s, double *grad_body_force) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  {
+    const std::string m = grad_check(c, nsteps, segment);
+    if (!m.empty()) return c->fail(RLBM_E_INVAL, m);
+  }
+  const GradLayout G = grad_layout(c, nsteps, segment);
+  if (!dev_workspace || reinterpret_cast<uintptr_t>(dev_workspace) % kAlign)
+    return c->fail(RLBM_E_INVAL, "dev_workspace must be a 256-byte aligned device pointer");
+  if (bytes < G.total) return c->fail(RLBM_E_NOMEM, "gradient workspace too small: " + std::to_string(bytes) + " < " + std::to_string(G.total));
+  if (c->nfluid < 1) return c->fail(RLBM_E_INVAL, "the lattice has no fluid cell");
+  Scoped dev(c->device);
+  char *w = static_cast<char *>(dev_workspace);
+  auto ckpt = [&](int k) { return w + G.ckpt + G.state_bytes * (size_t)k; };
+  auto slot = [&](int j) { return w + G.slots + G.state_bytes * (size_t)j; };
+  std::vector<CUtensorMap> mck(G.K), msl(G.nslots);
+  for (int k = 0; k < G.K; ++k) {
+    const std::string m = encode_state_map(c, ckpt(k), &mck[k]);
+    if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
+  }
+  for (int j = 0; j < G.nslots; ++j) {
+    const std::string m = encode_state_map(c, slot(j), &msl[j]);
+    if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
+  }
+  cudaError_t e;
+  // ghost rows of wall-bounded lattices are never written: start from zeroed buffers
+  if ((e = cudaMemsetAsync(w, 0, G.total, c->stream)) != cudaSuccess) return c->cuda_fail(e, "cudaMemsetAsync");
+
+  // forward: B_{-1} (the context's buffer) to checkpoint 0; B_{k seg - 1} into checkpoint k
+  const int64_t s0 = c->step;
+  if ((e = cudaMemcpyAsync(ckpt(0), c->ws + c->L.pop[c->cur], G.state_bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return c->cuda_fail(e, "copy of the start state");
+  int where = -1;  // B_{n-1}: -1 - k = checkpoint k, 0 / 1 = context buffer
+  for (int64_t n = 0; n < nsteps; ++n) {
+    const CUtensorMap *ti = where < 0 ? &mck[-1 - where] : &c->tmap_in[where];
+    void *fout;
+    int next;
+    if ((n + 1) % G.seg == 0 && n + 1 < nsteps) {
+      next = -1 - (int)((n + 1) / G.seg);
+      fout = ckpt((int)((n + 1) / G.seg));
+    } else {
+      next = where < 0 ? 0 : (where ^ 1);
+      fout = c->ws + c->L.pop[next];
+    }
+    c->phys.step = s0 + n;
+    if ((e = dispatch_step_raw(c, ti, fout, s0 + n, stir_for_step(c, s0 + n))) != cudaSuccess) return c->cuda_fail(e, "step kernel launch");
+    where = next;
+  }
+  c->cur = where;  // the last step writes a context buffer
+  c->step = s0 + nsteps;
+
+  // reverse sweep
+  if ((e = launch_adj_twiddles(reinterpret_cast<double2 *>(w + G.tw), c->cfg.nx, c->stream)) != cudaSuccess)
+    return c->cuda_fail(e, "twiddle kernel");
+  AdjointArgs a{};
+  a.acc = reinterpret_cast<double *>(w + G.acc);
+  a.zpart = w + G.zpart;
+  a.zsum = w + G.zsum;
+  a.tw = w + G.tw;
+  a.EY = c->ws + c->L.EY;
+  a.nrows = c->L.nrows;
+  a.nmodes = c->L.nmodes;
+  a.eyp = c->L.eyp;
+  a.mode_kx = c->at<int>(c->L.mode_kx);
+  a.row_start = c->at<int>(c->L.row_start);
+  a.seed = c->cfg.seed;
+  a.amp = c->cfg.force_amp;
+  a.gsig = reinterpret_cast<double *>(w + G.gsig);
+  a.err = c->at<unsigned>(c->L.err);
+  const double cj = 1.0 / ((double)nsteps * (double)c->nfluid);
+  int kc = 0;  // kap[kc] holds kappa_{n+1}
+  // the last state: objective only
+  a.B = c->ws + c->L.pop[c->cur];
+  a.kin = nullptr;
+  a.kout = w + G.kap[kc];
+  a.cj = cj;
+  a.G = c->ws + c->L.G[0];
+  a.step = s0 + nsteps;
+  if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
+  for (int k = G.K - 1; k >= 0; --k) {
+    const int64_t lo = (int64_t)k * G.seg, hi = std::min<int64_t>(lo + G.seg, nsteps);
+    // recompute B_lo .. B_{hi-2} from checkpoint k into the slots
+    if (hi - lo >= 2) {
+      if ((e = stir_prime(c, s0 + lo)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
+      for (int64_t n = lo; n <= hi - 2; ++n) {
+        const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
+        c->phys.step = s0 + n;
+        if ((e = dispatch_step_raw(c, ti, slot((int)(n - lo)), s0 + n, stir_for_step(c, s0 + n))) != cudaSuccess)
+          return c->cuda_fail(e, "step kernel launch (recompute)");
+      }
+    }
+    for (int64_t n = hi - 1; n >= lo; --n) {
+      if ((e = stir_prime(c, s0 + n)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
+      a.B = n == lo ? ckpt(k) : slot((int)(n - lo - 1));
+      a.kin = w + G.kap[kc];
+      a.kout = w + G.kap[kc ^ 1];
+      a.cj = n >= 1 ? cj : 0.0;
+      a.G = c->ws + c->L.G[(s0 + n) & 1];
+      a.step = s0 + n;
+      if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
+      kc ^= 1;
+    }
+  }
+  double *out = reinterpret_cast<double *>(w + G.out);
+  if ((e = launch_reduce_partials(a.acc, G.nblocks, out, c->stream)) != cudaSuccess) return c->cuda_fail(e, "reduction kernel");
+  // the context continues from step s0 + nsteps
+  c->phys.step = c->step;
+  if ((e = stir_prime(c, c->step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
+  double host[4];
+  if ((e = cudaMemcpyAsync(host, out, 32, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of the sums");
+  if (grad_sigma && c->L.nmodes &&
+      (e = cudaMemcpyAsync(grad_sigma, a.gsig, 8 * (size_t)c->L.nmodes, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return c->cuda_fail(e, "copy of the mode gradient");
+  if (rlbm_status s = check_device(c)) return s;
+  if (J) *J = host[3];
+  if (grad_eta_over_s) *grad_eta_over_s = -host[0] / c->cfg.eta_over_s;
+  if (grad_body_force) { grad_body_force[0] = host[1]; grad_body_force[1] = host[2]; }
+  return RLBM_OK;
 }
 
 }  // extern "C"

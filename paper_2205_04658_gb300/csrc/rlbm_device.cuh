@@ -191,6 +191,7 @@ template <typename R> struct Stir {
   unsigned long long seed;
   long long step_new;      // n + 2
   double amp;
+  const double *mode_scale;  // [nmodes] amplitude multipliers sigma_m; NULL = all 1
 };
 
 // ---------------------------------------------------------------------------
@@ -304,11 +305,11 @@ __device__ inline void stir_draws_part(const Stir<R> &s, int rank, int ncta) {
   for (int m = rank; m < s.nmodes; m += ncta) {
     if constexpr (sizeof(R) == 8) {
       double c[4];
-      stir_draw(s.seed, s.step_new, m, s.amp, c);
+      stir_draw(s.seed, s.step_new, m, s.mode_scale ? s.amp * s.mode_scale[m] : s.amp, c);
       s.coef_new[m] = R4<R>{(R)c[0], (R)c[1], (R)c[2], (R)c[3]};
     } else {
       float c[4];
-      stir_draw_f32(s.seed, s.step_new, m, (float)s.amp, c);
+      stir_draw_f32(s.seed, s.step_new, m, (float)(s.mode_scale ? s.amp * s.mode_scale[m] : s.amp), c);
       s.coef_new[m] = R4<R>{c[0], c[1], c[2], c[3]};
     }
   }

@@ -409,7 +409,7 @@ template <typename R> __device__ __forceinline__ Stir<R> member_stir(const Membe
   s.coef_next = (const R4<R> *)d.coef[(n + 1) & 1];
   s.coef_new = (R4<R> *)d.coef[n & 1];
   s.mode_kx = d.mode_kx; s.row_start = d.row_start;
-  s.seed = d.seed; s.step_new = n + 2; s.amp = 0.0;
+  s.seed = d.seed; s.step_new = n + 2; s.amp = 0.0; s.mode_scale = nullptr;
   return s;
 }
 
@@ -639,10 +639,11 @@ __global__ void fill_ghosts_kernel(S *__restrict__ f, const Geometry<typename Re
 // Stirring pipeline start at step n: coefficients of steps n and n+1, table of step n.
 template <typename R>
 __global__ void stir_draw_kernel(R4<R> *coef_a, R4<R> *coef_b, int nmodes, unsigned long long seed,
-                                 long long n, double amp) {
+                                 long long n, double amp, const double *__restrict__ scale) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * nmodes) return;
   const int m = t % nmodes;
+  if (scale) amp *= scale[m];
   // same arithmetic as the draws a step launch makes for later steps
   if constexpr (sizeof(R) == 8) {
     double c[4];
@@ -682,7 +683,7 @@ template <typename R> static Stir<R> to_stir(const HostStir &h) {
   s.G_cur = (const R4<R> *)h.G_cur; s.EY = (const R2<R> *)h.EY; s.G_next = (R4<R> *)h.G_next;
   s.coef_next = (const R4<R> *)h.coef_next; s.coef_new = (R4<R> *)h.coef_new;
   s.mode_kx = h.mode_kx; s.row_start = h.row_start; s.eyp = h.eyp;
-  s.seed = h.seed; s.step_new = h.step_new; s.amp = h.amp;
+  s.seed = h.seed; s.step_new = h.step_new; s.amp = h.amp; s.mode_scale = h.mode_scale;
   return s;
 }
 
@@ -875,7 +876,8 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
   if (hs.nmodes == 0) return cudaSuccess;
   const Stir<R> s = to_stir<R>(hs);
   stir_draw_kernel<R><<<(2 * hs.nmodes + 127) / 128, 128, 0, stream>>>((R4<R> *)coef_n, (R4<R> *)coef_n1,
-                                                                        hs.nmodes, hs.seed, n, hs.amp);
+                                                                        hs.nmodes, hs.seed, n, hs.amp,
+                                                                        hs.mode_scale);
   const long long entries = (long long)hs.nrows * nx;
   stir_table_kernel<R><<<(unsigned)((entries + 255) / 256), 256, 0, stream>>>(s, (R4<R> *)G_n,
                                                                              (const R4<R> *)coef_n, nx);

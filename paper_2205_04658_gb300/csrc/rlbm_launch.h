@@ -35,6 +35,7 @@ struct HostStir {
   unsigned long long seed;
   long long step_new;
   double amp;
+  const double *mode_scale;  // device [nmodes]; NULL = all 1
 };
 
 // One lattice of a batch, as the batched step kernel sees it (device memory, written by
@@ -87,6 +88,29 @@ RLBM_DECLARE_LAUNCHERS(f64)
 RLBM_DECLARE_LAUNCHERS(f32)
 RLBM_DECLARE_LAUNCHERS(f16)
 RLBM_DECLARE_LAUNCHERS(bf16)
+
+// One adjoint step (rlbm_adjoint.cu): buffers and tables of the launch.
+struct AdjointArgs {
+  const void *B;           // post-collision buffer B_{n-1} (storage type)
+  const void *kin;         // kappa_{n+1} (compute type), NULL for the last state
+  void *kout;              // kappa_n
+  double cj;               // objective weight of the state S_n
+  double *acc;             // [blocks][4] FP64 accumulators
+  void *zpart;             // [block rows][nrows][nx] R4 of the compute type
+  void *zsum;              // [nrows][nx] double4
+  const void *tw;          // [nx] double2 exp(+2 pi i t / nx)
+  const void *G, *EY;      // stirring tables of step n
+  int nrows, nmodes, eyp;
+  const int *mode_kx, *row_start;
+  unsigned long long seed;
+  long long step;          // step index n (draws of the mode gradient)
+  double amp;
+  double *gsig;            // [nmodes] accumulators of d J / d sigma_m
+  unsigned *err;
+};
+cudaError_t launch_adjoint_f64(int vset, const AdjointArgs &a, const HostGeom &g, const HostPhys &p, cudaStream_t st);
+cudaError_t launch_adjoint_f32(int vset, const AdjointArgs &a, const HostGeom &g, const HostPhys &p, cudaStream_t st);
+cudaError_t launch_adj_twiddles(double2 *tw, int n, cudaStream_t st);
 
 // Reductions and spectrum (rlbm_aux.cu)
 cudaError_t launch_counter_inc(long long *counter, cudaStream_t st);

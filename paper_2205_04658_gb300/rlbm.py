@@ -69,6 +69,10 @@ def lib():
             "rlbm_batch_last_error": (ctypes.c_char_p, [P]),
             "rlbm_batch_free": (None, [P]),
             "rlbm_spectrum_noalloc": (c_i32, [P, P, c_i32, c_i32, c_i32, P, P]),
+            "rlbm_num_modes": (c_i32, [P]),
+            "rlbm_set_mode_scale": (c_i32, [P, dp, c_i32]),
+            "rlbm_gradient_query_workspace": (c_i32, [P, c_i64, c_i32, ctypes.POINTER(c_sz)]),
+            "rlbm_gradient": (c_i32, [P, c_i64, c_i32, P, c_sz, dp, dp, dp, dp]),
             "rlbm_sync": (c_i32, [P]),
             "rlbm_current_step": (c_i64, [P]),
             "rlbm_last_error": (ctypes.c_char_p, [P]),
@@ -184,6 +188,34 @@ def rlbm_velocity_classes(vset=3):
     return out.reshape(q, 4)
 
 
+def rlbm_num_modes(ctx):
+    return lib().rlbm_num_modes(ctx)
+
+
+def rlbm_set_mode_scale(ctx, sigma):
+    s_ = np.ascontiguousarray(sigma, dtype=np.float64).ravel()
+    _check(lib().rlbm_set_mode_scale(ctx, _dptr(s_), int(s_.size)), ctx)
+
+
+def rlbm_gradient_query_workspace(ctx, nsteps, segment=0):
+    n = ctypes.c_size_t(0)
+    st = lib().rlbm_gradient_query_workspace(ctx, int(nsteps), int(segment), ctypes.byref(n))
+    if st != RLBM_OK:
+        raise RlbmError(st, lib().rlbm_last_error(None).decode())
+    return n.value
+
+
+def rlbm_gradient(ctx, nsteps, segment, dev_workspace, nbytes):
+    """(J, dJ/dsigma (nmodes,), dJ/d(eta/s), dJ/dF_body (2,))."""
+    J = np.zeros(1)
+    gs = np.zeros(max(1, rlbm_num_modes(ctx)))
+    ge = np.zeros(1)
+    gb = np.zeros(2)
+    _check(lib().rlbm_gradient(ctx, int(nsteps), int(segment), ctypes.c_void_p(dev_workspace), nbytes,
+                               _dptr(J), _dptr(gs), _dptr(ge), _dptr(gb)), ctx)
+    return J[0], gs[:rlbm_num_modes(ctx)], ge[0], gb
+
+
 def rlbm_sync(ctx):
     _check(lib().rlbm_sync(ctx), ctx)
 
@@ -256,6 +288,25 @@ class Lattice:
 
     def autotune(self, reps=10):
         return rlbm_autotune(self.ctx, reps)
+
+    @property
+    def num_modes(self):
+        return rlbm_num_modes(self.ctx)
+
+    def set_mode_scale(self, sigma):
+        rlbm_set_mode_scale(self.ctx, sigma)
+
+    def gradient(self, nsteps, segment=0):
+        """Runs nsteps steps and the adjoint: (J, dJ/dsigma, dJ/d(eta/s), dJ/dF_body).
+        The checkpoint workspace is allocated by torch for the call."""
+        import torch
+        nbytes = rlbm_gradient_query_workspace(self.ctx, nsteps, segment)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = (ws.data_ptr() + 255) // 256 * 256
+        with torch.cuda.stream(self.stream):
+            out = rlbm_gradient(self.ctx, nsteps, segment, ptr, nbytes)
+        del ws
+        return out
 
     def sync(self):
         rlbm_sync(self.ctx)

@@ -1,0 +1,207 @@
+"""GPU adjoint (rlbm_gradient, hand-written reverse of the fused step with checkpoints)
+against the oracle's FP64 adjoint and against central finite differences of the
+forward objective, plus the checkpointing and autograd plumbing.
+
+Objective: J = (1/N) sum_{n=1}^{N} mean over fluid cells of |v_n|^2 / 2."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import rlbm_adjoint as A
+from oracle import rlbm_oracle as O
+from paper_2205_04658_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_04658_gb300 import build as B
+    from paper_2205_04658_gb300 import rlbm
+    if not os.path.exists(rlbm.LIB_PATH):
+        B.build()
+    return rlbm
+
+
+def _stirred(nx=40, ny=36):
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=13, eps_amp=0.02, u_amp=0.05, kmax=3)
+    return dict(nx=nx, ny=ny, eta_over_s=0.06, kmin=2, kmax=4, force_amp=4e-3, seed=21,
+                body_force=(1e-3, -2e-3), init_eps=e, init_ux=ux, init_uy=uy)
+
+
+def _gpu_grad(R, cfg, nsteps, precision, segment=0, sigma=None):
+    lat = R.Lattice(cfg["nx"], cfg["ny"], precision=precision,
+                    **{k: v for k, v in cfg.items() if k not in ("nx", "ny", "mode_scale")})
+    if sigma is not None:
+        lat.set_mode_scale(sigma)
+    out = lat.gradient(nsteps, segment)
+    lat.close()
+    return out
+
+
+def _rel(a, b):
+    a, b = np.atleast_1d(a), np.atleast_1d(b)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 2e-4)])
+def test_stirred_gradient_matches_oracle_adjoint(R, precision, tol):
+    """40 x 36 (ragged against the 32 x 8 tile), shell 2..4, body force, 24 steps, with
+    non-unit multipliers."""
+    cfg = _stirred()
+    nm = len(O.shell_modes(2, 4))
+    sigma = 1.0 + 0.3 * np.sin(np.arange(nm))
+    ref = A.gradient(dict(cfg, mode_scale=sigma), 24)
+    J, gs, ge, gb = _gpu_grad(R, cfg, 24, precision, sigma=sigma)
+    assert abs(J - ref["J"]) <= (1e-12 if precision == "f64" else 1e-5) * ref["J"]
+    assert gs.shape == (nm,)
+    assert _rel(gs, ref["sigma"]) <= tol, (gs, ref["sigma"])
+    assert _rel(ge, ref["eta_over_s"]) <= tol, (ge, ref["eta_over_s"])
+    assert _rel(gb, ref["body_force"]) <= tol, (gb, ref["body_force"])
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 2e-4)])
+def test_walls_discs_gradient_matches_oracle_adjoint(R, precision, tol):
+    nx, ny = 48, 24
+    mask, _ = inputs.disc_mask(nx, ny, radius=2, fraction=0.06, seed=17, walls_y=True)
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=19, eps_amp=0.01, u_amp=0.04, kmax=3)
+    cfg = dict(nx=nx, ny=ny, walls_y=1, solid=mask, eta_over_s=0.05, body_force=(2e-3, 5e-4),
+               init_eps=e, init_ux=ux, init_uy=uy)
+    ref = A.gradient(cfg, 20)
+    J, gs, ge, gb = _gpu_grad(R, cfg, 20, precision)
+    assert abs(J - ref["J"]) <= (1e-12 if precision == "f64" else 1e-5) * ref["J"]
+    assert _rel(ge, ref["eta_over_s"]) <= tol
+    assert _rel(gb, ref["body_force"]) <= tol
+
+
+def test_circle_set_eta_gradient_matches_oracle_adjoint(R):
+    nx, ny = 40, 24
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=23, u_amp=0.05, kmax=3)
+    cfg = dict(nx=nx, ny=ny, vset=2, eta_over_s=0.08, init_eps=e, init_ux=ux, init_uy=uy)
+    ref = A.gradient(cfg, 16)
+    J, gs, ge, gb = _gpu_grad(R, cfg, 16, "f64")
+    assert abs(J - ref["J"]) <= 1e-12 * ref["J"]
+    assert _rel(ge, ref["eta_over_s"]) <= 1e-9
+    assert np.all(gb == 0.0)
+
+
+def test_checkpoint_segment_does_not_change_the_result(R):
+    """Every segment length recomputes the same states with the same arithmetic."""
+    cfg = _stirred(64, 40)
+    outs = [_gpu_grad(R, cfg, 30, "f32", segment=s) for s in (1, 4, 0, 7, 30)]
+    for o in outs[1:]:
+        assert o[0] == outs[0][0]
+        assert np.array_equal(o[1], outs[0][1])
+        assert o[2] == outs[0][2]
+        assert np.array_equal(o[3], outs[0][3])
+
+
+def test_context_continues_after_the_gradient(R):
+    """rlbm_gradient leaves the context exactly where rlbm_step(nsteps) would."""
+    cfg = _stirred(64, 40)
+    kw = {k: v for k, v in cfg.items() if k not in ("nx", "ny")}
+    a = R.Lattice(64, 40, precision="f32", **kw)
+    a.gradient(17, 5)
+    assert a.current_step == 17
+    a.step(6)
+    ga = a.moments()
+    a.close()
+    b = R.Lattice(64, 40, precision="f32", **kw)
+    b.step(23)
+    gb = b.moments()
+    b.close()
+    for k in range(3):
+        assert np.array_equal(ga[k], gb[k])
+
+
+def test_mode_scale_in_the_forward_matches_the_oracle(R):
+    cfg = _stirred()
+    nm = len(O.shell_modes(2, 4))
+    sigma = np.linspace(0.0, 2.0, nm)
+    ref = O.run(dict(cfg, mode_scale=sigma), 30)
+    lat = R.Lattice(cfg["nx"], cfg["ny"], precision="f64", **{k: v for k, v in cfg.items() if k not in ("nx", "ny")})
+    assert lat.num_modes == nm
+    lat.set_mode_scale(sigma)
+    lat.step(30)
+    got = lat.moments()
+    lat.close()
+    umax = max(np.abs(ref[1]).max(), np.abs(ref[2]).max())
+    assert np.abs(got[1] - ref[1]).max() <= 1e-10 * umax
+    assert np.abs(got[0] / ref[0] - 1.0).max() <= 1e-10
+
+
+def test_invalid_gradient_requests_are_rejected(R):
+    lat = R.Lattice(32, 32, precision="f16", eta_over_s=0.1)
+    with pytest.raises(R.RlbmError) as e:
+        lat.gradient(4)
+    assert e.value.status == R.RLBM_E_INVAL
+    lat.close()
+    lat = R.Lattice(32, 32, precision="f32", eta_over_s=0.1, kmin=2, kmax=3, force_amp=1e-3)
+    with pytest.raises(R.RlbmError):
+        lat.set_mode_scale(np.ones(lat.num_modes + 1))
+    with pytest.raises(R.RlbmError):
+        lat.gradient(0)
+    lat.close()
+
+
+def test_autograd_function_gradcheck(R):
+    """torch.autograd.gradcheck of the differentiable objective (FP64 lattice)."""
+    import torch
+    from paper_2205_04658_gb300 import adjoint
+    nx, ny = 32, 24
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=29, u_amp=0.04, kmax=3)
+    spec = dict(nx=nx, ny=ny, precision="f64", kmin=2, kmax=3, force_amp=5e-3, seed=31,
+                init_eps=e, init_ux=ux, init_uy=uy, nsteps=12, segment=4)
+    nm = len(O.shell_modes(2, 3))
+    sigma = torch.linspace(0.5, 1.5, nm, dtype=torch.float64, requires_grad=True)
+    eta = torch.tensor(0.07, dtype=torch.float64, requires_grad=True)
+    body = torch.tensor([1e-3, 0.0], dtype=torch.float64, requires_grad=True)
+    f = lambda s, et, b: adjoint.StirredKineticEnergy.apply(s, et, b, spec)
+    assert torch.autograd.gradcheck(f, (sigma, eta, body), eps=1e-6, atol=1e-12, rtol=1e-5)
+    J = adjoint.kinetic_energy(sigma, eta, body, **spec)
+    J.backward()
+    assert sigma.grad.shape == (nm,) and eta.grad.ndim == 0 and body.grad.shape == (2,)
+
+
+def _objective_fp64(R, nx, ny, nsteps, kw, sigma=None):
+    """J of a forward FP64 run through the plain step / totals path (no adjoint code)."""
+    lat = R.Lattice(nx, ny, precision="f64", **kw)
+    if sigma is not None:
+        lat.set_mode_scale(sigma)
+    acc = 0.0
+    for _ in range(nsteps):
+        lat.step(1)
+        acc += lat.totals()[3]
+    lat.close()
+    return acc / (nsteps * nx * ny)
+
+
+def test_adjoint_512_matches_central_differences(R):
+    """The stirred 512 x 512 workload (shell 4 <= |k| <= 6, 34 modes, amplitude 1e-4,
+    seed 5, eta/s 0.05), 2000 steps, sqrt(N) checkpoints: the FP32 adjoint against
+    central differences of the FP64 forward objective (h = 1e-4 relative)."""
+    nx = ny = 512
+    N = 2000
+    kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
+    J, gs, ge, gb = _gpu_grad(R, dict(nx=nx, ny=ny, **kw), N, "f32")
+    nm = gs.size
+    assert nm == 34
+    top = np.argsort(-np.abs(gs))[:3]
+    for m in top:
+        sp, sm = np.ones(nm), np.ones(nm)
+        sp[m] += 1e-4
+        sm[m] -= 1e-4
+        fd = (_objective_fp64(R, nx, ny, N, kw, sp) - _objective_fp64(R, nx, ny, N, kw, sm)) / 2e-4
+        assert abs(gs[m] - fd) <= 1e-4 * abs(fd), (m, gs[m], fd)
+    h = 1e-4 * 0.05
+    fd = (_objective_fp64(R, nx, ny, N, dict(kw, eta_over_s=0.05 + h))
+          - _objective_fp64(R, nx, ny, N, dict(kw, eta_over_s=0.05 - h))) / (2 * h)
+    assert abs(ge - fd) <= 1e-4 * abs(fd), (ge, fd)
+    hb = 1e-6
+    fd = (_objective_fp64(R, nx, ny, N, dict(kw, body_force=(hb, 0.0)))
+          - _objective_fp64(R, nx, ny, N, dict(kw, body_force=(-hb, 0.0)))) / (2 * hb)
+    assert abs(gb[0] - fd) <= 1e-4 * abs(fd), (gb[0], fd)
