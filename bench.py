@@ -45,9 +45,10 @@ def parse():
     p.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64"],
+    p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512"],
                    help="stirred: one lattice (default); ensemble64: 64 stirred members of uneven sizes "
-                        "advanced by one persistent launch per step")
+                        "advanced by one persistent launch per step; adjoint512: gradient of the kinetic "
+                        "energy of a 512^2 stirred run (2000 steps) by the checkpointed adjoint")
     return p.parse_args()
 
 
@@ -60,12 +61,16 @@ def workload_name(args):
             "dt 0.05, a 0.1, eps0 1 at rest" % (args.nx, args.ny, args.precision.upper()))
 
 
+STEP_KERNEL_SOURCES = ("rlbm_device.cuh", "rlbm_kernels.cuh", "rlbm_tma.cuh", "rlbm_launch.h", "rlbm_kernels_f32.cu")
+
+
 def csrc_digest():
+    """Digest of the sources the FP32 step kernel is compiled from (the kernel whose ncu
+    counters profiles/ holds); a change there invalidates the committed traffic figure."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2205_04658_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -405,12 +410,65 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Time per gradient of J = time-averaged mean |v|^2 / 2 of the 512^2 stirred run
+    (shell 4 <= |k| <= 6, 34 modes, amplitude 1e-4, seed 5, eta/s 0.05, 2000 steps) with
+    respect to the 34 mode multipliers, eta/s and the body force: forward with sqrt(N)
+    checkpoints, segment recomputation and the reverse sweep, all inside the timed call.
+    Compared with the forward alone (2000 steps)."""
+    import torch
+    from paper_2205_04658_gb300 import rlbm
+    torch.cuda.set_device(0)
+    rlbm.lib()
+    nx = ny = 512
+    N = 2000
+    prec = args.precision
+    kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
+    stream = torch.cuda.Stream()
+    lat = rlbm.Lattice(nx, ny, stream=stream, precision=prec, **kw)
+    nbytes = rlbm.rlbm_gradient_query_workspace(lat.ctx, N, 0)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    ptr = (ws.data_ptr() + 255) // 256 * 256
+    for _ in range(max(1, args.warmup // 10)):
+        rlbm.rlbm_gradient(lat.ctx, N, 0, ptr, nbytes)
+    reps = max(1, min(args.steps, 5))
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, gs, ge, gb = rlbm.rlbm_gradient(lat.ctx, N, 0, ptr, nbytes)  # returns after a stream sync
+        times.append(time.perf_counter() - t0)
+    fwd = []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lat.step(N)
+            b.record(stream)
+        torch.cuda.synchronize()
+        fwd.append(a.elapsed_time(b) / 1e3)
+    lat.close()
+    t = statistics.median(times)
+    tf = statistics.median(fwd)
+    line = {"metric": "time per gradient (adjoint, sqrt(N) checkpoints)", "value": t, "unit": "s",
+            "n_gpus": 1, "steps": reps, "warmup": max(1, args.warmup // 10), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": "gradient of the 512x512 stirred run (shell 4<=|k|<=6, 34 modes, amp 1e-4, "
+                                   "seed 5, eta/s 0.05), 2000 steps, wrt 34 mode multipliers, eta/s, body force",
+                       "checkpoint_segment": int(round(N ** 0.5 + 0.4999)), "workspace_bytes": nbytes},
+            "forward_only_s": tf, "gradient_over_forward": t / tf,
+            "gradient_mlups": nx * ny * N / t / 1e6, "J": J, "grad_eta_over_s": ge}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ensemble64":
         run_ensemble(args)
+    elif args.workload == "adjoint512":
+        run_adjoint(args)
     else:
         run_gb300(args)
 
