@@ -136,12 +136,15 @@ RLBM_API int32_t rlbm_num_planes(const rlbm_ctx *ctx);
 
 /* Launch shape of the fused step kernel: `ctas` persistent CTAs walk the lattice's
  * 32 x 8 tiles (0 = as many as are resident at once, the default; larger values are
- * clamped) and `stages` (1 or 2; 0 keeps the current value) tiles of shared memory rotate
- * in its TMA pipeline (default 2).  A tuning control: results do not depend on it.
- * The paper has no counterpart. */
-RLBM_API rlbm_status rlbm_set_launch(rlbm_ctx *ctx, int32_t ctas, int32_t stages);
+ * clamped), `stages` (1 or 2; 0 keeps the current value) tiles of shared memory rotate
+ * in its TMA pipeline (default 2), and `stir_rows` says where the stirring rows of a tile
+ * come from: 1 = staged with the tile by TMA (default), 2 = read from global memory (less
+ * shared memory per CTA, so more CTAs per SM); 0 keeps the current value.  A tuning
+ * control: results do not depend on it.  The paper has no counterpart. */
+RLBM_API rlbm_status rlbm_set_launch(rlbm_ctx *ctx, int32_t ctas, int32_t stages, int32_t stir_rows);
 
-/* Autotuner: times every launch shape it knows (pipeline depth x CTA count), `reps`
+/* Autotuner: times every launch shape it knows (pipeline depth x CTA count x stirring
+ * rows staged or read from global memory), `reps`
  * launches each, on the current state, and keeps the fastest.  The state and the step
  * counter are left as they were (the launches rewrite the next buffer only).  *ms_out
  * (may be NULL) receives the chosen shape's time per step in milliseconds.  Syncs.

@@ -280,14 +280,15 @@ adjoint_kernel(const S *__restrict__ B, const typename RealOf<S>::type *__restri
       if (x < g.nx) zpart[((long long)blockIdx.y * st.nrows + r) * g.nx + x] = z;
     }
   }
-  // block sums (fixed order) added to this block's accumulators
-  double v[4] = {(double)gom, (double)gFx, (double)gFy, (double)jv};
+  // block sums (fixed order) added to this block's accumulators: warp sums in the compute
+  // type (GB300's FP64 rate is 1/64 of FP32), the eight warp sums in FP64
+  R v[4] = {gom, gFx, gFy, jv};
   __shared__ double red[8][4];
   const int tid = ly * 32 + lx, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    if (lane == 0) red[warp][k] = v[k];
+    if (lane == 0) red[warp][k] = (double)v[k];
   }
   __syncthreads();
   if (tid < 4) {
@@ -297,49 +298,58 @@ adjoint_kernel(const S *__restrict__ B, const typename RealOf<S>::type *__restri
   }
 }
 
-// zsum[r][x] = sum over block rows of zpart (FP64), the k_y-row transform of the force
-// adjoint at column x.
+// zsum_j[r][x] = sum over block rows of zpart_j: the k_y-row transform of the force
+// adjoint of step j of a segment at column x (blockIdx.z = j), in the compute type.
 template <typename R>
-__global__ void zsum_kernel(const R4<R> *__restrict__ zpart, int nby, int nrows, int nx, R4<double> *__restrict__ zsum) {
+__global__ void zsum_kernel(const R4<R> *__restrict__ zpart, int nby, int nrows, int nx, R4<R> *__restrict__ zsum) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
+  const long long j = blockIdx.z;
   if (x >= nx) return;
-  R4<double> s{0.0, 0.0, 0.0, 0.0};
+  const R4<R> *zp = zpart + j * nby * nrows * nx + (long long)r * nx + x;
+  R4<R> s{R(0), R(0), R(0), R(0)};
+#pragma unroll 8
   for (int b = 0; b < nby; ++b) {
-    const R4<R> z = zpart[((long long)b * nrows + r) * nx + x];
-    s.x += (double)z.x; s.y += (double)z.y; s.z += (double)z.z; s.w += (double)z.w;
+    const R4<R> z = zp[(long long)b * nrows * nx];
+    s.x += z.x; s.y += z.y; s.z += z.z; s.w += z.w;
   }
-  zsum[(long long)r * nx + x] = s;
+  zsum[(j * nrows + r) * nx + x] = s;
 }
 
-// gsig[m] += d/d sigma_m of sum_x gF(x) . F(x) for the draws of step n:
+// gstep[j][m] = d/d sigma_m of sum_x gF(x) . F(x) for the draws of step n0 + j
+// (blockIdx.x = m, blockIdx.y = j):
 //   F(x, y) = sum_m sigma_m Re[(cx_m, cy_m) exp(i 2 pi (k_x x / nx + k_y y / ny))],
 // so the derivative is Re[cx_m W_x] + Re[cy_m W_y] with W = sum_x exp(i 2 pi k_x x / nx) zsum_r(x).
+// The per-step values are summed over all steps, in step order, at the end of the run,
+// so the checkpoint segmentation does not change a bit.
 template <typename R>
-__global__ void mode_grad_kernel(const R4<double> *__restrict__ zsum, const double2 *__restrict__ tw, const int *__restrict__ mode_kx,
-                                 const int *__restrict__ row_start, int nx, unsigned long long seed, long long n,
-                                 double amp, double *__restrict__ gsig) {
-  const int mo = blockIdx.x;
+__global__ void mode_grad_kernel(const R4<R> *__restrict__ zsum, int nrows, const R2<R> *__restrict__ tw,
+                                 const int *__restrict__ mode_kx, const int *__restrict__ row_start, int nx,
+                                 unsigned long long seed, long long n0, double amp, int nmodes,
+                                 double *__restrict__ gstep) {
+  const int mo = blockIdx.x, j = blockIdx.y;
   int r = 0;
   while (row_start[r + 1] <= mo) ++r;
   const int kx = mode_kx[mo];
-  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  const R4<R> *zs = zsum + ((long long)j * nrows + r) * nx;
+  R a[4] = {R(0), R(0), R(0), R(0)};
   for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-    int j = (kx * x) % nx;
-    if (j < 0) j += nx;
-    const double2 t = tw[j];
-    const R4<double> z = zsum[(long long)r * nx + x];
-    a[0] += t.x * z.x - t.y * z.y;
-    a[1] += t.x * z.y + t.y * z.x;
-    a[2] += t.x * z.z - t.y * z.w;
-    a[3] += t.x * z.w + t.y * z.z;
+    int t = (kx * x) % nx;
+    if (t < 0) t += nx;
+    const R2<R> e = tw[t];
+    const R4<R> z = zs[x];
+    a[0] += e.x * z.x - e.y * z.y;
+    a[1] += e.x * z.y + e.y * z.x;
+    a[2] += e.x * z.z - e.y * z.w;
+    a[3] += e.x * z.w + e.y * z.z;
   }
   __shared__ double red[8][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    for (int off = 16; off > 0; off >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], off);
-    if (lane == 0) red[warp][k] = a[k];
+    double v = (double)a[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][k] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -348,23 +358,33 @@ __global__ void mode_grad_kernel(const R4<double> *__restrict__ zsum, const doub
       for (int k = 0; k < 4; ++k) W[k] += red[w8][k];
     double c[4];
     if constexpr (sizeof(R) == 8) {
-      stir_draw(seed, n, mo, amp, c);
+      stir_draw(seed, n0 + j, mo, amp, c);
     } else {
       float cf[4];
-      stir_draw_f32(seed, n, mo, (float)amp, cf);
+      stir_draw_f32(seed, n0 + j, mo, (float)amp, cf);
       for (int k = 0; k < 4; ++k) c[k] = (double)cf[k];
     }
-    gsig[mo] += c[0] * W[0] - c[1] * W[1] + c[2] * W[2] - c[3] * W[3];
+    gstep[(long long)j * nmodes + mo] = c[0] * W[0] - c[1] * W[1] + c[2] * W[2] - c[3] * W[3];
   }
 }
 
-// exp(+2 pi i t / n) for t < n
-__global__ void adj_twiddle_kernel(double2 *tw, int n) {
+// gsig[m] = sum over the run's steps n = 0 .. N-1 of gstep[n][m], in step order.
+__global__ void mode_sum_kernel(const double *__restrict__ gstep, long long nsteps, int nmodes, double *__restrict__ gsig) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nmodes) return;
+  double s = 0.0;
+  for (long long n = 0; n < nsteps; ++n) s += gstep[n * nmodes + m];
+  gsig[m] = s;
+}
+
+// exp(+2 pi i t / n) for t < n, FP64 and rounded to FP32
+__global__ void adj_twiddle_kernel(double2 *tw, float2 *twf, int n) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   double s, c;
   sincospi(2.0 * t / n, &s, &c);
   tw[t] = make_double2(c, s);
+  twf[t] = make_float2((float)c, (float)s);
 }
 
 template <typename S, int VS, bool MASK, bool FORCE>
@@ -383,12 +403,19 @@ static cudaError_t launch_adjoint_v(const AdjointArgs &a, const Geometry<typenam
   else
     adjoint_kernel<S, VS, MASK, FORCE, false><<<grid, block, 0, st>>>((const S *)a.B, nullptr, (R *)a.kout, g, p, s,
                                                                      (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !FORCE || a.nrows == 0 || !a.kin) return e;
-  zsum_kernel<R><<<dim3((g.nx + 255) / 256, a.nrows), 256, 0, st>>>((const R4<R> *)a.zpart, (int)grid.y, a.nrows, g.nx,
-                                                                   (R4<double> *)a.zsum);
-  mode_grad_kernel<R><<<a.nmodes, 256, 0, st>>>((const R4<double> *)a.zsum, (const double2 *)a.tw, a.mode_kx, a.row_start,
-                                                g.nx, a.seed, a.step, a.amp, a.gsig);
+  return cudaGetLastError();
+}
+
+// dJ/dsigma contributions of nj consecutive steps n0 .. n0 + nj - 1 whose adjoint launches
+// left their row projections in zpart[j] (j = n - n0).
+template <typename R>
+static cudaError_t launch_mode_grads_t(const ModeGradArgs &a, cudaStream_t st) {
+  if (a.nrows == 0 || a.nmodes == 0 || a.nj == 0) return cudaSuccess;
+  zsum_kernel<R><<<dim3((a.nx + 127) / 128, a.nrows, a.nj), 128, 0, st>>>((const R4<R> *)a.zpart, a.nby, a.nrows, a.nx,
+                                                                         (R4<R> *)a.zsum);
+  const void *tw = sizeof(R) == 8 ? a.tw : a.twf;
+  mode_grad_kernel<R><<<dim3(a.nmodes, a.nj), 256, 0, st>>>((const R4<R> *)a.zsum, a.nrows, (const R2<R> *)tw, a.mode_kx,
+                                                           a.row_start, a.nx, a.seed, a.n0, a.amp, a.nmodes, a.gstep);
   return cudaGetLastError();
 }
 
@@ -419,8 +446,15 @@ cudaError_t launch_adjoint_f64(int vset, const AdjointArgs &a, const HostGeom &g
 cudaError_t launch_adjoint_f32(int vset, const AdjointArgs &a, const HostGeom &g, const HostPhys &p, cudaStream_t st) {
   return launch_adjoint_t<float>(vset, a, g, p, st);
 }
-cudaError_t launch_adj_twiddles(double2 *tw, int n, cudaStream_t st) {
-  adj_twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(tw, n);
+cudaError_t launch_mode_grads_f64(const ModeGradArgs &a, cudaStream_t st) { return launch_mode_grads_t<double>(a, st); }
+cudaError_t launch_mode_grads_f32(const ModeGradArgs &a, cudaStream_t st) { return launch_mode_grads_t<float>(a, st); }
+cudaError_t launch_mode_sum(const double *gstep, long long nsteps, int nmodes, double *gsig, cudaStream_t st) {
+  if (nmodes == 0) return cudaSuccess;
+  mode_sum_kernel<<<(nmodes + 127) / 128, 128, 0, st>>>(gstep, nsteps, nmodes, gsig);
+  return cudaGetLastError();
+}
+cudaError_t launch_adj_twiddles(double2 *tw, float2 *twf, int n, cudaStream_t st) {
+  adj_twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(tw, twf, n);
   return cudaGetLastError();
 }
 

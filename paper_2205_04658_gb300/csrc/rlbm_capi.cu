@@ -59,7 +59,7 @@ Modes shell_modes(int kmin, int kmax) {
 bool stirring_on(const rlbm_config &c) { return c.force_amp != 0.0; }
 
 struct Layout {
-  size_t pop[2], nbmask, err, EY, G[2], coef[2], mode_kx, row_start, mode_scale;
+  size_t pop[2], nbmask, err, ctr, EY, G[2], coef[2], mode_kx, row_start, mode_scale;
   size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, total;
   long long plane;
   int pitch, xoff, Q, nrows, nmodes, max_bins, eyp;
@@ -88,6 +88,7 @@ Layout make_layout(const rlbm_config &c) {
   L.pop[1] = take(sb * L.Q * L.plane);
   L.nbmask = take((c.solid || c.walls_y) ? 2 * ncell : 0);
   L.err = take(16);
+  L.ctr = take(16);  // tile counters of the step kernel (two, used by alternate launches)
   L.eyp = (c.ny + 7) / 8 * 8;  // EY rows padded to 8 entries (16-byte TMA strides)
   L.EY = take(2 * rb * (size_t)L.nrows * L.eyp);
   L.G[0] = take(4 * rb * (size_t)L.nrows * c.nx);
@@ -172,6 +173,7 @@ struct rlbm_ctx {
   int cur = 0;           // population buffer holding f*_n
   int64_t step = 0;
   long long nfluid = 0;  // cells that are not solid
+  bool unit_scale = true;  // every stirring multiplier sigma_m is 1
   rlbm_status latched = RLBM_OK;
   std::string msg;
   HostGeom geom;
@@ -179,6 +181,8 @@ struct rlbm_ctx {
   dim3 block{32, 8, 1};       // moments kernel
   int grid_limit = 0;          // step kernel: 0 = one wave of resident CTAs
   int stages = 2;              // shared-memory pipeline depth of the step kernel (1 or 2)
+  int stir_rows = 1;           // stirring rows: 1 = staged with each tile, 2 = read from global memory
+  unsigned launch_seq = 0;     // step-kernel launches so far (selects the tile counter)
   CUtensorMap tmap_in[2], tmap_G[2], tmap_EY;
   std::vector<uint8_t> host_stage;
 
@@ -196,15 +200,19 @@ struct rlbm_ctx {
 
 namespace {
 
-// Step `s` (its tables: s.G_cur of step n) from the buffer behind `ti` into `fout`.
-cudaError_t dispatch_step_raw(rlbm_ctx *c, const CUtensorMap *ti, void *fout, int64_t n, const HostStir &s) {
+// Step n from the buffer behind `ti` into `fout`; its stirring rows come from s.G_cur and,
+// when staged by TMA, through `tgmap` (NULL: the context's table of step parity n & 1).
+cudaError_t dispatch_step_raw(rlbm_ctx *c, const CUtensorMap *ti, void *fout, int64_t n, const HostStir &s,
+                              const CUtensorMap *tgmap = nullptr) {
   unsigned *err = c->at<unsigned>(c->L.err);
-  const void *tg = &c->tmap_G[n & 1], *te = &c->tmap_EY;
+  const void *tg = tgmap ? tgmap : &c->tmap_G[n & 1], *te = &c->tmap_EY;
+  int *ctr = c->at<int>(c->L.ctr);
+  const unsigned seq = c->launch_seq++;
   switch (c->cfg.precision) {
-    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
-    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
-    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
-    default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stream);
+    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
+    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
+    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
+    default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
   }
 }
 
@@ -261,6 +269,23 @@ std::string encode_state_map(const rlbm_ctx *c, void *base, CUtensorMap *out) {
   return "";
 }
 
+// Load map of a stirring-row table {nrows}{nx} R4 at `base` (staged shells, nrows <= 16).
+std::string encode_table_map(const rlbm_ctx *c, void *base, CUtensorMap *out) {
+  EncodeTiledFn encode = tensor_map_encoder();
+  if (!encode) return "cuTensorMapEncodeTiled is not available";
+  const int prec = c->cfg.precision;
+  const CUtensorMapDataType rt = prec == RLBM_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const size_t rb = real_bytes(prec);
+  const cuuint32_t e2[2] = {1, 1};
+  const cuuint64_t dg[2] = {(cuuint64_t)4 * c->cfg.nx, (cuuint64_t)c->L.nrows};
+  const cuuint64_t sg[1] = {(cuuint64_t)4 * c->cfg.nx * rb};
+  const cuuint32_t bg[2] = {4 * 32, (cuuint32_t)c->L.nrows};
+  CUresult r = encode(out, rt, 2, base, dg, sg, bg, e2, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (stirring table map) failed with " + std::to_string((int)r);
+  return "";
+}
+
 std::string make_tensor_maps(rlbm_ctx *c) {
   EncodeTiledFn encode = tensor_map_encoder();
   if (!encode) return "cuTensorMapEncodeTiled is not available";
@@ -278,12 +303,8 @@ std::string make_tensor_maps(rlbm_ctx *c) {
     const size_t rb = real_bytes(prec);
     const cuuint32_t e2[2] = {1, 1};
     for (int b = 0; b < 2; ++b) {
-      const cuuint64_t dg[2] = {(cuuint64_t)4 * c->cfg.nx, (cuuint64_t)c->L.nrows};
-      const cuuint64_t sg[1] = {(cuuint64_t)4 * c->cfg.nx * rb};
-      const cuuint32_t bg[2] = {4 * 32, (cuuint32_t)c->L.nrows};
-      CUresult r = encode(&c->tmap_G[b], rt, 2, c->ws + c->L.G[b], dg, sg, bg, e2, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled (stirring table map) failed with " + std::to_string((int)r);
+      const std::string m = encode_table_map(c, c->ws + c->L.G[b], &c->tmap_G[b]);
+      if (!m.empty()) return m;
     }
     const cuuint64_t de[2] = {(cuuint64_t)2 * c->L.eyp, (cuuint64_t)c->L.nrows};
     const cuuint64_t se[1] = {(cuuint64_t)2 * c->L.eyp * rb};
@@ -339,7 +360,7 @@ HostStir stir_for_step(rlbm_ctx *c, int64_t n) {
   s.seed = c->cfg.seed;
   s.step_new = n + 2;
   s.amp = c->cfg.force_amp;
-  s.mode_scale = c->at<double>(L.mode_scale);
+  s.mode_scale = c->unit_scale ? nullptr : c->at<double>(L.mode_scale);
   return s;
 }
 
@@ -577,6 +598,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
     if ((e = dispatch_init(c, c->ws + L.pop[b], de, dux, duy)) != cudaSuccess) { c->cuda_fail(e, "init kernel"); return bail(RLBM_E_CUDA); }
   }
   if ((e = cudaMemsetAsync(c->ws + L.err, 0, 16, c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaMemsetAsync"); return bail(RLBM_E_CUDA); }
+  if ((e = cudaMemsetAsync(c->ws + L.ctr, 0, 16, c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaMemsetAsync"); return bail(RLBM_E_CUDA); }
   if ((e = stir_prime(c, 0)) != cudaSuccess) { c->cuda_fail(e, "stirring set-up kernels"); return bail(RLBM_E_CUDA); }
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaStreamSynchronize"); return bail(RLBM_E_CUDA); }
   c->cur = 0;
@@ -690,11 +712,13 @@ int32_t rlbm_velocity_classes(int32_t vset, double *out) {
   return Q;
 }
 
-rlbm_status rlbm_set_launch(rlbm_ctx *c, int32_t ctas, int32_t stages) {
+rlbm_status rlbm_set_launch(rlbm_ctx *c, int32_t ctas, int32_t stages, int32_t stir_rows) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
-  if (ctas < 0 || stages < 0 || stages > 2) return c->fail(RLBM_E_INVAL, "ctas must be >= 0 and stages 0, 1 or 2");
+  if (ctas < 0 || stages < 0 || stages > 2 || stir_rows < 0 || stir_rows > 2)
+    return c->fail(RLBM_E_INVAL, "ctas must be >= 0, stages 0, 1 or 2 and stir_rows 0, 1 or 2");
   c->grid_limit = ctas;
   if (stages) c->stages = stages;
+  if (stir_rows) c->stir_rows = stir_rows;
   return RLBM_OK;
 }
 
@@ -705,37 +729,46 @@ rlbm_status rlbm_autotune(rlbm_ctx *c, int32_t reps, double *ms_out) {
   Scoped dev(c->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  // candidate launch shapes: pipeline depth x persistent CTA count (0 = all resident)
+  // candidate launch shapes: pipeline depth x persistent CTA count (0 = all resident) x
+  // where the stirring rows come from (staged with each tile, or global memory)
   const int stage_opts[2] = {2, 1};
   const int grid_opts[4] = {0, 2 * sms, 3 * sms, 4 * sms};
+  const int rows_opts[2] = {1, 2};
+  const int nrows_opts = (c->L.nrows > 0 && c->L.nrows <= 16) ? 2 : 1;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return c->fail(RLBM_E_CUDA, "cudaEventCreate failed");
-  const int save_grid = c->grid_limit, save_stages = c->stages;
+  const int save_grid = c->grid_limit, save_stages = c->stages, save_rows = c->stir_rows;
   float best = 1e30f;
-  int best_grid = save_grid, best_stages = save_stages;
+  int best_grid = save_grid, best_stages = save_stages, best_rows = save_rows;
   const HostStir st = stir_for_step(c, c->step);
   cudaError_t e = cudaSuccess;
-  for (int si = 0; si < 2 && e == cudaSuccess; ++si)
-    for (int gi = 0; gi < 4 && e == cudaSuccess; ++gi) {
-      c->stages = stage_opts[si];
-      c->grid_limit = grid_opts[gi];
-      // the step kernel reads the current buffer and writes the other one; repeating it
-      // leaves the state (and the step counter) as it was
-      if ((e = dispatch_step(c, c->cur, st)) != cudaSuccess) break;  // warm-up
-      cudaEventRecord(e0, c->stream);
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch_step(c, c->cur, st);
-      cudaEventRecord(e1, c->stream);
-      if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_grid = c->grid_limit; best_stages = c->stages; }
-    }
+  for (int ri = 0; ri < nrows_opts && e == cudaSuccess; ++ri)
+    for (int si = 0; si < 2 && e == cudaSuccess; ++si)
+      for (int gi = 0; gi < 4 && e == cudaSuccess; ++gi) {
+        c->stir_rows = rows_opts[ri];
+        c->stages = stage_opts[si];
+        c->grid_limit = grid_opts[gi];
+        // the step kernel reads the current buffer and writes the other one; repeating it
+        // leaves the state (and the step counter) as it was
+        if ((e = dispatch_step(c, c->cur, st)) != cudaSuccess) break;  // warm-up
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch_step(c, c->cur, st);
+        cudaEventRecord(e1, c->stream);
+        if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_grid = c->grid_limit; best_stages = c->stages; best_rows = c->stir_rows; }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->grid_limit = best_grid;
   c->stages = best_stages;
-  if (e != cudaSuccess) { c->grid_limit = save_grid; c->stages = save_stages; return c->cuda_fail(e, "autotune launch"); }
+  c->stir_rows = best_rows;
+  if (e != cudaSuccess) {
+    c->grid_limit = save_grid; c->stages = save_stages; c->stir_rows = save_rows;
+    return c->cuda_fail(e, "autotune launch");
+  }
   if (ms_out) *ms_out = best / reps;
   return check_device(c);
 }
@@ -975,8 +1008,8 @@ namespace {
 struct GradLayout {
   int64_t N;
   int seg, K, nslots;
-  size_t state_bytes, kap_bytes;
-  size_t ckpt, slots, kap[2], acc, zpart, zsum, tw, gsig, out, total;
+  size_t state_bytes, kap_bytes, table_bytes, zpart_bytes;
+  size_t ckpt, slots, kap[2], acc, gst, zpart, zsum, tw, twf, gstep, gsig, out, total;
   long long nblocks;
   int nby;
 };
@@ -989,10 +1022,13 @@ GradLayout grad_layout(const rlbm_ctx *c, int64_t N, int32_t segment) {
   G.K = (int)((N + G.seg - 1) / G.seg);
   G.nslots = G.seg - 1;
   const int prec = c->cfg.precision;
+  const size_t rb = real_bytes(prec);
   G.state_bytes = align_up(store_bytes(prec) * c->L.Q * c->L.plane);
-  G.kap_bytes = align_up(real_bytes(prec) * c->L.Q * c->L.plane);
+  G.kap_bytes = align_up(rb * c->L.Q * c->L.plane);
   G.nby = (c->cfg.ny + 7) / 8;
   G.nblocks = (long long)((c->cfg.nx + 31) / 32) * G.nby;
+  G.table_bytes = align_up(4 * rb * (size_t)c->L.nrows * c->cfg.nx);
+  G.zpart_bytes = 4 * rb * (size_t)G.nby * c->L.nrows * c->cfg.nx;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1)); return o; };
   G.ckpt = take(G.state_bytes * G.K);
@@ -1000,9 +1036,12 @@ GradLayout grad_layout(const rlbm_ctx *c, int64_t N, int32_t segment) {
   G.kap[0] = take(G.kap_bytes);
   G.kap[1] = take(G.kap_bytes);
   G.acc = take(32 * (size_t)G.nblocks);
-  G.zpart = take(4 * real_bytes(prec) * (size_t)G.nby * c->L.nrows * c->cfg.nx);
-  G.zsum = take(32 * (size_t)c->L.nrows * c->cfg.nx);
+  G.gst = take(G.table_bytes * G.seg);                       // stirring rows of a segment's steps
+  G.zpart = take(G.zpart_bytes * G.seg);                     // force-adjoint row projections
+  G.zsum = take(4 * rb * (size_t)c->L.nrows * c->cfg.nx * G.seg);
   G.tw = take(16 * (size_t)c->cfg.nx);
+  G.twf = take(8 * (size_t)c->cfg.nx);
+  G.gstep = take(8 * (size_t)c->L.nmodes * (size_t)N);
   G.gsig = take(8 * (size_t)c->L.nmodes);
   G.out = take(64);
   G.total = off;
@@ -1038,11 +1077,15 @@ rlbm_status rlbm_set_mode_scale(rlbm_ctx *c, const double *sigma, int32_t nmodes
   if (nmodes != c->L.nmodes) return c->fail(RLBM_E_INVAL, "nmodes must equal rlbm_num_modes(ctx) = " + std::to_string(c->L.nmodes));
   if (nmodes == 0) return RLBM_OK;
   if (!sigma) return c->fail(RLBM_E_INVAL, "sigma is NULL");
-  for (int m = 0; m < nmodes; ++m)
+  bool unit = true;
+  for (int m = 0; m < nmodes; ++m) {
     if (!std::isfinite(sigma[m])) return c->fail(RLBM_E_INVAL, "sigma must be finite");
+    unit = unit && sigma[m] == 1.0;
+  }
   Scoped dev(c->device);
   cudaError_t e = cudaMemcpyAsync(c->ws + c->L.mode_scale, sigma, 8 * (size_t)nmodes, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return c->cuda_fail(e, "copy of the mode multipliers");
+  c->unit_scale = unit;
   // the coefficients and table of the current and next step are redrawn with them
   if ((e = stir_prime(c, c->step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
   return check_device(c);
@@ -1073,7 +1116,7 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   char *w = static_cast<char *>(dev_workspace);
   auto ckpt = [&](int k) { return w + G.ckpt + G.state_bytes * (size_t)k; };
   auto slot = [&](int j) { return w + G.slots + G.state_bytes * (size_t)j; };
-  std::vector<CUtensorMap> mck(G.K), msl(G.nslots);
+  std::vector<CUtensorMap> mck(G.K), msl(G.nslots), mgt;
   for (int k = 0; k < G.K; ++k) {
     const std::string m = encode_state_map(c, ckpt(k), &mck[k]);
     if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
@@ -1081,6 +1124,15 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   for (int j = 0; j < G.nslots; ++j) {
     const std::string m = encode_state_map(c, slot(j), &msl[j]);
     if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
+  }
+  auto gtab = [&](int j) { return w + G.gst + G.table_bytes * (size_t)j; };
+  const bool staged_rows = c->L.nrows > 0 && c->L.nrows <= 16;
+  if (staged_rows) {
+    mgt.resize(G.seg);
+    for (int j = 0; j < G.seg; ++j) {
+      const std::string m = encode_table_map(c, gtab(j), &mgt[j]);
+      if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
+    }
   }
   cudaError_t e;
   // ghost rows of wall-bounded lattices are never written: start from zeroed buffers
@@ -1110,57 +1162,78 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   c->step = s0 + nsteps;
 
   // reverse sweep
-  if ((e = launch_adj_twiddles(reinterpret_cast<double2 *>(w + G.tw), c->cfg.nx, c->stream)) != cudaSuccess)
+  if ((e = launch_adj_twiddles(reinterpret_cast<double2 *>(w + G.tw), reinterpret_cast<float2 *>(w + G.twf), c->cfg.nx,
+                               c->stream)) != cudaSuccess)
     return c->cuda_fail(e, "twiddle kernel");
   AdjointArgs a{};
   a.acc = reinterpret_cast<double *>(w + G.acc);
-  a.zpart = w + G.zpart;
-  a.zsum = w + G.zsum;
-  a.tw = w + G.tw;
   a.EY = c->ws + c->L.EY;
   a.nrows = c->L.nrows;
-  a.nmodes = c->L.nmodes;
   a.eyp = c->L.eyp;
-  a.mode_kx = c->at<int>(c->L.mode_kx);
-  a.row_start = c->at<int>(c->L.row_start);
-  a.seed = c->cfg.seed;
-  a.amp = c->cfg.force_amp;
-  a.gsig = reinterpret_cast<double *>(w + G.gsig);
   a.err = c->at<unsigned>(c->L.err);
+  ModeGradArgs mg{};
+  mg.zpart = w + G.zpart;
+  mg.zsum = w + G.zsum;
+  mg.tw = w + G.tw;
+  mg.twf = w + G.twf;
+  mg.nby = G.nby;
+  mg.nrows = c->L.nrows;
+  mg.nx = c->cfg.nx;
+  mg.nmodes = c->L.nmodes;
+  mg.mode_kx = c->at<int>(c->L.mode_kx);
+  mg.row_start = c->at<int>(c->L.row_start);
+  mg.seed = c->cfg.seed;
+  mg.amp = c->cfg.force_amp;
+  double *gstep = reinterpret_cast<double *>(w + G.gstep), *gsig = reinterpret_cast<double *>(w + G.gsig);
   const double cj = 1.0 / ((double)nsteps * (double)c->nfluid);
   int kc = 0;  // kap[kc] holds kappa_{n+1}
-  // the last state: objective only
+  // the last state: objective only (its force terms are multiplied by a zero adjoint)
   a.B = c->ws + c->L.pop[c->cur];
   a.kin = nullptr;
   a.kout = w + G.kap[kc];
   a.cj = cj;
   a.G = c->ws + c->L.G[0];
-  a.step = s0 + nsteps;
+  a.zpart = w + G.zpart;
   if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
   for (int k = G.K - 1; k >= 0; --k) {
     const int64_t lo = (int64_t)k * G.seg, hi = std::min<int64_t>(lo + G.seg, nsteps);
-    // recompute B_lo .. B_{hi-2} from checkpoint k into the slots
-    if (hi - lo >= 2) {
-      if ((e = stir_prime(c, s0 + lo)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
-      for (int64_t n = lo; n <= hi - 2; ++n) {
-        const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
-        c->phys.step = s0 + n;
-        if ((e = dispatch_step_raw(c, ti, slot((int)(n - lo)), s0 + n, stir_for_step(c, s0 + n))) != cudaSuccess)
-          return c->cuda_fail(e, "step kernel launch (recompute)");
+    // stirring rows of steps lo .. hi-1 into the segment's table store, and the states
+    // B_lo .. B_{hi-2} from checkpoint k into the slots
+    if (c->L.nmodes) {
+      HostStir sp = stir_for_step(c, s0 + lo);
+      void *cn = c->ws + c->L.coef[(s0 + lo) & 1], *cn1 = c->ws + c->L.coef[(s0 + lo + 1) & 1];
+      e = c->cfg.precision == RLBM_F64 ? launch_stir_prime_f64(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream)
+                                       : launch_stir_prime_f32(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream);
+      if (e != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
+    }
+    for (int64_t n = lo; n <= hi - 2; ++n) {
+      const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
+      HostStir st = stir_for_step(c, s0 + n);
+      if (c->L.nmodes) {
+        st.G_cur = gtab((int)(n - lo));
+        st.G_next = gtab((int)(n - lo + 1));
       }
+      c->phys.step = s0 + n;
+      if ((e = dispatch_step_raw(c, ti, slot((int)(n - lo)), s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr)) != cudaSuccess)
+        return c->cuda_fail(e, "step kernel launch (recompute)");
     }
     for (int64_t n = hi - 1; n >= lo; --n) {
-      if ((e = stir_prime(c, s0 + n)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
       a.B = n == lo ? ckpt(k) : slot((int)(n - lo - 1));
       a.kin = w + G.kap[kc];
       a.kout = w + G.kap[kc ^ 1];
       a.cj = n >= 1 ? cj : 0.0;
-      a.G = c->ws + c->L.G[(s0 + n) & 1];
-      a.step = s0 + n;
+      a.G = gtab((int)(n - lo));
+      a.zpart = w + G.zpart + G.zpart_bytes * (size_t)(n - lo);
       if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
       kc ^= 1;
     }
+    mg.nj = (int)(hi - lo);
+    mg.n0 = s0 + lo;
+    mg.gstep = gstep + (size_t)lo * c->L.nmodes;
+    e = c->cfg.precision == RLBM_F64 ? launch_mode_grads_f64(mg, c->stream) : launch_mode_grads_f32(mg, c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "mode gradient kernels");
   }
+  if ((e = launch_mode_sum(gstep, nsteps, c->L.nmodes, gsig, c->stream)) != cudaSuccess) return c->cuda_fail(e, "mode sum kernel");
   double *out = reinterpret_cast<double *>(w + G.out);
   if ((e = launch_reduce_partials(a.acc, G.nblocks, out, c->stream)) != cudaSuccess) return c->cuda_fail(e, "reduction kernel");
   // the context continues from step s0 + nsteps
@@ -1169,7 +1242,7 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   double host[4];
   if ((e = cudaMemcpyAsync(host, out, 32, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of the sums");
   if (grad_sigma && c->L.nmodes &&
-      (e = cudaMemcpyAsync(grad_sigma, a.gsig, 8 * (size_t)c->L.nmodes, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+      (e = cudaMemcpyAsync(grad_sigma, gsig, 8 * (size_t)c->L.nmodes, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
     return c->cuda_fail(e, "copy of the mode gradient");
   if (rlbm_status s = check_device(c)) return s;
   if (J) *J = host[3];

@@ -281,6 +281,26 @@ __device__ inline void stir_table_part(const Stir<R> &s, int rank, int ncta, int
     s.G_next[e] = stir_row_entry<R>(coef, kx, rs, (int)(e / nx), (int)(e % nx), nx);
 }
 
+// Byte sizes of the mode data a step launch copies to shared memory for the table of the
+// next step: coefficients (16-byte R4 per mode for FP32, 32 for FP64), k_x and the row
+// ranges, each part padded to 16 bytes (the copies are untiled bulk copies).
+__host__ __device__ inline int mode_coef_bytes(int nmodes, int rbytes) { return nmodes * 4 * rbytes; }
+__host__ __device__ inline int mode_kx_bytes(int nmodes) { return (nmodes * 4 + 15) / 16 * 16; }
+__host__ __device__ inline int mode_rows_bytes(int nrows) { return ((nrows + 1) * 4 + 15) / 16 * 16; }
+
+// This CTA's share of the table of step n+1 from mode data already in shared memory.
+// Entry e goes to CTA e mod ncta; within the CTA the entries are dealt round-robin over
+// the warps (lane-major), so that no single warp carries the table's latency.
+template <typename R>
+__device__ inline void stir_table_staged(const Stir<R> &s, int rank, int ncta, int tid, int nthr, int nx,
+                                         const R4<R> *coef, const int *kx, const int *rs) {
+  const int nwarps = nthr >> 5;
+  const int slot = (tid & 31) * nwarps + (tid >> 5);
+  const long long entries = (long long)s.nrows * nx;
+  for (long long e = rank + (long long)ncta * slot; e < entries; e += (long long)ncta * nthr)
+    s.G_next[e] = stir_row_entry<R>(coef, kx, rs, (int)(e / nx), (int)(e % nx), nx);
+}
+
 // Mode m of step n in FP32 (the draws of the FP32-compute paths; the uniform u_j and
 // the Box-Muller transform in single precision, about 1e-7 relative).
 __device__ inline void stir_draw_f32(unsigned long long seed, long long n, int m, float amp, float out[4]) {

@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(NTHREADS / CPT)
 step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tG,
             const __grid_constant__ CUtensorMap tEY, S *__restrict__ fout,
             const Geometry<typename RealOf<S>::type> g, const Physics<typename RealOf<S>::type> p,
-            const Stir<typename RealOf<S>::type> st, int prep_bytes, unsigned *__restrict__ err) {
+            const Stir<typename RealOf<S>::type> st, int prep_bytes, int srows_in, int *__restrict__ tile_ctr,
+            unsigned seq, unsigned *__restrict__ err) {
   using R = typename RealOf<S>::type;
   using TL = Tile<S, VS>;
   constexpr int NT = NTHREADS / CPT;
@@ -297,80 +298,119 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // every TMA box lands on a 128-byte boundary of this aligned base
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  const bool staged = FORCE && st.nrows > 0 && st.nrows <= TL::MAX_SROWS;
-  const int srows = staged ? st.nrows : 0;
+  // stirring rows staged with the tile (srows_in > 0) or read from global memory (L2)
+  const bool staged = FORCE && srows_in > 0;
+  const int srows = staged ? srows_in : 0;
   const int stage_stride = TL::stage(srows), ey_off = TL::IN_STRIDE + TL::g_bytes(srows);
+  // barriers: one per stage, then one for the mode data; then the tile of each stage
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * stage_stride);
+  int *tile_of = reinterpret_cast<int *>(smem + NST * stage_stride + 32);
 
   const int tid = threadIdx.x;
   const int ntx = (g.nx + TILE_X - 1) / TILE_X, nty = (g.ny + TILE_Y - 1) / TILE_Y;
   const int ntiles = ntx * nty;
-  const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
-  // tile k of this CTA is wid + k * nworkers; its (x, y) tile coordinates advance by
-  // (nworkers mod ntx, nworkers div ntx) with a carry
-  const int stx = nworkers % ntx, sty = nworkers / ntx;
   const uint32_t stage_bytes = TL::IN_BYTES + srows * (TL::G_ROW + TL::EY_ROW);
+  // The mode data of step n+1 (coefficients, k_x, row ranges), copied on its own barrier
+  // when it fits in the `prep` area past the barriers.
+  constexpr int RB = (int)sizeof(R);
+  const int cb = mode_coef_bytes(st.nmodes, RB), kb = mode_kx_bytes(st.nmodes), rb_ = mode_rows_bytes(st.nrows);
+  const bool prep_copy = FORCE && st.nrows > 0 && cb + kb + rb_ <= prep_bytes;
+  unsigned char *prep = smem + NST * stage_stride + 64;
+  // Tiles are handed out by a counter of this launch (launches alternate between two; the
+  // first CTA clears the other one for the next launch).  Every tile is computed the same
+  // way by whichever CTA takes it, so the results do not depend on the order.
+  int *ctr = tile_ctr + (seq & 1u);
 
   if (tid == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s <= NST; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
+    if (wid == 0) tile_ctr[(seq + 1u) & 1u] = 0;
   }
   __syncthreads();
-  int itx = wid % ntx, ity = wid / ntx;  // next tile to stage (thread 0)
-  auto issue = [&](int k) {  // stage the k-th tile of this CTA into stage k % NST
-    const int x0 = itx * TILE_X, y0 = ity * TILE_Y;
-    unsigned char *st0 = smem + (k % NST) * stage_stride;
-    uint64_t *b = &bar[k % NST];
+  // thread 0: stage s takes tile t (or, with t past the end, only completes its barrier)
+  auto fill = [&](int s, int t) {
+    uint64_t *b = &bar[s];
+    tile_of[s] = t < ntiles ? t : -1;
+    if (t >= ntiles) {
+      mbar_arrive(b);
+      return;
+    }
+    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    unsigned char *st0 = smem + s * stage_stride;
     mbar_expect_tx(b, stage_bytes);
     tma_load_3d(st0, &tin, b, x0 + TL::XOFF - TL::V, y0, 0);
     if (staged) {
       tma_load_2d(st0 + TL::IN_STRIDE, &tG, b, 4 * x0, 0);
       tma_load_2d(st0 + ey_off, &tEY, b, 2 * y0, 0);
     }
-    itx += stx; ity += sty;
-    if (itx >= ntx) { itx -= ntx; ++ity; }
   };
-  if (tid == 0)
-    for (int k = 0; k < NST && k < my_tiles; ++k) issue(k);
-
-  // While the first tiles are in flight: this CTA's share of the stirring table of step
-  // n+1 (mode data staged in shared memory past the barriers) and, for the CTAs of
-  // highest index, one Philox draw of step n+2.
-  if (FORCE && st.nrows) {
-    stir_table_part<R>(st, wid, nworkers, tid, NT, g.nx, smem + NST * stage_stride + 64, prep_bytes);
-    if (tid == 32) stir_draws_part<R>(st, nworkers - 1 - wid, nworkers);  // modes m = rank, rank + nworkers, ...
+  int pending = 0;  // thread 0: the tile the next refill will stage (fetched one tile ahead)
+  if (tid == 0) {
+    if (prep_copy) {
+      mbar_expect_tx(&bar[NST], cb + kb + rb_);
+      bulk_load(prep, st.coef_next, cb, &bar[NST]);
+      bulk_load(prep + cb, st.mode_kx, kb, &bar[NST]);
+      bulk_load(prep + cb + kb, st.row_start, rb_, &bar[NST]);
+    }
+    for (int s = 0; s < NST; ++s) fill(s, atomicAdd(ctr, 1));
+    pending = atomicAdd(ctr, 1);
   }
 
-  // Every thread waits for its staged tile (bounded); the vote in the barrier makes the
-  // whole CTA wind down together if a copy never lands.
+  // While the first tiles are in flight: for the CTAs of highest index, one Philox draw
+  // of step n+2 (pure arithmetic; the multipliers are read only when they differ from 1),
+  // and this CTA's share of the table of step n+1 (entry e to CTA e mod nworkers).
+  if (FORCE && st.nrows && tid == 32) stir_draws_part<R>(st, nworkers - 1 - wid, nworkers);
   bool alive = true;
-  {
-    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
+  if (FORCE && st.nrows) {
+    if (prep_copy) {
+      const bool ok = mbar_wait_bounded(&bar[NST], 0, WAIT_CYCLES);
+      if (__syncthreads_or(!ok)) alive = false;
+      if (alive) {
+        const R4<R> *cs = reinterpret_cast<const R4<R> *>(prep);
+        const int *ks = reinterpret_cast<const int *>(prep + cb), *rs = reinterpret_cast<const int *>(prep + cb + kb);
+        stir_table_staged<R>(st, wid, nworkers, tid, NT, g.nx, cs, ks, rs);
+      }
+    } else {
+      stir_table_part<R>(st, wid, nworkers, tid, NT, g.nx, nullptr, 0);
+    }
+  }
+
+  // Every thread waits for the staged tile (bounded); the vote in the barrier makes the
+  // whole CTA wind down together if a copy never lands.
+  if (alive) {
+    const bool ok = mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
     if (__syncthreads_or(!ok)) alive = false;
   }
-  int ctx_ = wid % ntx, cty = wid / ntx;  // tile being computed
-  for (int k = 0; alive && k < my_tiles; ++k) {
-    const int x0 = ctx_ * TILE_X, y0 = cty * TILE_Y;
-    ctx_ += stx; cty += sty;
-    if (ctx_ >= ntx) { ctx_ -= ntx; ++cty; }
-    tile_cells<S, VS, MASK, FORCE, CPT>(smem + (k % NST) * stage_stride, ey_off, fout, x0, y0, tid, g, g, p, st,
-                                        staged, err);
+  for (int k = 0; alive; ++k) {
+    const int s = k % NST;
+    const int t = tile_of[s];
+    if (t < 0) break;
+    tile_cells<S, VS, MASK, FORCE, CPT>(smem + s * stage_stride, ey_off, fout, (t % ntx) * TILE_X,
+                                        (t / ntx) * TILE_Y, tid, g, g, p, st, staged, err);
     if (NST == 1) {  // the only stage is free once every thread is done with it
       __syncthreads();
-      if (tid == 0 && k + 1 < my_tiles) issue(k + 1);
+      if (tid == 0) {
+        fill(0, pending);
+        pending = atomicAdd(ctr, 1);
+      }
     }
-    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % NST], ((k + 1) / NST) & 1, WAIT_CYCLES);
-    if (__syncthreads_or(!ok)) {  // (NST = 2: also the barrier after which stage k % 2 is free)
+    // the next stage's barrier completes with its tile, or at once when it has none
+    const int sn = (k + 1) % NST;
+    const bool ok = mbar_wait_bounded(&bar[sn], ((k + 1) / NST) & 1, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {  // (NST = 2: also the barrier after which stage s is free)
       alive = false;
       break;
     }
-    if (NST >= 2 && tid == 0 && k + NST < my_tiles) issue(k + NST);
+    if (NST >= 2 && tid == 0) {
+      fill(s, pending);
+      pending = atomicAdd(ctr, 1);
+    }
   }
   if (!alive && tid == 0) {
     // a staged copy did not land in time: latch the error and wait (bounded) once more
     // for this CTA's copies still in flight before returning
     atomicOr(err, ERR_TIMEOUT);
-    for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
+    for (int s2 = 0; s2 <= NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
   }
 }
 
@@ -691,16 +731,18 @@ template <typename S, int VS, bool MASK, bool FORCE, int NST>
 static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, const CUtensorMap &tEY, void *fout,
                                  const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,
                                  const Stir<typename RealOf<S>::type> &s, unsigned *err, int grid_limit,
-                                 cudaStream_t stream) {
+                                 int stir_rows, int *tile_ctr, unsigned seq, cudaStream_t stream) {
   using TL = Tile<S, VS>;
   constexpr int CPT = sizeof(S) == 8 ? 1 : 2;
   constexpr int NT = NTHREADS / CPT;
   auto kern = step_kernel<S, VS, MASK, FORCE, CPT, NST>;
-  const int srows = (FORCE && s.nrows > 0 && s.nrows <= TL::MAX_SROWS) ? s.nrows : 0;
+  const int srows = (FORCE && s.nrows > 0 && s.nrows <= TL::MAX_SROWS && stir_rows != 2) ? s.nrows : 0;
   // room to stage the stirring modes of the next step (coefficients, k_x, row ranges)
-  const int prep_bytes = (FORCE && s.nrows && s.nmodes <= 1024)
-                             ? (s.nmodes * (int)(sizeof(R4<typename RealOf<S>::type>) + sizeof(int)) + (s.nrows + 1) * 4 + 127) / 128 * 128
-                             : 0;
+  const int prep_bytes =
+      (FORCE && s.nrows && s.nmodes <= 1024)
+          ? (mode_coef_bytes(s.nmodes, (int)sizeof(typename RealOf<S>::type)) + mode_kx_bytes(s.nmodes) +
+             mode_rows_bytes(s.nrows) + 127) / 128 * 128
+          : 0;
   const int smem = TL::smem(NST, srows) + prep_bytes;
   static int configured_dev = -1, configured_smem = -1, max_blocks = 0, sms = 0;
   int dev = 0;
@@ -720,7 +762,7 @@ static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, 
   if (grid_limit > 0 && grid_limit < workers) workers = grid_limit;
   if (workers > ntiles) workers = ntiles;
   if (workers < 1) workers = 1;
-  kern<<<workers, NT, smem, stream>>>(tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, err);
+  kern<<<workers, NT, smem, stream>>>(tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, srows, tile_ctr, seq, err);
   return cudaGetLastError();
 }
 
@@ -728,23 +770,25 @@ template <typename S, int NST>
 static cudaError_t launch_step_n(int vset, const CUtensorMap &mi, const CUtensorMap &mg, const CUtensorMap &me,
                                  void *fout, const Geometry<typename RealOf<S>::type> &g,
                                  const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &s,
-                                 bool mask, bool force, unsigned *err, int grid_limit, cudaStream_t stream) {
+                                 bool mask, bool force, unsigned *err, int grid_limit, int stir_rows,
+                                 int *ctr, unsigned seq, cudaStream_t stream) {
   if (vset == 3) {
     if (force) {
-      if (mask) return launch_step_v<S, 3, true, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
-      return launch_step_v<S, 3, false, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+      if (mask) return launch_step_v<S, 3, true, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
+      return launch_step_v<S, 3, false, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
     }
-    if (mask) return launch_step_v<S, 3, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
-    return launch_step_v<S, 3, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+    if (mask) return launch_step_v<S, 3, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
+    return launch_step_v<S, 3, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
   }
-  if (mask) return launch_step_v<S, 2, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
-  return launch_step_v<S, 2, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stream);
+  if (mask) return launch_step_v<S, 2, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
+  return launch_step_v<S, 2, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
 }
 
 template <typename S>
 static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, const void *tey, void *fout,
                                  const HostGeom &hg, const HostPhys &hp, const HostStir &hs, unsigned *err,
-                                 int grid_limit, int stages, cudaStream_t stream) {
+                                 int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,
+                                 cudaStream_t stream) {
   using R = typename RealOf<S>::type;
   const Geometry<R> g = to_geom<R>(hg);
   Physics<R> p;
@@ -756,8 +800,9 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, cons
   const Stir<R> s = to_stir<R>(hs);
   const CUtensorMap &mi = *(const CUtensorMap *)tin, &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
   const bool mask = hg.nbmask != nullptr, force = hp.has_force != 0;
-  if (stages == 1) return launch_step_n<S, 1>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stream);
-  return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stream);
+  if (stages == 1)
+    return launch_step_n<S, 1>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, stream);
+  return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, stream);
 }
 
 template <typename S, int VS, bool MASK, bool FORCE, int NST>
@@ -890,8 +935,9 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
   namespace rlbm {                                                                                       \
   cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
-                                int grid_limit, int stages, cudaStream_t st) {                           \
-    return launch_step_t<S>(vset, tin, tg, tey, fout, g, p, s, err, grid_limit, stages, st);            \
+                                int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,      \
+                                cudaStream_t st) {                                                       \
+    return launch_step_t<S>(vset, tin, tg, tey, fout, g, p, s, err, grid_limit, stages, stir_rows, ctr, seq, st); \
   }                                                                                                      \
   cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
                                       int srows, double amp, const long long *bstep, bool mask, int stages, \

@@ -71,7 +71,8 @@ struct BatchTables {
 #define RLBM_DECLARE_LAUNCHERS(SUF)                                                                      \
   cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
-                                int grid_limit, int stages, cudaStream_t st);                            \
+                                int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,      \
+                                cudaStream_t st);                                                        \
   cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st);               \
   cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
                                       int srows, double amp, const long long *bstep, bool mask, int stages, \
@@ -96,21 +97,30 @@ struct AdjointArgs {
   void *kout;              // kappa_n
   double cj;               // objective weight of the state S_n
   double *acc;             // [blocks][4] FP64 accumulators
-  void *zpart;             // [block rows][nrows][nx] R4 of the compute type
-  void *zsum;              // [nrows][nx] double4
-  const void *tw;          // [nx] double2 exp(+2 pi i t / nx)
+  void *zpart;             // [block rows][nrows][nx] R4 of the compute type (this step's slot)
   const void *G, *EY;      // stirring tables of step n
-  int nrows, nmodes, eyp;
+  int nrows, eyp;
+  unsigned *err;
+};
+// The mode gradients of nj consecutive steps from their adjoint launches' row projections.
+struct ModeGradArgs {
+  const void *zpart;       // [nj][block rows][nrows][nx] R4 of the compute type
+  void *zsum;              // [nj][nrows][nx] R4 of the compute type
+  const void *tw;          // [nx] double2 exp(+2 pi i t / nx)
+  const void *twf;         // [nx] float2, the same rounded to FP32
+  int nj, nby, nrows, nx, nmodes;
   const int *mode_kx, *row_start;
   unsigned long long seed;
-  long long step;          // step index n (draws of the mode gradient)
+  long long n0;            // step index of j = 0
   double amp;
-  double *gsig;            // [nmodes] accumulators of d J / d sigma_m
-  unsigned *err;
+  double *gstep;           // [nj][nmodes] per-step d J / d sigma_m (this segment's rows)
 };
 cudaError_t launch_adjoint_f64(int vset, const AdjointArgs &a, const HostGeom &g, const HostPhys &p, cudaStream_t st);
 cudaError_t launch_adjoint_f32(int vset, const AdjointArgs &a, const HostGeom &g, const HostPhys &p, cudaStream_t st);
-cudaError_t launch_adj_twiddles(double2 *tw, int n, cudaStream_t st);
+cudaError_t launch_mode_grads_f64(const ModeGradArgs &a, cudaStream_t st);
+cudaError_t launch_mode_grads_f32(const ModeGradArgs &a, cudaStream_t st);
+cudaError_t launch_mode_sum(const double *gstep, long long nsteps, int nmodes, double *gsig, cudaStream_t st);
+cudaError_t launch_adj_twiddles(double2 *tw, float2 *twf, int n, cudaStream_t st);
 
 // Reductions and spectrum (rlbm_aux.cu)
 cudaError_t launch_counter_inc(long long *counter, cudaStream_t st);

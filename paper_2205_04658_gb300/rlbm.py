@@ -59,7 +59,7 @@ def lib():
             "rlbm_get_state": (c_i32, [P, dp, ctypes.POINTER(c_i64)]),
             "rlbm_set_state": (c_i32, [P, dp, c_i64]),
             "rlbm_num_planes": (c_i32, [P]),
-            "rlbm_set_launch": (c_i32, [P, c_i32, c_i32]),
+            "rlbm_set_launch": (c_i32, [P, c_i32, c_i32, c_i32]),
             "rlbm_autotune": (c_i32, [P, c_i32, dp]),
             "rlbm_velocity_classes": (c_i32, [c_i32, dp]),
             "rlbm_batch_query_workspace": (c_i32, [c_i32, ctypes.POINTER(c_sz)]),
@@ -164,8 +164,8 @@ def rlbm_num_planes(ctx):
     return lib().rlbm_num_planes(ctx)
 
 
-def rlbm_set_launch(ctx, ctas, stages=0):
-    _check(lib().rlbm_set_launch(ctx, int(ctas), int(stages)), ctx)
+def rlbm_set_launch(ctx, ctas, stages=0, stir_rows=0):
+    _check(lib().rlbm_set_launch(ctx, int(ctas), int(stages), int(stir_rows)), ctx)
 
 
 def rlbm_autotune(ctx, reps=10):
@@ -283,8 +283,8 @@ class Lattice:
     def current_step(self):
         return rlbm_current_step(self.ctx)
 
-    def set_launch(self, ctas, stages=0):
-        rlbm_set_launch(self.ctx, ctas, stages)
+    def set_launch(self, ctas, stages=0, stir_rows=0):
+        rlbm_set_launch(self.ctx, ctas, stages, stir_rows)
 
     def autotune(self, reps=10):
         return rlbm_autotune(self.ctx, reps)

@@ -217,7 +217,7 @@ def test_launch_shapes_give_identical_results(R):
     e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=21, u_amp=0.03)
     kw = dict(eta_over_s=0.05, kmin=3, kmax=6, force_amp=1e-3, seed=8, init_eps=e, init_ux=ux, init_uy=uy)
     outs = []
-    for shape in ((0, 2), (0, 1), (7, 2), (3, 1), None):
+    for shape in ((0, 2, 1), (0, 1, 1), (7, 2, 1), (3, 1, 1), (0, 2, 2), (5, 1, 2), None):
         lat = R.Lattice(nx, ny, precision="f32", **kw)
         if shape is None:
             assert lat.autotune(3) > 0
