@@ -232,24 +232,41 @@ template <> __device__ __forceinline__ void sincospi_R<float>(float a, float *s,
 
 // One entry of the per-row stirring table of a step:
 //   G_r(x) = sum_{m in row r} (cx_m, cy_m) exp(i 2 pi k_x,m x / nx),
-// the phase evaluated from the exact integer residue k_x,m x mod nx.  `coef`, `kx` and
-// `row_start` may live in shared memory.
+// the phase evaluated from the exact integer residue k_x,m x mod nx.  The modes of a row
+// are summed in four interleaved parts (m = first + l, l + 4, ...), combined as
+// (p0 + p1) + (p2 + p3): the table builders that split an entry over four lanes and those
+// that do not then give the same bits.  `coef`, `kx` and `row_start` may live in shared
+// memory.
 template <typename R>
-__device__ inline R4<R> stir_row_entry(const R4<R> *coef, const int *kx, const int *row_start, int r, int x, int nx) {
+__device__ inline R4<R> stir_entry_part(const R4<R> *coef, const int *kx, const int *row_start, int r, int x, int nx,
+                                        int l4) {
   R4<R> g{R(0), R(0), R(0), R(0)};
   const int m1 = row_start[r + 1];
-  for (int m = row_start[r]; m < m1; ++m) {
+  for (int m = row_start[r] + l4; m < m1; m += 4) {
     int j = (kx[m] * x) % nx;  // |k_x| < nx / 2 and x < nx <= 32768: no 32-bit overflow
     if (j < 0) j += nx;
     R sn, cs;
     sincospi_R<R>(R(2 * j) / R(nx), &sn, &cs);
     const R4<R> c = coef[m];
-    g.x += c.x * cs - c.y * sn;
-    g.y += c.x * sn + c.y * cs;
-    g.z += c.z * cs - c.w * sn;
-    g.w += c.z * sn + c.w * cs;
+    g.x = fma(c.x, cs, fma(-c.y, sn, g.x));
+    g.y = fma(c.x, sn, fma(c.y, cs, g.y));
+    g.z = fma(c.z, cs, fma(-c.w, sn, g.z));
+    g.w = fma(c.z, sn, fma(c.w, cs, g.w));
   }
   return g;
+}
+
+template <typename R> __device__ __forceinline__ R4<R> r4_sum(const R4<R> &a, const R4<R> &b) {
+  return R4<R>{a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
+}
+
+template <typename R>
+__device__ inline R4<R> stir_row_entry(const R4<R> *coef, const int *kx, const int *row_start, int r, int x, int nx) {
+  const R4<R> p0 = stir_entry_part<R>(coef, kx, row_start, r, x, nx, 0);
+  const R4<R> p1 = stir_entry_part<R>(coef, kx, row_start, r, x, nx, 1);
+  const R4<R> p2 = stir_entry_part<R>(coef, kx, row_start, r, x, nx, 2);
+  const R4<R> p3 = stir_entry_part<R>(coef, kx, row_start, r, x, nx, 3);
+  return r4_sum<R>(r4_sum<R>(p0, p1), r4_sum<R>(p2, p3));
 }
 
 template <typename R>
@@ -289,16 +306,41 @@ __host__ __device__ inline int mode_kx_bytes(int nmodes) { return (nmodes * 4 + 
 __host__ __device__ inline int mode_rows_bytes(int nrows) { return ((nrows + 1) * 4 + 15) / 16 * 16; }
 
 // This CTA's share of the table of step n+1 from mode data already in shared memory.
-// Entry e goes to CTA e mod ncta; within the CTA the entries are dealt round-robin over
-// the warps (lane-major), so that no single warp carries the table's latency.
+// Entry e goes to CTA e mod ncta.  Within the CTA, quads of lanes take the entries (dealt
+// round-robin over the warps) and split each entry's modes four ways, summing with two
+// shuffles: a row of the shell holds up to a dozen modes, and the longest entry, not the
+// number of entries, sets the time.  Every thread reaches the shuffles the same number of
+// times (all lanes of a warp take part).
 template <typename R>
 __device__ inline void stir_table_staged(const Stir<R> &s, int rank, int ncta, int tid, int nthr, int nx,
                                          const R4<R> *coef, const int *kx, const int *rs) {
-  const int nwarps = nthr >> 5;
-  const int slot = (tid & 31) * nwarps + (tid >> 5);
+  const int nwarps = nthr >> 5, nquads = nthr >> 2;
+  const int lane = tid & 31, warp = tid >> 5, l4 = tid & 3;
+  const int quad = warp + nwarps * (lane >> 2);  // quads of one warp are nwarps apart
   const long long entries = (long long)s.nrows * nx;
-  for (long long e = rank + (long long)ncta * slot; e < entries; e += (long long)ncta * nthr)
-    s.G_next[e] = stir_row_entry<R>(coef, kx, rs, (int)(e / nx), (int)(e % nx), nx);
+  const long long mine = entries > rank ? (entries - 1 - rank) / ncta + 1 : 0;  // this CTA's entries
+  for (long long base = 0; base < mine; base += nquads) {
+    const long long i = base + quad;
+    R4<R> g{R(0), R(0), R(0), R(0)};
+    int r = 0, x = 0;
+    if (i < mine) {
+      const long long e = rank + i * ncta;
+      r = (int)(e / nx);
+      x = (int)(e % nx);
+      g = stir_entry_part<R>(coef, kx, rs, r, x, nx, l4);
+    }
+    // lane 0 of the quad ends with (p0 + p1) + (p2 + p3), as stir_row_entry
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+      R4<R> o;
+      o.x = __shfl_xor_sync(0xffffffffu, g.x, off);
+      o.y = __shfl_xor_sync(0xffffffffu, g.y, off);
+      o.z = __shfl_xor_sync(0xffffffffu, g.z, off);
+      o.w = __shfl_xor_sync(0xffffffffu, g.w, off);
+      g = r4_sum<R>(g, o);
+    }
+    if (i < mine && l4 == 0) s.G_next[(long long)r * nx + x] = g;
+  }
 }
 
 // Mode m of step n in FP32 (the draws of the FP32-compute paths; the uniform u_j and
