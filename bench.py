@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--shape", default=None,
+                   help="ctas,stages,stir_rows: use this launch shape instead of tuning (profiling runs)")
     p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512"],
                    help="stirred: one lattice (default); ensemble64: 64 stirred members of uneven sizes "
                         "advanced by one persistent launch per step; adjoint512: gradient of the kinetic "
@@ -248,10 +250,16 @@ def run_gb300(args):
     cells = nx * ny
     kw = workload(args, rank)
     lat = rlbm.Lattice(nx, ny, precision=prec, **kw)
-    tuned_ms = lat.autotune(20)  # launch shape (pipeline depth, CTA count); the state is not advanced
     stream = lat.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    shape = tune_flushed(lat, flush, torch)  # the same candidates, timed under the timed region's L2 flush
+    if args.shape:
+        tuned_ms = None
+        c_, s_, r_ = (int(v) for v in args.shape.split(","))
+        lat.set_launch(c_, s_, r_)
+        shape = {"ctas": c_, "stages": s_, "stir_rows": r_, "ms": None}
+    else:
+        tuned_ms = lat.autotune(20)  # launch shape (pipeline depth, CTA count); the state is not advanced
+        shape = tune_flushed(lat, flush, torch)  # the same candidates, timed under the timed region's L2 flush
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
