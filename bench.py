@@ -42,16 +42,20 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--nx", type=int, default=1024)
     p.add_argument("--ny", type=int, default=1024)
-    p.add_argument("--precision", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    p.add_argument("--precision", default=None, choices=["f64", "f32", "f16", "bf16"],
+                   help="storage type (default: f32; f16 for the graphene and ensemble workloads)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--shape", default=None,
                    help="ctas,stages,stir_rows: use this launch shape instead of tuning (profiling runs)")
-    p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512"],
+    p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512", "graphene"],
                    help="stirred: one lattice (default); ensemble64: 64 stirred members of uneven sizes "
                         "advanced by one persistent launch per step; adjoint512: gradient of the kinetic "
                         "energy of a 512^2 stirred run (2000 steps) by the checkpointed adjoint")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.precision is None:
+        a.precision = "f16" if a.workload in ("graphene", "ensemble64") else "f32"
+    return a
 
 
 def workload(args, rank):
@@ -498,6 +502,55 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_graphene(args):
+    """The graphene-like sample: 2048 x 512, x periodic, bounce-back walls in y, uniform
+    body force 1e-6 along x, discs of radius 6 at 1 %, 5 % and 15 % area (geometry seeds
+    31, 35, 315), eta/s 0.05, in the requested storage type (default FP16 with stochastic
+    rounding).  One line per area fraction.  The two population buffers (2 x 71 MB in
+    FP16) fit in L2, so L2 is flushed (a 256 MiB write) before every timed step."""
+    import numpy as np
+    import torch
+    from paper_2205_04658_gb300 import rlbm, inputs
+    torch.cuda.set_device(0)
+    rlbm.lib()
+    prec = args.precision
+    nx, ny = 2048, 512
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for frac, gseed in ((0.01, 31), (0.05, 35), (0.15, 315)):
+        mask, _ = inputs.disc_mask(nx, ny, radius=6, fraction=frac, seed=gseed, walls_y=True)
+        lat = rlbm.Lattice(nx, ny, precision=prec, walls_y=1, solid=mask, body_force=(1e-6, 0.0), eta_over_s=0.05)
+        lat.autotune(10)
+        stream = lat.stream
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                flush.zero_()
+                lat.step(1)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                lat.step(1)
+                b.record(stream)
+        torch.cuda.synchronize()
+        lat.sync()
+        times = [a.elapsed_time(b) for a, b in ev]
+        lat.close()
+        ms = float(np.mean(times))
+        cells = nx * ny
+        fluid = int((mask == 0).sum())
+        alg = ALG_BYTES[prec] * cells + 2 * cells  # populations + the 16-bit neighbour mask
+        line = {"metric": METRIC, "value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+                "config": {"workload": "graphene-like 2048x512, walls in y, body force 1e-6, discs r=6 at %d %% "
+                                       "(%d fluid cells), %s storage" % (round(100 * frac), fluid, prec.upper()),
+                           "l2": "flushed before every timed step (256 MiB write)"},
+                "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": measured_peak()[0],
+                             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / measured_peak()[0],
+                             "alg_bytes_per_cell": alg / cells}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -506,6 +559,8 @@ def main():
         run_ensemble(args)
     elif args.workload == "adjoint512":
         run_adjoint(args)
+    elif args.workload == "graphene":
+        run_graphene(args)
     else:
         run_gb300(args)
 

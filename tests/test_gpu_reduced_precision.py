@@ -107,6 +107,41 @@ def test_developed_stirred_slice_200_steps(R, precision, bound):
         lat.close()
 
 
+@pytest.mark.parametrize("precision,bound", [("f16", 1e-3), ("bf16", 1e-2)])
+def test_walls_discs_body_force_slice_200_steps(R, precision, bound):
+    """The graphene-like shape at reduced size: x periodic, bounce-back walls in y, discs
+    of radius 6 at 5 % area, a uniform body force along x; the flow is developed for 1000
+    steps by the FP64 library path (itself checked against the oracle to 1e-10 with walls
+    and discs), quantised to FP16, and the 200-step slice from it is compared with the
+    oracle run from the same start."""
+    nx, ny = 192, 64
+    mask, _ = inputs.disc_mask(nx, ny, radius=6, fraction=0.05, seed=35, walls_y=True)
+    cfg = dict(nx=nx, ny=ny, walls_y=1, solid=mask, body_force=(2e-4, 0.0), eta_over_s=0.05)
+    kw = {k: v for k, v in cfg.items() if k not in ("nx", "ny")}
+    dev = R.Lattice(nx, ny, precision="f64", **kw)
+    dev.step(1000)
+    h, step = dev.get_state()
+    dev.close()
+    h = h.astype(np.float16).astype(np.float64)
+    o = O.Oracle(cfg)
+    hp = np.zeros((h.shape[0], ny + 2, nx))  # the oracle's window carries the wall rows y = -1, ny
+    hp[:, 1:-1] = h
+    o.fstar = unfold(R, o, hp)
+    o.fstar[:, o.win.solid] = 0.0
+    o.step_index = step
+    o.run(200)
+    E, UX, UY, _ = o.fields()
+    ref = (E[1:-1], UX[1:-1], UY[1:-1])
+    lat = R.Lattice(nx, ny, precision=precision, **kw)
+    lat.set_state(h, step)
+    lat.step(200)
+    gpu = lat.moments()
+    lat.close()
+    err = u_error(gpu, ref)
+    print("walls+discs slice %s: u error / max|u| = %.2e (max|u| = %.2e)" % (precision, err, np.abs(ref[1]).max()))
+    assert err <= bound
+
+
 def test_stochastic_rounding_repeats_exactly(R):
     kw = dict(eta_over_s=0.05, kmin=2, kmax=4, force_amp=1e-3, seed=9)
     outs = []
