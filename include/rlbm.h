@@ -207,6 +207,12 @@ RLBM_API rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers,
 /* Launch shape of the batched step kernel (as rlbm_set_launch). */
 RLBM_API rlbm_status rlbm_batch_set_launch(rlbm_batch *b, int32_t ctas, int32_t stages);
 
+/* Autotuner of the batched launch: times every launch shape it knows (pipeline depth x
+ * persistent CTA count), `reps` launches each, on the members' current states without
+ * advancing them, and keeps the fastest.  *ms_out (may be NULL) receives its time per
+ * batched step in milliseconds.  Syncs the batch's stream.  The paper has no counterpart. */
+RLBM_API rlbm_status rlbm_batch_autotune(rlbm_batch *b, int32_t reps, double *ms_out);
+
 /* Advance every member by nsteps >= 0 steps.  Async. */
 RLBM_API rlbm_status rlbm_batch_step(rlbm_batch *b, int64_t nsteps);
 

@@ -840,6 +840,18 @@ bool same_physics(const rlbm_config &a, const rlbm_config &b) {
          a.rounding == b.rounding && a.fp64_landau_vmax == b.fp64_landau_vmax;
 }
 
+// The member table as the batched kernel reads it: every member's current buffer and
+// step (members may have been stepped on their own), and the batch step counter at 0.
+cudaError_t batch_prepare(rlbm_batch *b) {
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    b->h_mem[i].cur0 = b->members[i]->cur;
+    b->h_mem[i].step0 = b->members[i]->step;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(MemberDesc) * b->h_mem.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bstep, 0, sizeof(long long), b->stream);
+  return e;
+}
+
 cudaError_t batch_launch_one(rlbm_batch *b) {
   rlbm_ctx *c0 = b->members[0];
   BatchTables bt{b->d_mem, b->d_tile0, b->d_entry0, b->d_draw0, (int)b->members.size()};
@@ -924,7 +936,7 @@ rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers, void *de
   if ((e = cudaMemcpyAsync(b->d_tile0, tile0.data(), sizeof(int) * (nmembers + 1), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
       (e = cudaMemcpyAsync(b->d_entry0, entry0.data(), sizeof(long long) * (nmembers + 1), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
       (e = cudaMemcpyAsync(b->d_draw0, draw0.data(), sizeof(int) * (nmembers + 1), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(b->stream)) != cudaSuccess) {
+      (e = batch_prepare(b)) != cudaSuccess || (e = cudaStreamSynchronize(b->stream)) != cudaSuccess) {
     g_thread_error = std::string("batch tables upload: ") + cudaGetErrorString(e);
     delete b;
     return RLBM_E_CUDA;
@@ -942,6 +954,62 @@ rlbm_status rlbm_batch_set_launch(rlbm_batch *b, int32_t ctas, int32_t stages) {
   return RLBM_OK;
 }
 
+rlbm_status rlbm_batch_autotune(rlbm_batch *b, int32_t reps, double *ms_out) {
+  if (!b) { g_thread_error = "batch is NULL"; return RLBM_E_INVAL; }
+  if (reps < 1) return b->fail(RLBM_E_INVAL, "reps must be >= 1");
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (b->members[i]->latched != RLBM_OK) return b->fail(RLBM_E_STATE, "member " + std::to_string(i) + " is in an error state");
+  Scoped dev(b->device);
+  // the trial launches read the member table of the members' current states
+  if (cudaError_t e0_ = batch_prepare(b); e0_ != cudaSuccess) return b->cuda_fail(e0_, "batch descriptor upload");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  BatchTables bt{b->d_mem, b->d_tile0, b->d_entry0, b->d_draw0, (int)b->members.size()};
+  rlbm_ctx *c0 = b->members[0];
+  const double amp = c0->cfg.force_amp;
+  // one batched step without advancing the step counter: every member's next buffer and
+  // next-step tables are rewritten with the same values, so repeating it changes nothing
+  auto trial = [&]() -> cudaError_t {
+    switch (c0->cfg.precision) {
+      case RLBM_F64: return launch_batch_step_f64(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream);
+      case RLBM_F32: return launch_batch_step_f32(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream);
+      case RLBM_F16: return launch_batch_step_f16(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream);
+      default: return launch_batch_step_bf16(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream);
+    }
+  };
+  const int stage_opts[2] = {2, 1};
+  const int grid_opts[5] = {0, sms, 2 * sms, 3 * sms, 4 * sms};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return b->fail(RLBM_E_CUDA, "cudaEventCreate failed");
+  const int save_grid = b->grid_limit, save_stages = b->stages;
+  float best = 1e30f;
+  int best_grid = save_grid, best_stages = save_stages;
+  cudaError_t e = cudaSuccess;
+  for (int si = 0; si < 2 && e == cudaSuccess; ++si)
+    for (int gi = 0; gi < 5 && e == cudaSuccess; ++gi) {
+      b->stages = stage_opts[si];
+      b->grid_limit = grid_opts[gi];
+      if ((e = trial()) != cudaSuccess) break;  // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = trial();
+      cudaEventRecord(e1, b->stream);
+      if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_grid = b->grid_limit; best_stages = b->stages; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->grid_limit = e == cudaSuccess ? best_grid : save_grid;
+  b->stages = e == cudaSuccess ? best_stages : save_stages;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
+  if (e != cudaSuccess) return b->cuda_fail(e, "batch autotune launch");
+  if (ms_out) *ms_out = best / reps;
+  // device errors (if any) surface through the members' next syncing call
+  return RLBM_OK;
+}
+
 rlbm_status rlbm_batch_step(rlbm_batch *b, int64_t nsteps) {
   if (!b) { g_thread_error = "batch is NULL"; return RLBM_E_INVAL; }
   if (nsteps < 0) return b->fail(RLBM_E_INVAL, "nsteps must be >= 0");
@@ -949,13 +1017,7 @@ rlbm_status rlbm_batch_step(rlbm_batch *b, int64_t nsteps) {
     if (b->members[i]->latched != RLBM_OK) return b->fail(RLBM_E_STATE, "member " + std::to_string(i) + " is in an error state");
   if (nsteps == 0) return RLBM_OK;
   Scoped dev(b->device);
-  // the members' current buffers and steps (they may have been stepped on their own)
-  for (size_t i = 0; i < b->members.size(); ++i) {
-    b->h_mem[i].cur0 = b->members[i]->cur;
-    b->h_mem[i].step0 = b->members[i]->step;
-  }
-  cudaError_t e = cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(MemberDesc) * b->h_mem.size(), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bstep, 0, sizeof(long long), b->stream);
+  cudaError_t e = batch_prepare(b);
   if (e != cudaSuccess) return b->cuda_fail(e, "batch descriptor upload");
   // Whole chunks of steps replay one captured CUDA graph (kernel + counter advance per
   // step); the remainder, and any run on the legacy default stream (which cannot be

@@ -66,6 +66,7 @@ def lib():
             "rlbm_batch_init": (c_i32, [ctypes.POINTER(P), c_i32, P, c_sz, P, ctypes.POINTER(P)]),
             "rlbm_batch_set_launch": (c_i32, [P, c_i32, c_i32]),
             "rlbm_batch_step": (c_i32, [P, c_i64]),
+            "rlbm_batch_autotune": (c_i32, [P, c_i32, dp]),
             "rlbm_batch_last_error": (ctypes.c_char_p, [P]),
             "rlbm_batch_free": (None, [P]),
             "rlbm_spectrum_noalloc": (c_i32, [P, P, c_i32, c_i32, c_i32, P, P]),
@@ -351,6 +352,12 @@ def rlbm_batch_step(b, nsteps):
     _bcheck(lib().rlbm_batch_step(b, int(nsteps)), b)
 
 
+def rlbm_batch_autotune(b, reps=5):
+    ms = ctypes.c_double(0.0)
+    _bcheck(lib().rlbm_batch_autotune(b, int(reps), ctypes.byref(ms)), b)
+    return ms.value
+
+
 def rlbm_batch_free(b):
     lib().rlbm_batch_free(b)
 
@@ -373,6 +380,9 @@ class Batch:
 
     def set_launch(self, ctas, stages=0):
         rlbm_batch_set_launch(self.b, ctas, stages)
+
+    def autotune(self, reps=5):
+        return rlbm_batch_autotune(self.b, reps)
 
     def close(self):
         if getattr(self, "b", None) is not None:

@@ -53,7 +53,12 @@ def test_batch_equals_members_stepped_alone(R, precision):
     for lat in alone:
         lat.step(nsteps)
     b = R.Batch(batched, stream=stream)
+    # tuned before the first step too (the member table is valid from rlbm_batch_init on)
+    assert b.autotune(1) > 0.0
     b.step(nsteps)
+    # the autotuner changes the launch shape only: the members are not advanced and the
+    # next steps are the same arithmetic
+    assert b.autotune(2) > 0.0
     b.step(3)
     for lat in alone:
         lat.step(3)
