@@ -236,7 +236,7 @@ adjoint_kernel(const S *__restrict__ B, const typename RealOf<S>::type *__restri
     if (FORCE) {
       for (int r = 0; r < st.nrows; ++r) {
         const R4<R> G = st.G[(long long)r * g.nx + x];
-        const R2<R> E = st.EY[(long long)r * st.eyp + y];
+        const R2<R> E = ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp, y);
         Fx = fma(G.x, E.x, fma(-G.y, E.y, Fx));
         Fy = fma(G.z, E.x, fma(-G.w, E.y, Fy));
       }
@@ -270,7 +270,7 @@ adjoint_kernel(const S *__restrict__ B, const typename RealOf<S>::type *__restri
       for (int j = 0; j < 8; ++j) {
         const int yy = blockIdx.y * 8 + j;
         if (yy >= g.ny) break;
-        const R2<R> E = st.EY[(long long)r * st.eyp + yy];
+        const R2<R> E = ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp, yy);
         const R2<R> F = sF[j][lx];
         z.x += F.x * E.x;
         z.y += F.x * E.y;

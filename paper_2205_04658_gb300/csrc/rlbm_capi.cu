@@ -377,12 +377,6 @@ cudaError_t stir_prime(rlbm_ctx *c, int64_t n) {
   }
 }
 
-template <typename R> void put_pairs(std::vector<uint8_t> &out, const std::vector<double> &re, const std::vector<double> &im) {
-  out.resize(re.size() * 2 * sizeof(R));
-  R *p = reinterpret_cast<R *>(out.data());
-  for (size_t i = 0; i < re.size(); ++i) { p[2 * i] = (R)re[i]; p[2 * i + 1] = (R)im[i]; }
-}
-
 // Reads the device error word after a synchronisation and latches it.
 rlbm_status check_device(rlbm_ctx *c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -550,16 +544,25 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   // stirring tables (library's own; FP64-built, stored in the compute type)
   if (L.nmodes) {
     const Modes m = shell_modes(cfg->kmin, cfg->kmax);
-    std::vector<double> ey_re((size_t)L.nrows * L.eyp, 0.0), ey_im((size_t)L.nrows * L.eyp, 0.0);
+    // phase rows in the layout of ey_index: per row 2 eyp reals, blocks of 8 lattice rows,
+    // entry k of a block = (Re y, Re y+4, Im y, Im y+4) for y = 8 b + k
+    std::vector<double> ey((size_t)L.nrows * 2 * L.eyp, 0.0);
     for (int r = 0; r < L.nrows; ++r)
       for (int y = 0; y < cfg->ny; ++y) {
         const long long j = ((long long)m.row_ky[r] * y) % cfg->ny;
-        ey_re[(size_t)r * L.eyp + y] = std::cos(2.0 * M_PI * j / cfg->ny);
-        ey_im[(size_t)r * L.eyp + y] = std::sin(2.0 * M_PI * j / cfg->ny);
+        const size_t i = (size_t)r * 2 * L.eyp + ey_index(y);
+        ey[i] = std::cos(2.0 * M_PI * j / cfg->ny);
+        ey[i + 2] = std::sin(2.0 * M_PI * j / cfg->ny);
       }
     keep.emplace_back();
-    if (cfg->precision == RLBM_F64) put_pairs<double>(keep.back(), ey_re, ey_im);
-    else put_pairs<float>(keep.back(), ey_re, ey_im);
+    if (cfg->precision == RLBM_F64) {
+      keep.back().resize(ey.size() * sizeof(double));
+      std::memcpy(keep.back().data(), ey.data(), ey.size() * sizeof(double));
+    } else {
+      keep.back().resize(ey.size() * sizeof(float));
+      float *pf = reinterpret_cast<float *>(keep.back().data());
+      for (size_t i = 0; i < ey.size(); ++i) pf[i] = (float)ey[i];
+    }
     const std::vector<double> ones(L.nmodes, 1.0);
     keep.emplace_back(reinterpret_cast<const uint8_t *>(ones.data()), reinterpret_cast<const uint8_t *>(ones.data()) + 8 * ones.size());
     if ((e = put(L.mode_scale, keep.back().data(), keep.back().size())) != cudaSuccess ||

@@ -298,6 +298,16 @@ __device__ inline void stir_table_part(const Stir<R> &s, int rank, int ncta, int
     s.G_next[e] = stir_row_entry<R>(coef, kx, rs, (int)(e / nx), (int)(e % nx), nx);
 }
 
+// The per-row phase table EY_r(y) = exp(i 2 pi k_y(r) y / ny): each k_y row holds 2 eyp
+// reals in blocks of 8 lattice rows; entry k (0..3) of block b holds
+// (Re y, Re y+4, Im y, Im y+4) for y = 8b + k.  One 16-byte load then gives a thread of the
+// paired kernels (cells y and y + 4) both phases as register pairs.
+__host__ __device__ __forceinline__ int ey_index(int y) { return (y >> 3) * 16 + (y & 3) * 4 + ((y >> 2) & 1); }
+template <typename R> __device__ __forceinline__ R2<R> ey_at(const R *row, int y) {
+  const int i = ey_index(y);
+  return R2<R>{row[i], row[i + 2]};
+}
+
 // Byte sizes of the mode data a step launch copies to shared memory for the table of the
 // next step: coefficients (16-byte R4 per mode for FP32, 32 for FP64), k_x and the row
 // ranges, each part padded to 16 bytes (the copies are untiled bulk copies).

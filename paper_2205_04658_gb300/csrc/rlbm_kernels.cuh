@@ -88,14 +88,14 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
       if (FORCE) {
         if (staged) {
           const R4<R> *Gs = reinterpret_cast<const R4<R> *>(stg + TL::IN_STRIDE) + lx;
-          const R2<R> *Es = reinterpret_cast<const R2<R> *>(stg + ey_off) + ly;
-          // F = sum_r Re[G_r(x) EY_r(y)], two rows per iteration
+          const R *Er = reinterpret_cast<const R *>(stg + ey_off) + ey_index(ly);
+          // F = sum_r Re[G_r(x) EY_r(y)], two rows per iteration (staged phase rows: 16 reals)
           R Fx2 = R(0), Fy2 = R(0);
           int r = 0;
 #pragma unroll 1
           for (; r + 1 < st.nrows; r += 2) {
             const R4<R> G0 = Gs[r * TILE_X], G1 = Gs[(r + 1) * TILE_X];
-            const R2<R> E0 = Es[r * TILE_Y], E1 = Es[(r + 1) * TILE_Y];
+            const R2<R> E0{Er[r * 16], Er[r * 16 + 2]}, E1{Er[(r + 1) * 16], Er[(r + 1) * 16 + 2]};
             Fx = fma(G0.x, E0.x, fma(-G0.y, E0.y, Fx));
             Fy = fma(G0.z, E0.x, fma(-G0.w, E0.y, Fy));
             Fx2 = fma(G1.x, E1.x, fma(-G1.y, E1.y, Fx2));
@@ -103,7 +103,7 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
           }
           if (r < st.nrows) {
             const R4<R> G0 = Gs[r * TILE_X];
-            const R2<R> E0 = Es[r * TILE_Y];
+            const R2<R> E0{Er[r * 16], Er[r * 16 + 2]};
             Fx = fma(G0.x, E0.x, fma(-G0.y, E0.y, Fx));
             Fy = fma(G0.z, E0.x, fma(-G0.w, E0.y, Fy));
           }
@@ -112,7 +112,7 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         } else {
           for (int r = 0; r < st.nrows; ++r) {
             const R4<R> G = st.G_cur[(long long)r * g.nx + x];
-            const R2<R> E = st.EY[(long long)r * st.eyp + y];
+            const R2<R> E = ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp, y);
             Fx += G.x * E.x - G.y * E.y;
             Fy += G.z * E.x - G.w * E.y;
           }
@@ -195,8 +195,11 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         if (MASK && ((nbB >> (4 - 3 * sy - sx)) & 1u)) vB = load_h_s<S, float>(own + DB);
         acc = fma(T(wts.beta2[q][3]), T(vA, vB), acc);
       }
-      // a lane without fluid (outside the lattice or solid) computes the rest state
-      h[q] = both ? acc : T(flA ? acc.v.x : 0.0f, flB ? acc.v.y : 0.0f);
+      h[q] = acc;
+    }
+    if (!both) {  // a lane without fluid (outside the lattice or solid) computes the rest state
+#pragma unroll
+      for (int q = 0; q < Q; ++q) h[q] = T(flA ? h[q].v.x : 0.0f, flB ? h[q].v.y : 0.0f);
     }
     const Mom<T> M = moments_of<T, T, VS, FORCE>(h);
     const Macro<T> m = cell_macro_pair<VS>(h, M, p.vmax2);
@@ -205,21 +208,23 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     if (FORCE) {
       if (staged) {
         const R4<float> *Gs = reinterpret_cast<const R4<float> *>(stg + TL::IN_STRIDE) + lx;
-        const R2<float> *Es = reinterpret_cast<const R2<float> *>(stg + ey_off) + ly;
+        // (Re yA, Re yB, Im yA, Im yB) of each staged phase row: the pairs load as they are used
+        const R4<float> *Es = reinterpret_cast<const R4<float> *>(stg + ey_off) + ly;
 #pragma unroll 1
         for (int r = 0; r < st.nrows; ++r) {
           const R4<float> G = Gs[r * TILE_X];
-          const R2<float> EA = Es[r * TILE_Y], EB = Es[r * TILE_Y + TILE_Y / 2];
-          const T Ere(EA.x, EB.x), Eim(EA.y, EB.y);
+          const R4<float> E = Es[r * 4];
+          const T Ere(E.x, E.y), Eim(E.z, E.w);
           Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
           Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
         }
       } else {
         for (int r = 0; r < st.nrows; ++r) {
           const R4<float> G = st.G_cur[(long long)r * g.nx + x];
-          const R2<float> EA = st.EY[(long long)r * st.eyp + yA];
-          const R2<float> EB = st.EY[(long long)r * st.eyp + (yB < g.ny ? yB : yA)];
-          const T Ere(EA.x, EB.x), Eim(EA.y, EB.y);
+          // yA = y0 + ly with ly < 4: yA and yB = yA + 4 share one entry of the phase table
+          const R4<float> E = *reinterpret_cast<const R4<float> *>(reinterpret_cast<const float *>(st.EY) +
+                                                                   (long long)r * 2 * st.eyp + ey_index(yA));
+          const T Ere(E.x, E.y), Eim(E.z, E.w);
           Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
           Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
         }
