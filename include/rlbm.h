@@ -130,6 +130,15 @@ RLBM_API rlbm_status rlbm_spectrum(rlbm_ctx *ctx, int32_t nbins, double *E);
  * values of h_i = f*_i / (w_i eps0) - 1 in double, plane order of the library's folded
  * velocity classes (rlbm_num_planes gives the count).  set_state also sets the step
  * counter.  Both sync.  The paper has no counterpart (it records moments only). */
+/* Energy of a band of wave vectors of the current state's velocity field (v = u^i / u^0):
+ * (1/2) sum over k2lo <= k_x^2 + k_y^2 < k2hi of |v^(k)|^2 / (nx ny)^2, integer wave-number
+ * indices; k2hi <= 0 means no upper bound.  With k2lo = 0 and k2hi = kmin^2 it is the mean
+ * kinetic energy of the velocities filtered to the range below the stirring shell (Part I,
+ * "Model and Methods": the recorded velocities are filtered to remove the driven range);
+ * sqrt(2 E) is the filtered rms velocity.  Same normalisation as rlbm_spectrum (the band
+ * [0, infinity) is half the mean |v|^2).  Syncs. */
+RLBM_API rlbm_status rlbm_band_energy(rlbm_ctx *ctx, int64_t k2lo, int64_t k2hi, double *E);
+
 RLBM_API rlbm_status rlbm_get_state(rlbm_ctx *ctx, double *host, int64_t *step);
 RLBM_API rlbm_status rlbm_set_state(rlbm_ctx *ctx, const double *host, int64_t step);
 RLBM_API int32_t rlbm_num_planes(const rlbm_ctx *ctx);

@@ -360,6 +360,23 @@ def spectrum(ux, uy, nbins, solid=None):
     return E
 
 
+def band_energy(ux, uy, k2lo, k2hi=0):
+    """(1/2) sum over integer wave vectors with k2lo <= k_x^2 + k_y^2 < k2hi (k2hi <= 0: no
+    upper bound) of |v^(k)|^2 / (N_x N_y)^2, v = u^i / u^0: the kinetic energy of the field
+    filtered to a band (Part I, "Model and Methods": the recorded velocities are filtered
+    to remove the driven range)."""
+    ny, nx = ux.shape
+    u0 = np.sqrt(1.0 + ux * ux + uy * uy)
+    P = np.abs(np.fft.fft2(ux / u0)) ** 2 + np.abs(np.fft.fft2(uy / u0)) ** 2
+    kx = np.rint(np.fft.fftfreq(nx) * nx).astype(np.int64)
+    ky = np.rint(np.fft.fftfreq(ny) * ny).astype(np.int64)
+    k2 = kx[None, :] ** 2 + ky[:, None] ** 2
+    sel = k2 >= k2lo
+    if k2hi > 0:
+        sel &= k2 < k2hi
+    return 0.5 * P[sel].sum() / float(nx * ny) ** 2
+
+
 # --------------------------------------------------------------------------
 # Driver
 # --------------------------------------------------------------------------

@@ -168,9 +168,10 @@ __global__ void bin_kernel(const double2 *__restrict__ Z, int nx, int ny, double
       if (sb[i] != 0.0) atomicAdd(&bins[i], sb[i]);
 }
 
-cudaError_t launch_spectrum(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
-                            const double2 *twy, double2 *z0, double2 *z1, double *bins, int nbins,
-                            cudaStream_t st) {
+// Z = 2-D transform of v_x + i v_y (v = u / u^0), laid out [k_x][k_y]; returns which of
+// the two work buffers holds it.
+static double2 *velocity_transform(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
+                                   const double2 *twy, double2 *z0, double2 *z1, cudaStream_t st) {
   const long long ncell = (long long)nx * ny;
   make_z_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(ux, uy, z0, ncell);
   const FftPlan px = make_plan(nx), py = make_plan(ny);
@@ -179,7 +180,54 @@ cudaError_t launch_spectrum(const double *ux, const double *uy, int nx, int ny, 
   double2 *o = (px.nstages % 2) ? z0 : z1;
   transpose_kernel<<<dim3((nx + 31) / 32, (ny + 31) / 32), dim3(32, 8), 0, st>>>(r, o, nx, ny);
   fft_rows_kernel<<<nx, 256, 0, st>>>(o, r, twy, py);
-  double2 *Z = (py.nstages % 2) ? r : o;
+  return (py.nstages % 2) ? r : o;
+}
+
+// Energy of a band of wave vectors, k2lo <= k_x^2 + k_y^2 < k2hi (k2hi <= 0: no upper
+// bound): (1/2) sum |V_x|^2 + |V_y|^2 / (nx ny)^2, as the spectrum's bins but with an exact
+// integer band edge (the velocity filter that removes the driven range).  One FP64 partial
+// per block (k_x column), summed in order afterwards.
+__global__ void band_kernel(const double2 *__restrict__ Z, int nx, int ny, long long k2lo, long long k2hi,
+                            double scale, double *__restrict__ partials) {
+  const int qx = blockIdx.x;
+  const long long kx = qx < (nx + 1) / 2 ? qx : qx - nx;
+  double acc = 0.0;
+  for (int qy = threadIdx.x; qy < ny; qy += blockDim.x) {
+    const long long ky = qy < (ny + 1) / 2 ? qy : qy - ny;
+    const long long k2 = kx * kx + ky * ky;
+    if (k2 < k2lo || (k2hi > 0 && k2 >= k2hi)) continue;
+    const double2 v = Z[(long long)qx * ny + qy];
+    acc += scale * (v.x * v.x + v.y * v.y);
+  }
+  __shared__ double red[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    partials[(long long)qx * 4] = s;
+    partials[(long long)qx * 4 + 1] = partials[(long long)qx * 4 + 2] = partials[(long long)qx * 4 + 3] = 0.0;
+  }
+}
+
+cudaError_t launch_band_energy(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
+                               const double2 *twy, double2 *z0, double2 *z1, long long k2lo, long long k2hi,
+                               double *partials, double *out4, cudaStream_t st) {
+  double2 *Z = velocity_transform(ux, uy, nx, ny, twx, twy, z0, z1, st);
+  const double scale = 0.5 / ((double)nx * ny * (double)nx * ny);
+  band_kernel<<<nx, 256, 0, st>>>(Z, nx, ny, k2lo, k2hi, scale, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(partials, nx, out4, st);
+}
+
+cudaError_t launch_spectrum(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
+                            const double2 *twy, double2 *z0, double2 *z1, double *bins, int nbins,
+                            cudaStream_t st) {
+  const long long ncell = (long long)nx * ny;
+  double2 *Z = velocity_transform(ux, uy, nx, ny, twx, twy, z0, z1, st);
   cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(double) * nbins, st);
   if (e != cudaSuccess) return e;
   const size_t smem = nbins <= 6144 ? sizeof(double) * nbins : 0;

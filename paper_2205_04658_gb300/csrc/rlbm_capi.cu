@@ -101,7 +101,7 @@ Layout make_layout(const rlbm_config &c) {
   L.eps = take(8 * ncell);
   L.ux = take(8 * ncell);
   L.uy = take(8 * ncell);
-  L.partials = take(32 * (size_t)L.max_blocks);
+  L.partials = take(32 * (size_t)std::max<long long>(L.max_blocks, c.nx));  // moments blocks, or one per k_x column
   L.totals = take(32);
   L.twx = take(16 * (size_t)c.nx);
   L.twy = take(16 * (size_t)c.ny);
@@ -699,6 +699,25 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
   if ((e = dispatch_ghosts(c, c->cur)) != cudaSuccess) return c->cuda_fail(e, "ghost fill kernel");
   if ((e = stir_prime(c, step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
   return check_device(c);
+}
+
+rlbm_status rlbm_band_energy(rlbm_ctx *c, int64_t k2lo, int64_t k2hi, double *E) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (!E || k2lo < 0) return c->fail(RLBM_E_INVAL, "E must be non-NULL and k2lo >= 0");
+  Scoped dev(c->device);
+  cudaError_t e = dispatch_moments(c);
+  if (e != cudaSuccess) return c->cuda_fail(e, "moments kernel launch");
+  double *out = c->at<double>(c->L.totals);
+  e = launch_band_energy(c->at<double>(c->L.ux), c->at<double>(c->L.uy), c->cfg.nx, c->cfg.ny,
+                         c->at<double2>(c->L.twx), c->at<double2>(c->L.twy), c->at<double2>(c->L.z0),
+                         c->at<double2>(c->L.z1), k2lo, k2hi, c->at<double>(c->L.partials), out, c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "band energy kernels");
+  double host[4];
+  if ((e = cudaMemcpyAsync(host, out, 32, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of the band energy");
+  if (rlbm_status s = check_device(c)) return s;
+  *E = host[0];
+  return RLBM_OK;
 }
 
 int32_t rlbm_num_planes(const rlbm_ctx *c) { return c ? c->L.Q : -1; }

@@ -125,6 +125,9 @@ cudaError_t launch_adj_twiddles(double2 *tw, float2 *twf, int n, cudaStream_t st
 // Reductions and spectrum (rlbm_aux.cu)
 cudaError_t launch_counter_inc(long long *counter, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st);
+cudaError_t launch_band_energy(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
+                               const double2 *twy, double2 *z0, double2 *z1, long long k2lo, long long k2hi,
+                               double *partials, double *out4, cudaStream_t st);
 cudaError_t launch_spectrum(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
                             const double2 *twy, double2 *z0, double2 *z1, double *bins, int nbins,
                             cudaStream_t st);

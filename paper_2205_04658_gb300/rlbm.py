@@ -56,6 +56,7 @@ def lib():
             "rlbm_step": (c_i32, [P, c_i64]),
             "rlbm_moments": (c_i32, [P, dp, dp, dp, dp]),
             "rlbm_spectrum": (c_i32, [P, c_i32, dp]),
+            "rlbm_band_energy": (c_i32, [P, c_i64, c_i64, dp]),
             "rlbm_get_state": (c_i32, [P, dp, ctypes.POINTER(c_i64)]),
             "rlbm_set_state": (c_i32, [P, dp, c_i64]),
             "rlbm_num_planes": (c_i32, [P]),
@@ -149,6 +150,12 @@ def rlbm_moments(ctx, eps=None, ux=None, uy=None, totals=None):
 
 def rlbm_spectrum(ctx, nbins, E):
     _check(lib().rlbm_spectrum(ctx, int(nbins), _dptr(E)), ctx)
+
+
+def rlbm_band_energy(ctx, k2lo, k2hi):
+    E = np.zeros(1)
+    _check(lib().rlbm_band_energy(ctx, int(k2lo), int(k2hi), _dptr(E)), ctx)
+    return E[0]
 
 
 def rlbm_get_state(ctx, host):
@@ -270,6 +277,14 @@ class Lattice:
         E = np.empty(nbins)
         rlbm_spectrum(self.ctx, nbins, E)
         return E
+
+    def band_energy(self, k2lo, k2hi=0):
+        """(1/2) sum of |v^(k)|^2 / (nx ny)^2 over k2lo <= |k|^2 < k2hi (k2hi <= 0: unbounded)."""
+        return rlbm_band_energy(self.ctx, k2lo, k2hi)
+
+    def filtered_velocity(self, kf):
+        """rms velocity of the field filtered to |k| < kf (the range below a stirring shell)."""
+        return float(np.sqrt(2.0 * self.band_energy(0, kf * kf)))
 
     def get_state(self):
         q = rlbm_num_planes(self.ctx)

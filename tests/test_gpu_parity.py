@@ -135,6 +135,24 @@ def test_spectrum_matches_oracle(R):
     lat.close()
 
 
+def test_band_energy_matches_oracle(R):
+    """The velocity filter (energy of the wave vectors below the stirring shell) and its
+    complement, on a stirred state after 30 steps, against the oracle's band energy."""
+    nx, ny = 48, 40
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=17, u_amp=0.05, kmax=6)
+    cfg = dict(nx=nx, ny=ny, eta_over_s=0.05, kmin=3, kmax=6, force_amp=1e-3, seed=4,
+               init_eps=e, init_ux=ux, init_uy=uy)
+    o = O.Oracle(cfg).run(30)
+    E, UX, UY, _ = o.fields()
+    lat = R.Lattice(nx, ny, precision="f64", **{k: v for k, v in cfg.items() if k not in ("nx", "ny")})
+    lat.step(30)
+    for lo, hi in ((0, 9), (9, 0), (0, 0), (10, 37)):
+        ref = O.band_energy(UX, UY, lo, hi)
+        assert abs(lat.band_energy(lo, hi) - ref) <= 1e-10 * O.band_energy(UX, UY, 0, 0)
+    assert lat.filtered_velocity(3) == pytest.approx(np.sqrt(2 * O.band_energy(UX, UY, 0, 9)), rel=1e-9)
+    lat.close()
+
+
 def test_spectrum_non_power_of_two_sizes(R):
     """768 = 3 * 2^8 and 90 = 2 * 3^2 * 5 exercise the mixed-radix transform."""
     for nx, ny in ((768, 24), (90, 26)):

@@ -1,6 +1,7 @@
 """Pins of the oracle's energy spectrum (Sec. "Turbulence": E(k) as the shell
 density of 1/2 |v(k)|^2)."""
 import numpy as np
+import pytest
 
 from oracle import rlbm_oracle as O
 from paper_2205_04658_gb300 import inputs
@@ -43,3 +44,25 @@ def test_matches_direct_dft_8x8():
             n = int(round(np.sqrt(kx * kx + ky * ky)))
             ref[n] += 0.5 * (abs(zx) ** 2 + abs(zy) ** 2) / 64 ** 2
     assert np.abs(E - ref).max() < 1e-15
+
+
+def test_band_energy_parseval_and_complement():
+    """The unbounded band is half the mean |v|^2 (Parseval); a band and its complement add
+    up to it; a single mode lands in exactly the band holding its |k|^2."""
+    rng = np.random.default_rng(5)
+    ux = 0.05 * rng.standard_normal((12, 20))
+    uy = 0.05 * rng.standard_normal((12, 20))
+    u0 = np.sqrt(1 + ux * ux + uy * uy)
+    total = 0.5 * np.mean((ux / u0) ** 2 + (uy / u0) ** 2)
+    assert O.band_energy(ux, uy, 0, 0) == pytest.approx(total, rel=1e-13)
+    lo = O.band_energy(ux, uy, 0, 17)
+    hi = O.band_energy(ux, uy, 17, 0)
+    assert lo + hi == pytest.approx(total, rel=1e-13)
+    # one mode (k_x, k_y) = (3, 2), |k|^2 = 13
+    Y, X = np.mgrid[0:12, 0:20]
+    vx = 0.01 * np.cos(2 * np.pi * (3 * X / 20 + 2 * Y / 12))
+    g = 1.0 / np.sqrt(1.0 - vx * vx)  # u = gamma v with v = vx exactly
+    e13 = O.band_energy(g * vx, 0 * vx, 13, 14)
+    assert e13 == pytest.approx(0.5 * np.mean(vx * vx), rel=1e-12)
+    assert O.band_energy(g * vx, 0 * vx, 0, 13) < 1e-30
+    assert O.band_energy(g * vx, 0 * vx, 14, 0) < 1e-30
