@@ -93,6 +93,13 @@ typedef struct {
   const double *init_ux;   /* host, nx*ny initial u^x (spatial part of u^mu); NULL = 0 */
   const double *init_uy;   /* host, nx*ny initial u^y; NULL = 0 */
   double fp64_landau_vmax; /* F32/F16/BF16: |v| above which Landau runs in FP64; 0 = 0.5 */
+  int32_t open_x;          /* 0 = x periodic (default); 1 = open channel (Part II, "Model and
+                              Methods"): at x = 0 the populations streaming in are those of
+                              the equilibrium at eps0 moving with u^x = inflow_ux, and at
+                              x = nx - 1 the outflow is zero-gradient (the column beyond the
+                              last one repeats it).  y stays periodic unless walls_y. */
+  double inflow_ux;        /* open_x: spatial u^x of the inflow (in units of the particle
+                              speed); |inflow_ux| < 1 */
 } rlbm_config;
 
 /* Device bytes the workspace must hold for this configuration (the populations,
@@ -138,6 +145,13 @@ RLBM_API rlbm_status rlbm_spectrum(rlbm_ctx *ctx, int32_t nbins, double *E);
  * sqrt(2 E) is the filtered rms velocity.  Same normalisation as rlbm_spectrum (the band
  * [0, infinity) is half the mean |v|^2).  Syncs. */
 RLBM_API rlbm_status rlbm_band_energy(rlbm_ctx *ctx, int64_t k2lo, int64_t k2hi, double *E);
+
+/* Column means of the current state's velocity v = u^i / u^0 (solid cells count as 0):
+ * jx[x] = (1/ny) sum_y v^x(x, y), jy likewise; host arrays of nx values (either may be NULL).
+ * The current density of Part II ("Model and Methods") in units of the particle speed:
+ * jx[nx - 1] at the outflow border over time gives j(t), jx over a span of columns j(x).
+ * Syncs. */
+RLBM_API rlbm_status rlbm_column_means(rlbm_ctx *ctx, double *jx, double *jy);
 
 RLBM_API rlbm_status rlbm_get_state(rlbm_ctx *ctx, double *host, int64_t *step);
 RLBM_API rlbm_status rlbm_set_state(rlbm_ctx *ctx, const double *host, int64_t step);

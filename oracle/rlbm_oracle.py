@@ -273,6 +273,37 @@ def stream(fstar, v, courant, solid, opp):
     return out
 
 
+def stream_open(fstar, v, courant, solid, opp, f_in, wall_rows):
+    """Pull streaming of an open channel (Part II, "Model and Methods"): the populations
+    arriving from beyond x = 0 are those of the inflow equilibrium f_in (Q,), and beyond
+    x = N_x - 1 the last column repeats itself (zero-gradient outflow).  y keeps the
+    window's own wrap.  The two boundary columns are appended to a copy of the window, it is
+    streamed as usual, and the interior is kept.  wall_rows (H,) marks solid wall rows,
+    which stay solid in the appended columns too."""
+    q, h, w = fstar.shape
+    pad = np.empty((q, h, w + 2))
+    pad[:, :, 1:-1] = fstar
+    pad[:, :, 0] = f_in[:, None]
+    pad[:, :, -1] = fstar[:, :, -1]
+    pad[:, wall_rows, 0] = 0.0
+    sp = np.zeros((h, w + 2), bool)
+    sp[:, 1:-1] = solid
+    sp[:, 0] = wall_rows
+    sp[:, -1] = wall_rows
+    return stream(pad, v, courant, sp, opp)[:, :, 1:-1]
+
+
+def column_means(ux, uy, solid=None):
+    """j(x) = mean over y of v = u^i / u^0 per column (solid cells count as zero): the current
+    density of Part II in units of the particle speed."""
+    u0 = np.sqrt(1.0 + ux * ux + uy * uy)
+    vx, vy = ux / u0, uy / u0
+    if solid is not None:
+        vx = np.where(solid, 0.0, vx)
+        vy = np.where(solid, 0.0, vy)
+    return vx.mean(axis=0), vy.mean(axis=0)
+
+
 # --------------------------------------------------------------------------
 # Stirring force (Part I, "Model and Methods": random amplitude and in-plane
 # direction on the wave vectors of a shell, transformed to configuration space)
@@ -382,7 +413,8 @@ def band_energy(ux, uy, k2lo, k2hi=0):
 # --------------------------------------------------------------------------
 DEFAULTS = dict(walls_y=0, vset=3, a=0.1, dt=0.05, eta_over_s=0.1, eps0=1.0,
                 body_force=(0.0, 0.0), kmin=0, kmax=0, force_amp=0.0, seed=0,
-                solid=None, init_eps=None, init_ux=None, init_uy=None, mode_scale=None)
+                solid=None, init_eps=None, init_ux=None, init_uy=None, mode_scale=None,
+                open_x=0, inflow_ux=0.0)
 
 
 class Window:
@@ -424,6 +456,8 @@ class Oracle:
         c.update(cfg)
         self.cfg = c
         nx, ny = c["nx"], c["ny"]
+        if c["open_x"] and xs is not None and len(xs) != nx:
+            raise ValueError("an open channel is run on the whole lattice width")
         if xs is None:
             xs = np.arange(nx)
         if ys is None:
@@ -442,6 +476,17 @@ class Oracle:
         u = four_velocity(ux, uy, self.dp)
         self.fstar = equilibrium(ideal_T(eps, u, self.dp), self.v, self.w)
         self.fstar[:, self.win.solid] = 0.0
+        if c["open_x"]:
+            u_in = four_velocity(np.array([c["inflow_ux"]]), np.array([0.0]), self.dp)
+            self.f_in = equilibrium(ideal_T(np.array([c["eps0"]]), u_in, self.dp), self.v, self.w)[:, 0]
+            self.wall_rows = (self.win.Y < 0) | (self.win.Y >= ny) if c["walls_y"] else np.zeros(self.win.Y.shape, bool)
+            self.wall_rows = self.wall_rows[:, 0]
+
+    def streamed(self):
+        """f_n = stream(f*_n) with the lattice's boundaries."""
+        if self.cfg["open_x"]:
+            return stream_open(self.fstar, self.v, self.courant, self.win.solid, self.opp, self.f_in, self.wall_rows)
+        return stream(self.fstar, self.v, self.courant, self.win.solid, self.opp)
 
     def force_field(self, n):
         c = self.cfg
@@ -464,7 +509,7 @@ class Oracle:
 
     def step(self):
         c = self.cfg
-        f = stream(self.fstar, self.v, self.courant, self.win.solid, self.opp)
+        f = self.streamed()
         fluid, T, eps, u = self.macroscopic(f)
         Tloc = temperature(eps, c["vset"])
         ff = f[:, fluid]
@@ -486,7 +531,7 @@ class Oracle:
         """eps, u^x, u^y of the current state f_n = stream(f*_n) (zero at solid
         cells) and the totals (sum T^00, sum T^0x, sum T^0y, sum 1/2 |v|^2) over
         fluid cells."""
-        f = stream(self.fstar, self.v, self.courant, self.win.solid, self.opp)
+        f = self.streamed()
         fluid, T, eps, u = self.macroscopic(f)
         E = np.zeros(self.win.X.shape)
         UX = np.zeros(self.win.X.shape)

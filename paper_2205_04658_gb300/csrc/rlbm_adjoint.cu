@@ -248,8 +248,8 @@ adjoint_kernel(const S *__restrict__ B, const typename RealOf<S>::type *__restri
     R *o = kout + (long long)(y + 1) * g.pitch + x + PadLayout<R>::XOFF;
 #pragma unroll
     for (int q = 0; q < Q; ++q) o[q * g.plane] = kap[q];
-    const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
-    const int gyv = g.walls ? INT_MIN : (y == 0 ? g.ny : (y == g.ny - 1 ? -1 : INT_MIN));
+    const int gxv = ghost_col(x, g.nx, g.walls);
+    const int gyv = ghost_row(y, g.ny, g.walls);
     if (gxv != INT_MIN || gyv != INT_MIN) {
       const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
       for (int a = 0; a < 3; ++a) {

@@ -38,6 +38,40 @@ cudaError_t launch_counter_inc(long long *counter, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Column means of the velocity v = u / u^0 of the moments fields (solid cells hold u = 0):
+// j_x(x) = (1/ny) sum_y v^x, j_y likewise.  One block per column, fixed-order sums.
+__global__ void column_means_kernel(const double *__restrict__ ux, const double *__restrict__ uy, int nx, int ny,
+                                    double *__restrict__ jx, double *__restrict__ jy) {
+  const int x = blockIdx.x;
+  double ax = 0.0, ay = 0.0;
+  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+    const double a = ux[(long long)y * nx + x], b = uy[(long long)y * nx + x];
+    const double iu0 = 1.0 / sqrt(1.0 + a * a + b * b);
+    ax += a * iu0;
+    ay += b * iu0;
+  }
+  __shared__ double red[2][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    ax += __shfl_down_sync(0xffffffffu, ax, off);
+    ay += __shfl_down_sync(0xffffffffu, ay, off);
+  }
+  if (lane == 0) { red[0][warp] = ax; red[1][warp] = ay; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sx += red[0][w]; sy += red[1][w]; }
+    jx[x] = sx / ny;
+    jy[x] = sy / ny;
+  }
+}
+
+cudaError_t launch_column_means(const double *ux, const double *uy, int nx, int ny, double *jx, double *jy,
+                                cudaStream_t st) {
+  column_means_kernel<<<nx, 256, 0, st>>>(ux, uy, nx, ny, jx, jy);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st) {
   reduce_partials_kernel<<<1, 256, 0, st>>>(partials, nblocks, totals);
   return cudaGetLastError();

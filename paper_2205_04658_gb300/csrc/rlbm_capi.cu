@@ -60,7 +60,7 @@ bool stirring_on(const rlbm_config &c) { return c.force_amp != 0.0; }
 
 struct Layout {
   size_t pop[2], nbmask, err, ctr, EY, G[2], coef[2], mode_kx, row_start, mode_scale;
-  size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, total;
+  size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, cols, total;
   long long plane;
   int pitch, xoff, Q, nrows, nmodes, max_bins, eyp;
   long long max_blocks;
@@ -108,6 +108,7 @@ Layout make_layout(const rlbm_config &c) {
   L.z0 = take(16 * ncell);
   L.z1 = take(16 * ncell);
   L.bins = take(8 * (size_t)L.max_bins);
+  L.cols = take(16 * (size_t)c.nx);  // column means j_x, j_y
   L.total = off;
   return L;
 }
@@ -134,6 +135,8 @@ std::string validate(const rlbm_config *c) {
   if (c->vset == 2 && (stirring_on(*c) || c->body_force[0] != 0.0 || c->body_force[1] != 0.0))
     return "the projected force is defined for the three-dimensional momentum set (vset 3) only";
   if (!(c->fp64_landau_vmax >= 0.0 && c->fp64_landau_vmax < 1.0)) return "fp64_landau_vmax must lie in [0, 1)";
+  if (c->open_x != 0 && c->open_x != 1) return "open_x must be 0 or 1";
+  if (c->open_x && !(std::fabs(c->inflow_ux) < 1.0)) return "inflow_ux must be finite with |inflow_ux| < 1";
   return "";
 }
 
@@ -227,6 +230,19 @@ cudaError_t dispatch_ghosts(rlbm_ctx *c, int b) {
     case RLBM_F32: return launch_ghosts_f32(c->cfg.vset, f, c->geom, c->stream);
     case RLBM_F16: return launch_ghosts_f16(c->cfg.vset, f, c->geom, c->stream);
     default: return launch_ghosts_bf16(c->cfg.vset, f, c->geom, c->stream);
+  }
+}
+
+// Inflow and outflow columns of an open channel (no-op for x periodic).
+cudaError_t dispatch_open_ghosts(rlbm_ctx *c, int b) {
+  if (!c->cfg.open_x) return cudaSuccess;
+  void *f = c->ws + c->L.pop[b];
+  const double u = c->cfg.inflow_ux;
+  switch (c->cfg.precision) {
+    case RLBM_F64: return launch_open_ghosts_f64(c->cfg.vset, f, c->geom, u, c->stream);
+    case RLBM_F32: return launch_open_ghosts_f32(c->cfg.vset, f, c->geom, u, c->stream);
+    case RLBM_F16: return launch_open_ghosts_f16(c->cfg.vset, f, c->geom, u, c->stream);
+    default: return launch_open_ghosts_bf16(c->cfg.vset, f, c->geom, u, c->stream);
   }
 }
 
@@ -487,7 +503,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   std::memset(c->geom.beta, 0, sizeof(c->geom.beta));
   if (cfg->vset == 3) fill_beta<3>(C, c->geom.beta); else fill_beta<2>(C, c->geom.beta);
   c->geom.nx = cfg->nx; c->geom.ny = cfg->ny; c->geom.pitch = L.pitch; c->geom.plane = L.plane;
-  c->geom.walls = cfg->walls_y;
+  c->geom.walls = (cfg->walls_y ? WALLS_Y : 0) | (cfg->open_x ? OPEN_X : 0);
   c->geom.nbmask = nullptr;
   {
     const std::string tm = make_tensor_maps(c);
@@ -526,6 +542,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
         if (cfg->walls_y) return true;
         y = (y + ny) % ny;
       }
+      if (cfg->open_x && (x < 0 || x >= nx)) return false;  // inflow / outflow columns
       x = (x + nx) % nx;
       return cfg->solid && cfg->solid[(size_t)y * nx + x] != 0;
     };
@@ -599,6 +616,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
       return bail(RLBM_E_CUDA);
     }
     if ((e = dispatch_init(c, c->ws + L.pop[b], de, dux, duy)) != cudaSuccess) { c->cuda_fail(e, "init kernel"); return bail(RLBM_E_CUDA); }
+    if ((e = dispatch_open_ghosts(c, b)) != cudaSuccess) { c->cuda_fail(e, "open-channel ghost kernel"); return bail(RLBM_E_CUDA); }
   }
   if ((e = cudaMemsetAsync(c->ws + L.err, 0, 16, c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaMemsetAsync"); return bail(RLBM_E_CUDA); }
   if ((e = cudaMemsetAsync(c->ws + L.ctr, 0, 16, c->stream)) != cudaSuccess) { c->cuda_fail(e, "cudaMemsetAsync"); return bail(RLBM_E_CUDA); }
@@ -697,6 +715,7 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
   if (e != cudaSuccess) return c->cuda_fail(e, "copy of the state");
   c->step = step;
   if ((e = dispatch_ghosts(c, c->cur)) != cudaSuccess) return c->cuda_fail(e, "ghost fill kernel");
+  if ((e = dispatch_open_ghosts(c, c->cur)) != cudaSuccess) return c->cuda_fail(e, "open-channel ghost kernel");
   if ((e = stir_prime(c, step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
   return check_device(c);
 }
@@ -718,6 +737,21 @@ rlbm_status rlbm_band_energy(rlbm_ctx *c, int64_t k2lo, int64_t k2hi, double *E)
   if (rlbm_status s = check_device(c)) return s;
   *E = host[0];
   return RLBM_OK;
+}
+
+rlbm_status rlbm_column_means(rlbm_ctx *c, double *jx, double *jy) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  Scoped dev(c->device);
+  cudaError_t e = dispatch_moments(c);
+  if (e != cudaSuccess) return c->cuda_fail(e, "moments kernel launch");
+  double *d = c->at<double>(c->L.cols);
+  const int nx = c->cfg.nx;
+  if ((e = launch_column_means(c->at<double>(c->L.ux), c->at<double>(c->L.uy), nx, c->cfg.ny, d, d + nx, c->stream)) != cudaSuccess)
+    return c->cuda_fail(e, "column means kernel");
+  if (jx && (e = cudaMemcpyAsync(jx, d, 8 * (size_t)nx, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of j_x");
+  if (jy && (e = cudaMemcpyAsync(jy, d + nx, 8 * (size_t)nx, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of j_y");
+  return check_device(c);
 }
 
 int32_t rlbm_num_planes(const rlbm_ctx *c) { return c ? c->L.Q : -1; }
@@ -913,6 +947,7 @@ rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers, void *de
     if (!same_physics(members[0]->cfg, members[i]->cfg))
       { g_thread_error = "member " + std::to_string(i) + " differs from member 0 in velocity set, storage type, a, dt, eta/s, eps0, force or rounding"; return RLBM_E_INVAL; }
     if (members[i]->device != members[0]->device) { g_thread_error = "members live on different devices"; return RLBM_E_INVAL; }
+    if (members[i]->cfg.open_x) { g_thread_error = "member " + std::to_string(i) + " is an open channel (batches take periodic-x lattices)"; return RLBM_E_INVAL; }
   }
   rlbm_batch *b = new (std::nothrow) rlbm_batch();
   if (!b) { g_thread_error = "host allocation failed"; return RLBM_E_NOMEM; }
@@ -1135,6 +1170,7 @@ GradLayout grad_layout(const rlbm_ctx *c, int64_t N, int32_t segment) {
 std::string grad_check(const rlbm_ctx *c, int64_t nsteps, int32_t segment) {
   if (c->cfg.precision != RLBM_F64 && c->cfg.precision != RLBM_F32)
     return "the adjoint runs on FP64 and FP32 storage (the 16-bit forms round stochastically)";
+  if (c->cfg.open_x) return "the adjoint is built for periodic-x lattices (no open-channel boundaries)";
   if (nsteps < 1) return "nsteps must be >= 1";
   if (segment < 0) return "segment must be >= 0 (0 = ceil(sqrt(nsteps)))";
   return "";

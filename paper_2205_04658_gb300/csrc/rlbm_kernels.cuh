@@ -13,6 +13,17 @@
 namespace rlbm {
 
 constexpr int TILE_X = 32, TILE_Y = 8, NTHREADS = TILE_X * TILE_Y;
+
+// The ghost column a cell at x also writes (INT_MIN: none): with x periodic, its image
+// beyond the opposite edge; in an open channel, the last column repeats itself beyond the
+// outflow edge and nothing is written into the inflow column.
+__device__ __forceinline__ int ghost_col(int x, int nx, int walls) {
+  if (walls & OPEN_X) return x == nx - 1 ? nx : INT_MIN;
+  return x == 0 ? nx : (x == nx - 1 ? -1 : INT_MIN);
+}
+__device__ __forceinline__ int ghost_row(int y, int ny, int walls) {
+  return (walls & WALLS_Y) ? INT_MIN : (y == 0 ? ny : (y == ny - 1 ? -1 : INT_MIN));
+}
 constexpr long long WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: bounded TMA waits
 
 template <typename S, int VS> struct Tile {
@@ -131,8 +142,8 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     }
     // ghost copies of the periodic neighbours (boundary cells only)
     if (inside) {
-      const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
-      const int gyv = g.walls ? INT_MIN : (y == 0 ? g.ny : (y == g.ny - 1 ? -1 : INT_MIN));
+      const int gxv = ghost_col(x, g.nx, g.walls);
+      const int gyv = ghost_row(y, g.ny, g.walls);
       if (gxv != INT_MIN || gyv != INT_MIN) {
         const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
         for (int a = 0; a < 3; ++a) {
@@ -264,8 +275,8 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
   for (int lane = 0; lane < 2; ++lane) {
     const int y = lane ? yB : yA;
     if (!(lane ? inB : inA)) continue;
-    const int gxv = x == 0 ? g.nx : (x == g.nx - 1 ? -1 : INT_MIN);
-    const int gyv = g.walls ? INT_MIN : (y == 0 ? g.ny : (y == g.ny - 1 ? -1 : INT_MIN));
+    const int gxv = ghost_col(x, g.nx, g.walls);
+    const int gyv = ghost_row(y, g.ny, g.walls);
     if (gxv == INT_MIN && gyv == INT_MIN) continue;
     const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
     for (int a = 0; a < 3; ++a) {
@@ -676,9 +687,28 @@ __global__ void fill_ghosts_kernel(S *__restrict__ f, const Geometry<typename Re
   S *pl = f + q * g.plane;
   const long long dst = (long long)(gy + 1) * g.pitch + gx + PadLayout<S>::XOFF;
   const bool yghost = gy < 0 || gy >= g.ny;
-  if (yghost && g.walls) { pl[dst] = store_h<S, typename RealOf<S>::type>(0); return; }
+  if (yghost && (g.walls & WALLS_Y)) { pl[dst] = store_h<S, typename RealOf<S>::type>(0); return; }
   const int sx = (gx + g.nx) % g.nx, sy = (gy + g.ny) % g.ny;
   pl[dst] = pl[(long long)(sy + 1) * g.pitch + sx + PadLayout<S>::XOFF];
+}
+
+// Open channel (walls bit OPEN_X): the column left of x = 0 holds the inflow equilibrium
+// (eps0, u^x = ux_in; written here once and never by the step kernel) and the column right
+// of x = nx - 1 repeats that column (zero-gradient outflow; the step kernel keeps it up).
+// Rows of bounce-back walls stay zero.  One thread per padded row, one grid row per plane.
+template <typename S, int VS>
+__global__ void open_ghosts_kernel(S *__restrict__ f, const Geometry<typename RealOf<S>::type> g, double ux_in) {
+  using V = VSet<VS>;
+  using R = typename RealOf<S>::type;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;  // padded row 0 .. ny + 1
+  const int q = blockIdx.y;
+  if (row >= g.ny + 2) return;
+  S *pl = f + q * g.plane + (long long)row * g.pitch + PadLayout<S>::XOFF;
+  pl[g.nx] = pl[g.nx - 1];
+  const bool wall_row = (g.walls & WALLS_Y) && (row == 0 || row == g.ny + 1);
+  const double u0 = sqrt(1.0 + ux_in * ux_in), uv = ux_in * V::vx(q);
+  const double heq = V::CA * u0 * uv + V::CB * uv * uv - V::CC * ux_in * ux_in;  // eps / eps0 = 1
+  pl[-1] = store_h<S, R>((R)(wall_row ? 0.0 : heq));
 }
 
 // Stirring pipeline start at step n: coefficients of steps n and n+1, table of step n.
@@ -920,6 +950,16 @@ static cudaError_t launch_init_t(int vset, void *fout, const HostGeom &hg, doubl
 }
 
 template <typename S>
+static cudaError_t launch_open_ghosts_t(int vset, void *f, const HostGeom &hg, double ux_in, cudaStream_t stream) {
+  using R = typename RealOf<S>::type;
+  const Geometry<R> g = to_geom<R>(hg);
+  const dim3 grid((hg.ny + 2 + 127) / 128, vset == 3 ? VSet<3>::Q : VSet<2>::Q);
+  if (vset == 3) open_ghosts_kernel<S, 3><<<grid, 128, 0, stream>>>((S *)f, g, ux_in);
+  else open_ghosts_kernel<S, 2><<<grid, 128, 0, stream>>>((S *)f, g, ux_in);
+  return cudaGetLastError();
+}
+
+template <typename S>
 static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *coef_n1, void *G_n, int nx,
                                        long long n, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
@@ -960,6 +1000,9 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
   }                                                                                                      \
   cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st) {              \
     return launch_ghosts_t<S>(vset, f, g, st);                                                           \
+  }                                                                                                      \
+  cudaError_t launch_open_ghosts_##SUF(int vset, void *f, const HostGeom &g, double ux_in, cudaStream_t st) { \
+    return launch_open_ghosts_t<S>(vset, f, g, ux_in, st);                                               \
   }                                                                                                      \
   cudaError_t launch_stir_prime_##SUF(const HostStir &s, void *cn, void *cn1, void *G, int nx,          \
                                       long long n, cudaStream_t st) {                                    \

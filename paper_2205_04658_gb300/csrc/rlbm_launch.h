@@ -8,6 +8,11 @@
 
 namespace rlbm {
 
+// Boundary flags of a lattice (Geometry::walls): bit 0 = bounce-back walls in y (the ghost
+// rows stay zero), bit 1 = open channel in x (inflow column left of x = 0, written once;
+// zero-gradient outflow right of x = nx - 1).
+constexpr int WALLS_Y = 1, OPEN_X = 2;
+
 struct HostGeom {
   int nx, ny, pitch;
   long long plane;         // elements per ghost-padded plane: pitch * (ny + 2)
@@ -82,6 +87,7 @@ struct BatchTables {
                                    cudaStream_t st);                                                     \
   cudaError_t launch_init_##SUF(int vset, void *fout, const HostGeom &g, double eps0, const double *e,  \
                                 const double *ux, const double *uy, cudaStream_t st);                   \
+  cudaError_t launch_open_ghosts_##SUF(int vset, void *f, const HostGeom &g, double ux_in, cudaStream_t st); \
   cudaError_t launch_stir_prime_##SUF(const HostStir &s, void *cn, void *cn1, void *G, int nx,          \
                                       long long n, cudaStream_t st);
 
@@ -125,6 +131,8 @@ cudaError_t launch_adj_twiddles(double2 *tw, float2 *twf, int n, cudaStream_t st
 // Reductions and spectrum (rlbm_aux.cu)
 cudaError_t launch_counter_inc(long long *counter, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st);
+cudaError_t launch_column_means(const double *ux, const double *uy, int nx, int ny, double *jx, double *jy,
+                                cudaStream_t st);
 cudaError_t launch_band_energy(const double *ux, const double *uy, int nx, int ny, const double2 *twx,
                                const double2 *twy, double2 *z0, double2 *z1, long long k2lo, long long k2hi,
                                double *partials, double *out4, cudaStream_t st);

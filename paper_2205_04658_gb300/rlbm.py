@@ -35,6 +35,7 @@ class rlbm_config(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("solid", ctypes.POINTER(ctypes.c_uint8)),
         ("init_eps", ctypes.POINTER(ctypes.c_double)), ("init_ux", ctypes.POINTER(ctypes.c_double)),
         ("init_uy", ctypes.POINTER(ctypes.c_double)), ("fp64_landau_vmax", ctypes.c_double),
+        ("open_x", ctypes.c_int32), ("inflow_ux", ctypes.c_double),
     ]
 
 
@@ -57,6 +58,7 @@ def lib():
             "rlbm_moments": (c_i32, [P, dp, dp, dp, dp]),
             "rlbm_spectrum": (c_i32, [P, c_i32, dp]),
             "rlbm_band_energy": (c_i32, [P, c_i64, c_i64, dp]),
+            "rlbm_column_means": (c_i32, [P, dp, dp]),
             "rlbm_get_state": (c_i32, [P, dp, ctypes.POINTER(c_i64)]),
             "rlbm_set_state": (c_i32, [P, dp, c_i64]),
             "rlbm_num_planes": (c_i32, [P]),
@@ -99,7 +101,8 @@ def _dptr(a):
 
 def make_config(nx, ny, precision="f32", walls_y=0, vset=3, a=0.1, dt=0.05, eta_over_s=0.1, eps0=1.0,
                 body_force=(0.0, 0.0), kmin=0, kmax=0, force_amp=0.0, seed=0, solid=None,
-                init_eps=None, init_ux=None, init_uy=None, fp64_landau_vmax=0.0, rounding="stochastic"):
+                init_eps=None, init_ux=None, init_uy=None, fp64_landau_vmax=0.0, rounding="stochastic",
+                open_x=0, inflow_ux=0.0):
     """An rlbm_config and the host arrays it points to (keep both alive until rlbm_init
     returns)."""
     keep = {}
@@ -123,6 +126,7 @@ def make_config(nx, ny, precision="f32", walls_y=0, vset=3, a=0.1, dt=0.05, eta_
     c.init_ux = arr(init_ux, np.float64, "ux")
     c.init_uy = arr(init_uy, np.float64, "uy")
     c.fp64_landau_vmax = fp64_landau_vmax
+    c.open_x, c.inflow_ux = int(open_x), float(inflow_ux)
     return c, keep
 
 
@@ -156,6 +160,10 @@ def rlbm_band_energy(ctx, k2lo, k2hi):
     E = np.zeros(1)
     _check(lib().rlbm_band_energy(ctx, int(k2lo), int(k2hi), _dptr(E)), ctx)
     return E[0]
+
+
+def rlbm_column_means(ctx, jx=None, jy=None):
+    _check(lib().rlbm_column_means(ctx, _dptr(jx), _dptr(jy)), ctx)
 
 
 def rlbm_get_state(ctx, host):
@@ -281,6 +289,13 @@ class Lattice:
     def band_energy(self, k2lo, k2hi=0):
         """(1/2) sum of |v^(k)|^2 / (nx ny)^2 over k2lo <= |k|^2 < k2hi (k2hi <= 0: unbounded)."""
         return rlbm_band_energy(self.ctx, k2lo, k2hi)
+
+    def column_means(self):
+        """(j_x, j_y): column means of v = u / u^0, nx values each."""
+        jx = np.empty(self.nx)
+        jy = np.empty(self.nx)
+        rlbm_column_means(self.ctx, jx, jy)
+        return jx, jy
 
     def filtered_velocity(self, kf):
         """rms velocity of the field filtered to |k| < kf (the range below a stirring shell)."""

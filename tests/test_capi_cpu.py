@@ -65,6 +65,8 @@ def test_workspace_size_scales_with_precision_and_lattice():
     (dict(walls_y=2), "walls_y"),
     (dict(fp64_landau_vmax=1.5), "fp64_landau_vmax"),
     (dict(eps0=-1.0), "eps0"),
+    (dict(open_x=2), "open_x"),
+    (dict(open_x=1, inflow_ux=1.5), "inflow_ux"),
 ])
 def test_invalid_configs_are_rejected(bad, msg):
     kw = dict(nx=64, ny=64, precision="f32")
