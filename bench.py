@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--shape", default=None,
                    help="ctas,stages,stir_rows: use this launch shape instead of tuning (profiling runs)")
-    p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512", "graphene"],
+    p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512", "graphene", "channel"],
                    help="stirred: one lattice (default); ensemble64: 64 stirred members of uneven sizes "
                         "advanced by one persistent launch per step; adjoint512: gradient of the kinetic "
                         "energy of a 512^2 stirred run (2000 steps) by the checkpointed adjoint")
@@ -575,6 +575,56 @@ def run_graphene(args):
         print(json.dumps(line), flush=True)
 
 
+def run_channel(args):
+    """Part II's sample as an open channel: 1024 x 256 nodes, inflow u^x = 0.1 at x = 0,
+    zero-gradient outflow, periodic sides, one or two impurities of 13 nodes (0.5 um at
+    0.038 um per node), eta/s set for Re = 6.37 (one impurity; the two-impurity run keeps
+    it).  Starts from the uniform inflow state.  The state (2 x 36 MB in FP32) fits in L2,
+    so L2 is flushed (a 256 MiB write) before every timed step."""
+    import numpy as np
+    import torch
+    from paper_2205_04658_gb300 import rlbm, inputs, units
+    torch.cuda.set_device(0)
+    rlbm.lib()
+    w = inputs.CHANNEL_1024x256
+    nx, ny = w["nx"], w["ny"]
+    es = units.eta_over_s_for_reynolds(w["reynolds"], w["diameter_nodes"], w["inflow_ux"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for count in (1, 2):
+        mask = inputs.channel_impurities(nx, ny, w["diameter_nodes"], count=count)
+        lat = rlbm.Lattice(nx, ny, precision=args.precision, open_x=1, inflow_ux=w["inflow_ux"], solid=mask,
+                           eta_over_s=es, init_ux=np.full((ny, nx), w["inflow_ux"]))
+        lat.autotune(10)
+        stream = lat.stream
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                flush.zero_()
+                lat.step(1)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                lat.step(1)
+                b.record(stream)
+        torch.cuda.synchronize()
+        times = [a.elapsed_time(b) for a, b in ev]
+        jx, _ = lat.column_means()
+        lat.close()
+        ms = float(np.mean(times))
+        cells = nx * ny
+        alg = ALG_BYTES[args.precision] * cells + 2 * cells
+        line = {"metric": METRIC, "value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": "open channel 1024x256 (Part II sample), inflow 0.1, %d impurit%s of 13 nodes, "
+                                       "eta/s %.4f (Re 6.37)" % (count, "y" if count == 1 else "ies", es),
+                           "l2": "flushed before every timed step (256 MiB write)"},
+                "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": measured_peak()[0],
+                             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / measured_peak()[0]},
+                "j_outflow": float(jx[-1])}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -585,6 +635,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "graphene":
         run_graphene(args)
+    elif args.workload == "channel":
+        run_channel(args)
     else:
         run_gb300(args)
 

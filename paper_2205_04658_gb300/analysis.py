@@ -60,3 +60,27 @@ def sample_run(lattice, nsamples, nbins, kf, every=DECORRELATION_STEPS, start=SE
         spectra.append(lattice.spectrum(nbins))
         vel.append(lattice.filtered_velocity(kf))
     return dict(steps=np.array(steps), spectra=np.array(spectra), filtered_velocity=np.array(vel))
+
+
+def current_density_run(lattice, nsteps, every=1, region=None):
+    """Part II's current density: advance an open-channel `lattice` by `nsteps` steps,
+    recording j_x at the outflow column every `every` steps (j(t)) and, at the end, j_x
+    across the columns of `region` (slice; default: the downstream half) (j(x)).
+    Returns dict(t_steps, j_t, j_x)."""
+    steps, jt = [], []
+    for i in range(0, nsteps, every):
+        lattice.step(min(every, nsteps - i))
+        jx, _ = lattice.column_means()
+        steps.append(lattice.current_step)
+        jt.append(jx[-1])
+    jx, _ = lattice.column_means()
+    if region is None:
+        region = slice(lattice.nx // 2, lattice.nx)
+    return dict(t_steps=np.array(steps), j_t=np.array(jt), j_x=jx[region])
+
+
+def fluctuation_spectrum(signal):
+    """|FFT|^2 of a signal's fluctuation about its mean, for the non-negative frequencies
+    (j(omega) from j(t), j(k_x) from j(x))."""
+    s = np.asarray(signal, dtype=np.float64)
+    return np.abs(np.fft.rfft(s - s.mean())) ** 2

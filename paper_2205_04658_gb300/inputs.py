@@ -91,3 +91,25 @@ ENSEMBLE_64 = dict(nmembers=64, side_seed=4, member_seed0=1000, precision="bf16"
                    eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4, steps=5000)
 ADJOINT_512 = dict(nx=512, ny=512, precision="f32", eta_over_s=0.05, kmin=4, kmax=6,
                    force_amp=1e-4, seed=5, steps=2000)
+
+
+def channel_impurities(nx, ny, diameter_nodes, count=1, separation_nodes=89):
+    """Solid mask of the Part II sample: one disc of the given (odd) diameter in the
+    obstruction region near the inflow border (centre at x = nx / 8, y = ny / 2); a second
+    one, when count = 2, next to it and slightly behind it with respect to the flow, at
+    the given centre-to-centre distance (offset 20 nodes downstream, the rest across)."""
+    r = diameter_nodes // 2
+    Y, X = np.mgrid[0:ny, 0:nx]
+    cx, cy = nx // 8, ny // 2
+    mask = (X - cx) ** 2 + (Y - cy) ** 2 <= r * r
+    if count == 2:
+        dx = 20
+        dy = int(round(np.sqrt(max(separation_nodes ** 2 - dx * dx, 0))))
+        cy2 = (cy + dy) % ny
+        mask |= (X - (cx + dx)) ** 2 + (np.minimum(np.abs(Y - cy2), ny - np.abs(Y - cy2))) ** 2 <= r * r
+    return mask.astype(np.uint8)
+
+
+# Part II sample: 1024 x 256 nodes at 0.038 um (a 40 um x 10 um graphene sheet), impurity
+# diameter 0.5 um = 13 nodes, inflow 0.1 v_F, periodic sides; eta/s set for Re = 6.37.
+CHANNEL_1024x256 = dict(nx=1024, ny=256, open_x=1, inflow_ux=0.1, diameter_nodes=13, reynolds=6.37)

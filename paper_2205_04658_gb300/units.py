@@ -87,3 +87,16 @@ class LatticeUnits:
         d = self.nodes(metres)
         k = int(math.floor((d - 1.0) / 2.0 + 0.5))
         return 2 * k + 1
+
+
+def temperature_lattice(eps=1.0):
+    """T(eps) of the paper's momentum set in lattice units: eps = 3 T^4 / pi^2."""
+    return (math.pi * math.pi * eps / 3.0) ** 0.25
+
+
+def eta_over_s_for_reynolds(reynolds_number, length_nodes, speed, a=0.1, eps0=1.0):
+    """eta/s that gives a lattice run the Reynolds number Re = L U / nu, with the relativistic
+    kinematic viscosity nu = eta / (eps + P) = (eta/s) / T (eps + P = T s at zero chemical
+    potential), L = length_nodes * a in lattice length units and U in units of the particle
+    speed."""
+    return length_nodes * a * speed * temperature_lattice(eps0) / reynolds_number

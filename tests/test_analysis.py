@@ -37,3 +37,20 @@ def test_power_law_slope_recovers_kolmogorov():
 def test_decorrelation_and_settling_constants():
     assert A.DECORRELATION_STEPS * 0.05 == pytest.approx(0.9)
     assert A.SETTLE_STEP * 0.05 == pytest.approx(32.0)
+
+
+def test_fluctuation_spectrum_of_a_single_frequency():
+    t = np.arange(64)
+    s = 0.3 + 0.01 * np.cos(2 * np.pi * 5 * t / 64)
+    P = A.fluctuation_spectrum(s)
+    assert np.argmax(P) == 5
+    assert P[0] < 1e-20
+    assert P[5] == pytest.approx((0.01 * 64 / 2) ** 2, rel=1e-12)
+
+
+def test_channel_impurities():
+    from paper_2205_04658_gb300 import inputs
+    one = inputs.channel_impurities(256, 128, 13)
+    assert one.sum() == sum(1 for dy in range(-6, 7) for dx in range(-6, 7) if dx * dx + dy * dy <= 36)
+    two = inputs.channel_impurities(256, 128, 13, count=2)
+    assert two.sum() == 2 * one.sum()

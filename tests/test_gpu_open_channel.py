@@ -103,3 +103,22 @@ def test_open_channel_is_rejected_by_batches_and_the_adjoint(R):
         a.gradient(4)
     assert e.value.status == R.RLBM_E_INVAL
     a.close()
+
+
+def test_current_density_pipeline(R):
+    """j(t) at the outflow and j(x) downstream of an impurity in a reduced Part II channel,
+    and their fluctuation spectra."""
+    from paper_2205_04658_gb300 import analysis as A, inputs as I, units as U
+    nx, ny = 256, 64
+    mask = I.channel_impurities(nx, ny, 13)
+    es = U.eta_over_s_for_reynolds(6.37, 13, 0.1)
+    lat = R.Lattice(nx, ny, precision="f32", open_x=1, inflow_ux=0.1, solid=mask, eta_over_s=es,
+                    init_ux=np.full((ny, nx), 0.1))
+    out = A.current_density_run(lat, 600, every=5)
+    lat.close()
+    assert out["j_t"].shape == (120,) and out["j_x"].shape == (nx // 2,)
+    assert np.all(np.isfinite(out["j_t"])) and np.all(out["j_t"] > 0.0)
+    # the impurity blocks part of the cross-section: downstream j stays below the inflow's
+    assert out["j_x"].max() < 0.1 / np.sqrt(1.01) * 1.05
+    pw = A.fluctuation_spectrum(out["j_t"])
+    assert pw.shape == (61,) and np.all(pw >= 0.0) and pw[0] < 1e-20

@@ -44,3 +44,11 @@ def test_natural_length_unit():
     assert U.length_unit_m() == pytest.approx(6.582119569e-10, rel=1e-12)
     assert U.to_natural_length(U.length_unit_m()) == pytest.approx(1.0, rel=1e-15)
     assert math.isclose(U.kinematic_viscosity_vf(v_f=U.C_M_S), U.kinematic_viscosity_natural(), rel_tol=1e-14)
+
+
+def test_eta_over_s_for_reynolds_round_trip():
+    """eta/s from Re, then Re = L U / nu back with nu = (eta/s) / T."""
+    es = U.eta_over_s_for_reynolds(6.37, 13, 0.1)
+    nu = es / U.temperature_lattice(1.0)
+    assert 13 * 0.1 * 0.1 / nu == pytest.approx(6.37, rel=1e-14)
+    assert U.temperature_lattice(1.0) == pytest.approx((math.pi ** 2 / 3) ** 0.25, rel=1e-15)
