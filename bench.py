@@ -58,6 +58,10 @@ def parse():
     return a
 
 
+# the stirred workload's job: 20 000 steps, energy spectrum every 500 steps
+E2E_JOB_STEPS, E2E_SPECTRUM_EVERY = 20000, 500
+
+
 def workload(args, rank):
     return dict(eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4, seed=2 + rank)
 
@@ -323,8 +327,9 @@ def run_gb300(args):
     lat.close()
     del flush
 
-    # end to end through the C ABI with host buffers: initial fields H2D (rlbm_init),
-    # K steps, eps/u^x/u^y/totals D2H (rlbm_moments)
+    # end to end through the C ABI with host buffers, the workload's whole job: initial
+    # fields H2D (rlbm_init), launch-shape tuning, 20 000 steps with the energy spectrum read
+    # back to pinned host memory every 500 steps, then eps/u^x/u^y/totals D2H (rlbm_moments)
     e2e = None
     if not args.no_e2e:
         e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=rank, eps_amp=0.0, u_amp=0.0)
@@ -339,12 +344,16 @@ def run_gb300(args):
         nbytes = rlbm.rlbm_query_workspace(cfg)
         ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         ptr = (ws.data_ptr() + 255) // 256 * 256
+        job, every, nbins = E2E_JOB_STEPS, E2E_SPECTRUM_EVERY, min(nx, ny) // 2
+        spec = torch.empty((job // every, nbins), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         ctx = rlbm.rlbm_init(cfg, ptr, nbytes, torch.cuda.current_stream().cuda_stream)
         rlbm.rlbm_autotune(ctx, 20)
-        rlbm.rlbm_step(ctx, args.steps)
+        for i in range(job // every):
+            rlbm.rlbm_step(ctx, every)
+            rlbm.rlbm_spectrum(ctx, nbins, spec[i].numpy())
         rlbm.rlbm_moments(ctx, pin[3].numpy(), pin[4].numpy(), pin[5].numpy(), tot.numpy())
         t1 = time.perf_counter()
         rlbm.rlbm_free(ctx)
@@ -353,11 +362,12 @@ def run_gb300(args):
             t = torch.tensor([dt], dtype=torch.float64, device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        e2e = {"value": world * cells * args.steps / dt / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": 3 * 8 * cells / args.steps,
-               "d2h_bytes_per_step": (3 * 8 * cells + 32) / args.steps,
-               "note": "rlbm_init from pinned host fields + rlbm_autotune + %d steps + rlbm_moments to pinned host"
-                       % args.steps}
+        e2e = {"value": world * cells * job / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 3 * 8 * cells / job,
+               "d2h_bytes_per_step": (spec.numel() * 8 + 3 * 8 * cells + 32) / job,
+               "job_steps": job, "seconds": dt,
+               "note": "rlbm_init from pinned host fields + rlbm_autotune + %d steps with rlbm_spectrum (%d bins) "
+                       "to pinned host every %d steps + rlbm_moments to pinned host" % (job, nbins, every)}
         del ws
 
     cpu = None
@@ -491,6 +501,9 @@ def run_adjoint(args):
     kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
     stream = torch.cuda.Stream()
     lat = rlbm.Lattice(nx, ny, stream=stream, precision=prec, **kw)
+    # launch shape of the step kernel that the gradient's forward and recomputation use
+    # (timed on the current state, which it does not advance)
+    tuned_ms = lat.autotune(20)
     nbytes = rlbm.rlbm_gradient_query_workspace(lat.ctx, N, 0)
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
     ptr = (ws.data_ptr() + 255) // 256 * 256
@@ -520,7 +533,8 @@ def run_adjoint(args):
             "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": {"workload": "gradient of the 512x512 stirred run (shell 4<=|k|<=6, 34 modes, amp 1e-4, "
                                    "seed 5, eta/s 0.05), 2000 steps, wrt 34 mode multipliers, eta/s, body force",
-                       "checkpoint_segment": int(round(N ** 0.5 + 0.4999)), "workspace_bytes": nbytes},
+                       "checkpoint_segment": int(round(N ** 0.5 + 0.4999)), "workspace_bytes": nbytes,
+                       "step_launch_tuned_ms": tuned_ms},
             "forward_only_s": tf, "gradient_over_forward": t / tf,
             "gradient_mlups": nx * ny * N / t / 1e6, "J": J, "grad_eta_over_s": ge}
     print(json.dumps(line), flush=True)

@@ -205,22 +205,24 @@ namespace {
 
 // Step n from the buffer behind `ti` into `fout`; its stirring rows come from s.G_cur and,
 // when staged by TMA, through `tgmap` (NULL: the context's table of step parity n & 1).
+// `chained`: the launch directly follows the step kernel of step n - 1 on the stream
+// (programmatic dependent launch).
 cudaError_t dispatch_step_raw(rlbm_ctx *c, const CUtensorMap *ti, void *fout, int64_t n, const HostStir &s,
-                              const CUtensorMap *tgmap = nullptr) {
+                              const CUtensorMap *tgmap = nullptr, bool chained = false) {
   unsigned *err = c->at<unsigned>(c->L.err);
   const void *tg = tgmap ? tgmap : &c->tmap_G[n & 1], *te = &c->tmap_EY;
   int *ctr = c->at<int>(c->L.ctr);
   const unsigned seq = c->launch_seq++;
   switch (c->cfg.precision) {
-    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
-    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
-    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
-    default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, c->stream);
+    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
+    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
+    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
+    default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
   }
 }
 
-cudaError_t dispatch_step(rlbm_ctx *c, int src, const HostStir &s) {
-  return dispatch_step_raw(c, &c->tmap_in[src], c->ws + c->L.pop[src ^ 1], c->step, s);
+cudaError_t dispatch_step(rlbm_ctx *c, int src, const HostStir &s, bool chained = false) {
+  return dispatch_step_raw(c, &c->tmap_in[src], c->ws + c->L.pop[src ^ 1], c->step, s, nullptr, chained);
 }
 
 cudaError_t dispatch_ghosts(rlbm_ctx *c, int b) {
@@ -636,7 +638,7 @@ rlbm_status rlbm_step(rlbm_ctx *c, int64_t nsteps) {
   for (int64_t i = 0; i < nsteps; ++i) {
     const HostStir s = stir_for_step(c, c->step);
     c->phys.step = c->step;
-    cudaError_t e = dispatch_step(c, c->cur, s);
+    cudaError_t e = dispatch_step(c, c->cur, s, i > 0);
     if (e != cudaSuccess) return c->cuda_fail(e, "step kernel launch");
     c->cur ^= 1;
     ++c->step;
@@ -1275,7 +1277,8 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
       fout = c->ws + c->L.pop[next];
     }
     c->phys.step = s0 + n;
-    if ((e = dispatch_step_raw(c, ti, fout, s0 + n, stir_for_step(c, s0 + n))) != cudaSuccess) return c->cuda_fail(e, "step kernel launch");
+    if ((e = dispatch_step_raw(c, ti, fout, s0 + n, stir_for_step(c, s0 + n), nullptr, n > 0)) != cudaSuccess)
+      return c->cuda_fail(e, "step kernel launch");
     where = next;
   }
   c->cur = where;  // the last step writes a context buffer
@@ -1334,7 +1337,8 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
         st.G_next = gtab((int)(n - lo + 1));
       }
       c->phys.step = s0 + n;
-      if ((e = dispatch_step_raw(c, ti, slot((int)(n - lo)), s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr)) != cudaSuccess)
+      if ((e = dispatch_step_raw(c, ti, slot((int)(n - lo)), s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr,
+                                 n > lo)) != cudaSuccess)
         return c->cuda_fail(e, "step kernel launch (recompute)");
     }
     for (int64_t n = hi - 1; n >= lo; --n) {

@@ -340,15 +340,22 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
   if (tid == 0) {
     for (int s = 0; s <= NST; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
-    if (wid == 0) tile_ctr[(seq + 1u) & 1u] = 0;
   }
+  // A launch chained to the previous step (programmatic dependent launch) may start while
+  // that step's grid drains: the state, the stirring tables, the mode data and the tile
+  // counters it wrote are touched only after it has completed and its writes are visible.
+  griddep_wait();
+  if (tid == 0 && wid == 0) tile_ctr[(seq + 1u) & 1u] = 0;
   __syncthreads();
-  // thread 0: stage s takes tile t (or, with t past the end, only completes its barrier)
+  // thread 0: stage s takes tile t (or, with t past the end, only completes its barrier:
+  // this CTA takes no further tile, and the next step's grid, when chained, may be
+  // scheduled once every CTA has come this far)
   auto fill = [&](int s, int t) {
     uint64_t *b = &bar[s];
     tile_of[s] = t < ntiles ? t : -1;
     if (t >= ntiles) {
       mbar_arrive(b);
+      griddep_launch_dependents();
       return;
     }
     const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
@@ -766,7 +773,7 @@ template <typename S, int VS, bool MASK, bool FORCE, int NST>
 static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, const CUtensorMap &tEY, void *fout,
                                  const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,
                                  const Stir<typename RealOf<S>::type> &s, unsigned *err, int grid_limit,
-                                 int stir_rows, int *tile_ctr, unsigned seq, cudaStream_t stream) {
+                                 int stir_rows, int *tile_ctr, unsigned seq, bool chained, cudaStream_t stream) {
   using TL = Tile<S, VS>;
   constexpr int CPT = sizeof(S) == 8 ? 1 : 2;
   constexpr int NT = NTHREADS / CPT;
@@ -797,6 +804,21 @@ static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, 
   if (grid_limit > 0 && grid_limit < workers) workers = grid_limit;
   if (workers > ntiles) workers = ntiles;
   if (workers < 1) workers = 1;
+  if (chained) {
+    // a step right after the previous one on the same stream: programmatic dependent
+    // launch lets its CTAs be scheduled while that step's last tiles finish
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(workers);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, srows, tile_ctr, seq, err);
+  }
   kern<<<workers, NT, smem, stream>>>(tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, srows, tile_ctr, seq, err);
   return cudaGetLastError();
 }
@@ -806,24 +828,24 @@ static cudaError_t launch_step_n(int vset, const CUtensorMap &mi, const CUtensor
                                  void *fout, const Geometry<typename RealOf<S>::type> &g,
                                  const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &s,
                                  bool mask, bool force, unsigned *err, int grid_limit, int stir_rows,
-                                 int *ctr, unsigned seq, cudaStream_t stream) {
+                                 int *ctr, unsigned seq, bool chained, cudaStream_t stream) {
   if (vset == 3) {
     if (force) {
-      if (mask) return launch_step_v<S, 3, true, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
-      return launch_step_v<S, 3, false, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
+      if (mask) return launch_step_v<S, 3, true, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+      return launch_step_v<S, 3, false, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
     }
-    if (mask) return launch_step_v<S, 3, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
-    return launch_step_v<S, 3, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
+    if (mask) return launch_step_v<S, 3, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+    return launch_step_v<S, 3, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
   }
-  if (mask) return launch_step_v<S, 2, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
-  return launch_step_v<S, 2, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, stream);
+  if (mask) return launch_step_v<S, 2, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+  return launch_step_v<S, 2, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
 }
 
 template <typename S>
 static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, const void *tey, void *fout,
                                  const HostGeom &hg, const HostPhys &hp, const HostStir &hs, unsigned *err,
                                  int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,
-                                 cudaStream_t stream) {
+                                 bool chained, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
   const Geometry<R> g = to_geom<R>(hg);
   Physics<R> p;
@@ -836,8 +858,8 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, cons
   const CUtensorMap &mi = *(const CUtensorMap *)tin, &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
   const bool mask = hg.nbmask != nullptr, force = hp.has_force != 0;
   if (stages == 1)
-    return launch_step_n<S, 1>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, stream);
-  return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, stream);
+    return launch_step_n<S, 1>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+  return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, chained, stream);
 }
 
 template <typename S, int VS, bool MASK, bool FORCE, int NST>
@@ -981,8 +1003,9 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
   cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
                                 int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,      \
-                                cudaStream_t st) {                                                       \
-    return launch_step_t<S>(vset, tin, tg, tey, fout, g, p, s, err, grid_limit, stages, stir_rows, ctr, seq, st); \
+                                bool chained, cudaStream_t st) {                                         \
+    return launch_step_t<S>(vset, tin, tg, tey, fout, g, p, s, err, grid_limit, stages, stir_rows, ctr, seq, \
+                            chained, st);                                                               \
   }                                                                                                      \
   cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
                                       int srows, double amp, const long long *bstep, bool mask, int stages, \

@@ -77,7 +77,7 @@ struct BatchTables {
   cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
                                 int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,      \
-                                cudaStream_t st);                                                        \
+                                bool chained, cudaStream_t st);                                          \
   cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st);               \
   cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
                                       int srows, double amp, const long long *bstep, bool mask, int stages, \

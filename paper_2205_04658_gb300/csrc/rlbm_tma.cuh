@@ -89,4 +89,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Programmatic dependent launch: wait until the grids this launch depends on have
+// completed and their memory operations are visible (returns at once for a launch without
+// that dependency), and let the dependent grid be scheduled once every CTA of this grid has
+// signalled or exited (one thread's signal counts for its CTA).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 }  // namespace rlbm
