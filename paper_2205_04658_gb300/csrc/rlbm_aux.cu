@@ -30,11 +30,15 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partials, long
   }
 }
 
-__global__ void counter_inc_kernel(long long *c) { *c += 1; }
+__global__ void counter_inc_kernel(long long *c, int *tile_ctr) {
+  *c += 1;
+  *tile_ctr = 0;
+}
 
-// Advances the batch step counter between two batched step launches (stream order).
-cudaError_t launch_counter_inc(long long *counter, cudaStream_t st) {
-  counter_inc_kernel<<<1, 1, 0, st>>>(counter);
+// Advances the batch step counter between two batched step launches (stream order) and
+// clears the tile counter for the next launch.
+cudaError_t launch_counter_inc(long long *counter, int *tile_ctr, cudaStream_t st) {
+  counter_inc_kernel<<<1, 1, 0, st>>>(counter, tile_ctr);
   return cudaGetLastError();
 }
 

@@ -864,6 +864,7 @@ struct rlbm_batch {
   MemberDesc *d_mem = nullptr;
   int *d_tile0 = nullptr, *d_draw0 = nullptr;
   long long *d_entry0 = nullptr, *d_bstep = nullptr;
+  int *d_tctr = nullptr;  // the batched kernel's tile counter
   std::vector<MemberDesc> h_mem;
   int ntiles = 0, srows = 0, stages = 2, grid_limit = 0;
   bool mask = false;
@@ -876,7 +877,7 @@ struct rlbm_batch {
 
 namespace {
 
-struct BatchLayout { size_t mem, tile0, entry0, draw0, bstep, total; };
+struct BatchLayout { size_t mem, tile0, entry0, draw0, bstep, tctr, total; };
 
 BatchLayout batch_layout(int n) {
   BatchLayout L{};
@@ -887,6 +888,7 @@ BatchLayout batch_layout(int n) {
   L.entry0 = take(sizeof(long long) * (size_t)(n + 1));
   L.draw0 = take(sizeof(int) * (size_t)(n + 1));
   L.bstep = take(sizeof(long long));
+  L.tctr = take(sizeof(int));
   L.total = off;
   return L;
 }
@@ -907,12 +909,13 @@ cudaError_t batch_prepare(rlbm_batch *b) {
   }
   cudaError_t e = cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(MemberDesc) * b->h_mem.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bstep, 0, sizeof(long long), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tctr, 0, sizeof(int), b->stream);
   return e;
 }
 
 cudaError_t batch_launch_one(rlbm_batch *b) {
   rlbm_ctx *c0 = b->members[0];
-  BatchTables bt{b->d_mem, b->d_tile0, b->d_entry0, b->d_draw0, (int)b->members.size()};
+  BatchTables bt{b->d_mem, b->d_tile0, b->d_entry0, b->d_draw0, b->d_tctr, (int)b->members.size()};
   cudaError_t e;
   const double amp = c0->cfg.force_amp;
   switch (c0->cfg.precision) {
@@ -922,7 +925,7 @@ cudaError_t batch_launch_one(rlbm_batch *b) {
     default: e = launch_batch_step_bf16(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream); break;
   }
   if (e != cudaSuccess) return e;
-  return launch_counter_inc(b->d_bstep, b->stream);
+  return launch_counter_inc(b->d_bstep, b->d_tctr, b->stream);
 }
 
 }  // namespace
@@ -962,6 +965,7 @@ rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers, void *de
   b->d_entry0 = reinterpret_cast<long long *>(b->ws + L.entry0);
   b->d_draw0 = reinterpret_cast<int *>(b->ws + L.draw0);
   b->d_bstep = reinterpret_cast<long long *>(b->ws + L.bstep);
+  b->d_tctr = reinterpret_cast<int *>(b->ws + L.tctr);
   b->stages = members[0]->stages;
   const int nrows = members[0]->L.nrows;
   b->srows = (nrows > 0 && nrows <= 16) ? nrows : 0;
@@ -1023,12 +1027,14 @@ rlbm_status rlbm_batch_autotune(rlbm_batch *b, int32_t reps, double *ms_out) {
   if (cudaError_t e0_ = batch_prepare(b); e0_ != cudaSuccess) return b->cuda_fail(e0_, "batch descriptor upload");
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  BatchTables bt{b->d_mem, b->d_tile0, b->d_entry0, b->d_draw0, (int)b->members.size()};
+  BatchTables bt{b->d_mem, b->d_tile0, b->d_entry0, b->d_draw0, b->d_tctr, (int)b->members.size()};
   rlbm_ctx *c0 = b->members[0];
   const double amp = c0->cfg.force_amp;
   // one batched step without advancing the step counter: every member's next buffer and
   // next-step tables are rewritten with the same values, so repeating it changes nothing
+  // (the tile counter is cleared before each trial, as the counter kernel does between steps)
   auto trial = [&]() -> cudaError_t {
+    if (cudaError_t me = cudaMemsetAsync(b->d_tctr, 0, sizeof(int), b->stream); me != cudaSuccess) return me;
     switch (c0->cfg.precision) {
       case RLBM_F64: return launch_batch_step_f64(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream);
       case RLBM_F32: return launch_batch_step_f32(c0->cfg.vset, bt, c0->geom, c0->phys, b->srows, amp, b->d_bstep, b->mask, b->stages, b->grid_limit, b->ntiles, b->stream);

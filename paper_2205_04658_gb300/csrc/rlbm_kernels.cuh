@@ -441,8 +441,11 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
 // The batched step: one persistent launch advances every lattice of a batch (an
 // ensemble of stirred realisations or impurity samples, uneven sizes) by one step.
 // The tiles of all members form one list (member m owns tiles tile0[m] .. tile0[m+1]);
-// CTAs walk it exactly as the single-lattice kernel walks one lattice, and take each
-// tile's member (binary search), buffers and TMA descriptors from the member table.
+// CTAs walk it exactly as the single-lattice kernel walks one lattice (tiles handed out
+// by a counter, cleared between launches by the kernel that advances the step), and take
+// each tile's member (binary search), buffers and TMA descriptors from the member table;
+// the thread that stages a tile resolves it once and leaves what the tile needs in
+// shared memory beside the stage.
 // The per-member step is step0 + *bstep, so a captured CUDA graph of launches can
 // replay with the counter advanced by a one-thread kernel between launches.  All members
 // share the velocity set, storage type, dt/a, eta/s, eps0, the force shell and the
@@ -452,6 +455,16 @@ struct BatchDims {
   int nx, ny, pitch, walls;
   long long plane;
   const uint16_t *nbmask;
+};
+
+// What the cells of a staged tile need of its member (written by the staging thread).
+struct alignas(16) TileInfo {
+  BatchDims dims;
+  void *fout;          // the buffer this step writes
+  unsigned *err;
+  long long n;         // the member's step index
+  int x0, y0, m;
+  unsigned round_key;
 };
 
 __device__ __forceinline__ int find_member(const int *prefix, int n, int t) {
@@ -490,27 +503,43 @@ batch_step_kernel(const BatchTables bt, const Geometry<typename RealOf<S>::type>
   const int srows = staged ? srows_in : 0;
   const int stage_stride = TL::stage(srows), ey_off = TL::IN_STRIDE + TL::g_bytes(srows);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * stage_stride);
+  TileInfo *info = reinterpret_cast<TileInfo *>(smem + NST * stage_stride + 64);
   const uint32_t stage_bytes = TL::IN_BYTES + srows * (TL::G_ROW + TL::EY_ROW);
   const long long bstep = *bstep_ptr;
 
   const int tid = threadIdx.x, wid = blockIdx.x, nworkers = gridDim.x;
   const int ntiles = bt.tile0[bt.n];
-  const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int k) {  // stage the k-th tile of this CTA into stage k % NST
-    const int t = wid + k * nworkers;
+  // thread 0: stage s takes tile t of the list (handed out by the launch's counter, so a
+  // CTA that runs ahead takes more tiles), or, with t past the end, only completes its
+  // barrier; the tile's member is resolved here, once, into the stage's TileInfo
+  auto fill = [&](int s, int t) {
+    TileInfo &ti = info[s];
+    uint64_t *b = &bar[s];
+    if (t >= ntiles) {
+      ti.m = -1;
+      mbar_arrive(b);
+      return;
+    }
     const int m = find_member(bt.tile0, bt.n, t);
     const MemberDesc &d = bt.mem[m];
     const int lt = t - bt.tile0[m];
     const int x0 = (lt % d.ntx) * TILE_X, y0 = (lt / d.ntx) * TILE_Y;
     const long long n = d.step0 + bstep;
     const int cur = (d.cur0 + (int)(bstep & 1)) & 1;
-    unsigned char *st0 = smem + (k % NST) * stage_stride;
-    uint64_t *b = &bar[k % NST];
+    ti.dims = BatchDims{d.nx, d.ny, d.pitch, d.walls, d.plane, d.nbmask};
+    ti.fout = d.f[cur ^ 1];
+    ti.err = d.err;
+    ti.n = n;
+    ti.x0 = x0;
+    ti.y0 = y0;
+    ti.m = m;
+    ti.round_key = d.round_key;
+    unsigned char *st0 = smem + s * stage_stride;
     mbar_expect_tx(b, stage_bytes);
     tma_load_3d(st0, &d.tin[cur], b, x0 + TL::XOFF - TL::V, y0, 0);
     if (staged) {
@@ -518,58 +547,93 @@ batch_step_kernel(const BatchTables bt, const Geometry<typename RealOf<S>::type>
       tma_load_2d(st0 + ey_off, &d.tEY, b, 2 * y0, 0);
     }
   };
-  if (tid == 0)
-    for (int k = 0; k < NST && k < my_tiles; ++k) issue(k);
+  int pending = 0;  // thread 0: the tile the next refill will stage (fetched one tile ahead)
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) fill(s, atomicAdd(bt.tile_ctr, 1));
+    pending = atomicAdd(bt.tile_ctr, 1);
+  }
   bool alive = true;
   {
-    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
+    const bool ok = mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
     if (__syncthreads_or(!ok)) alive = false;
   }
-  for (int k = 0; alive && k < my_tiles; ++k) {
-    const int t = wid + k * nworkers;
-    const int m = find_member(bt.tile0, bt.n, t);
-    const MemberDesc &d = bt.mem[m];
-    const int lt = t - bt.tile0[m];
-    const int x0 = (lt % d.ntx) * TILE_X, y0 = (lt / d.ntx) * TILE_Y;
-    const long long n = d.step0 + bstep;
-    const int cur = (d.cur0 + (int)(bstep & 1)) & 1;
-    const BatchDims dims{d.nx, d.ny, d.pitch, d.walls, d.plane, d.nbmask};
+  for (int k = 0; alive; ++k) {
+    const int s = k % NST;
+    const TileInfo ti = info[s];
+    if (ti.m < 0) break;
     Physics<R> p = p0;
-    p.round_key = d.round_key;
-    p.step = (unsigned)(n & 0xffffffffll);
-    const Stir<R> st = member_stir<R>(d, n);
-    tile_cells<S, VS, MASK, FORCE, CPT>(smem + (k % NST) * stage_stride, ey_off, (S *)d.f[cur ^ 1], x0, y0, tid,
-                                        dims, wts, p, st, staged, d.err);
-    if (NST == 1) {
+    p.round_key = ti.round_key;
+    p.step = (unsigned)(ti.n & 0xffffffffll);
+    // staged stirring rows need only their count (the shell is shared by all members)
+    Stir<R> st{};
+    if (FORCE && staged) st.nrows = srows;
+    else if (FORCE) st = member_stir<R>(bt.mem[ti.m], ti.n);
+    tile_cells<S, VS, MASK, FORCE, CPT>(smem + s * stage_stride, ey_off, (S *)ti.fout, ti.x0, ti.y0, tid, ti.dims,
+                                        wts, p, st, staged, ti.err);
+    if (NST == 1) {  // the only stage is free once every thread is done with it
       __syncthreads();
-      if (tid == 0 && k + 1 < my_tiles) issue(k + 1);
+      if (tid == 0) {
+        fill(0, pending);
+        pending = atomicAdd(bt.tile_ctr, 1);
+      }
     }
-    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % NST], ((k + 1) / NST) & 1, WAIT_CYCLES);
-    if (__syncthreads_or(!ok)) {
+    // the next stage's barrier completes with its tile, or at once when it has none
+    const int sn = (k + 1) % NST;
+    const bool ok = mbar_wait_bounded(&bar[sn], ((k + 1) / NST) & 1, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {  // (NST = 2: also the barrier after which stage s is free)
       alive = false;
       break;
     }
-    if (NST >= 2 && tid == 0 && k + NST < my_tiles) issue(k + NST);
+    if (NST >= 2 && tid == 0) {
+      fill(s, pending);
+      pending = atomicAdd(bt.tile_ctr, 1);
+    }
   }
   if (!alive && tid == 0) {
     atomicOr(bt.mem[0].err, ERR_TIMEOUT);
     for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
   }
-  // The stirring work of the following steps, spread over all CTAs after their tiles:
-  // table entries of step n+1 and draws of step n+2 of every member.
+  if (!alive) return;  // copies may still be in flight: stage 0 is not free
+  // The stirring work of the following steps, after the tiles: table entries of step n+1,
+  // then the draws of step n+2, of every member.  Each CTA takes a contiguous range of the
+  // entries (members in order, entry = row * nx + x) and builds it member by member, the
+  // member's mode data (coefficients of step n+1, k_x, row ranges) first copied into the
+  // free stage 0; consecutive threads take consecutive entries.
   if (FORCE && srows_in >= 0 && bt.mem[0].nrows) {
     const long long entries = bt.entry0[bt.n];
-    for (long long e = wid + (long long)nworkers * tid; e < entries; e += (long long)nworkers * NT) {
-      int lo = 0, hi = bt.n;
-      while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (bt.entry0[mid] <= e) lo = mid; else hi = mid; }
-      const MemberDesc &d = bt.mem[lo];
-      const long long n = d.step0 + bstep;
-      const Stir<R> st = member_stir<R>(d, n);
-      const long long le = e - bt.entry0[lo];
-      st.G_next[le] = stir_row_entry<R>(st, st.coef_next, (int)(le / d.nx), (int)(le % d.nx), d.nx);
+    const long long per = (entries + nworkers - 1) / nworkers;
+    long long e0 = (long long)wid * per;
+    const long long e1 = e0 + per < entries ? e0 + per : entries;
+    while (e0 < e1) {
+      int m = 0, hi = bt.n;  // entry0[m] <= e0 < entry0[hi]
+      while (hi - m > 1) { const int mid = (m + hi) >> 1; if (bt.entry0[mid] <= e0) m = mid; else hi = mid; }
+      const MemberDesc &d = bt.mem[m];
+      const long long mlo = bt.entry0[m], mend = bt.entry0[m + 1] < e1 ? bt.entry0[m + 1] : e1;
+      const Stir<R> st = member_stir<R>(d, d.step0 + bstep);
+      const int need = st.nmodes * (int)(sizeof(R4<R>) + sizeof(int)) + (st.nrows + 1) * (int)sizeof(int);
+      const R4<R> *coef = st.coef_next;
+      const int *kx = st.mode_kx, *rs = st.row_start;
+      if (need <= (int)TL::IN_STRIDE) {
+        R4<R> *c2 = reinterpret_cast<R4<R> *>(smem);
+        int *k2 = reinterpret_cast<int *>(c2 + st.nmodes);
+        int *r2 = k2 + st.nmodes;
+        for (int i = tid; i < st.nmodes; i += NT) { c2[i] = coef[i]; k2[i] = kx[i]; }
+        for (int i = tid; i <= st.nrows; i += NT) r2[i] = rs[i];
+        __syncthreads();
+        coef = c2; kx = k2; rs = r2;
+      }
+      const int nx = d.nx;
+      for (long long e = e0 + tid; e < mend; e += NT) {
+        const int le = (int)(e - mlo);  // < nrows * nx
+        st.G_next[le] = stir_row_entry<R>(coef, kx, rs, le / nx, le % nx, nx);
+      }
+      __syncthreads();  // the staged mode data is replaced by the next member's
+      e0 = mend;
     }
     const int draws = bt.draw0[bt.n];
-    for (int e = wid + nworkers * tid; e < draws; e += nworkers * NT) {
+    const int dper = (draws + nworkers - 1) / nworkers;
+    const int d1 = (wid + 1) * dper < draws ? (wid + 1) * dper : draws;
+    for (int e = wid * dper + tid; e < d1; e += NT) {
       const int m = find_member(bt.draw0, bt.n, e);
       const MemberDesc &d = bt.mem[m];
       Stir<R> st = member_stir<R>(d, d.step0 + bstep);
@@ -870,7 +934,7 @@ static cudaError_t launch_batch_v(const BatchTables &bt, const Geometry<typename
   constexpr int CPT = sizeof(S) == 8 ? 1 : 2;
   constexpr int NT = NTHREADS / CPT;
   auto kern = batch_step_kernel<S, VS, MASK, FORCE, CPT, NST>;
-  const int smem = TL::smem(NST, FORCE ? srows : 0);
+  const int smem = TL::smem(NST, FORCE ? srows : 0) + NST * (int)sizeof(TileInfo);
   static int configured_dev = -1, configured_smem = -1, max_blocks = 0, sms = 0;
   int dev = 0;
   cudaGetDevice(&dev);

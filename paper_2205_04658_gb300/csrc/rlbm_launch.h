@@ -70,6 +70,7 @@ struct BatchTables {
   const int *tile0;        // [n + 1]
   const long long *entry0; // [n + 1]
   const int *draw0;        // [n + 1]
+  int *tile_ctr;           // tiles handed out so far in this launch (0 before each launch)
   int n;
 };
 
@@ -129,7 +130,7 @@ cudaError_t launch_mode_sum(const double *gstep, long long nsteps, int nmodes, d
 cudaError_t launch_adj_twiddles(double2 *tw, float2 *twf, int n, cudaStream_t st);
 
 // Reductions and spectrum (rlbm_aux.cu)
-cudaError_t launch_counter_inc(long long *counter, cudaStream_t st);
+cudaError_t launch_counter_inc(long long *counter, int *tile_ctr, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st);
 cudaError_t launch_column_means(const double *ux, const double *uy, int nx, int ny, double *jx, double *jy,
                                 cudaStream_t st);
