@@ -26,25 +26,29 @@ template <typename R> struct AdjStir {
   int eyp;
 };
 
-// lam_q(x) = sum_c beta_{q,c} kappa_q(x + o_c), o_c in {(0,0), (sx,0), (0,sy), (sx,sy)}:
-// the transpose of `pull_global`; a solid source corner of the forward pull (the
-// neighbour x + o_c here) takes kappa_{opp(q)}(x) instead.
-template <typename T, int VS, bool MASK>
-__device__ __forceinline__ void pull_transpose(const T *__restrict__ kin, const Geometry<T> &g, int x, int y,
-                                               unsigned nb, T lam[VSet<VS>::Q]) {
+// Pulls of one cell from staged tiles (32 x 8 tile with its one-cell halo, the layout of
+// the forward step kernel's stages; b0 = the cell's offset in a staged plane).
+//   forward pull   h_q(x)   = sum_c beta_{q,c} B_q(x - o_c)
+//   transposed     lam_q(x) = sum_c beta_{q,c} kappa_q(x + o_c)
+// with o_c in {(0,0), (sx,0), (0,sy), (sx,sy)}.  A solid source corner of the forward pull
+// takes the cell's own reversed plane B_{opp(q)}(x); in the transpose the same corner (the
+// neighbour x + o_c) takes kappa_{opp(q)}(x).
+template <typename T, int VS, bool MASK, int SIGN>
+__device__ __forceinline__ void pull_staged(const T *tile, int plane, int txb, int b0, const Geometry<T> &g,
+                                            unsigned nb, T out[VSet<VS>::Q]) {
   constexpr int Q = VSet<VS>::Q;
-  const long long o = (long long)(y + 1) * g.pitch + x + PadLayout<T>::XOFF;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const T *pl = kin + q * g.plane + o;
+    const T *pl = tile + q * plane + b0;
+    const T *own = tile + VSet<VS>::opp(q) * plane + b0;
     const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
-    T acc = g.beta[q][0] * __ldg(pl);
-    const T own = __ldg(kin + VSet<VS>::opp(q) * g.plane + o);
-    if (sx != 0) acc += g.beta[q][1] * ((MASK && ((nb >> (4 + sx)) & 1u)) ? own : __ldg(pl + sx));
-    if (sy != 0) acc += g.beta[q][2] * ((MASK && ((nb >> (4 + 3 * sy)) & 1u)) ? own : __ldg(pl + (long long)sy * g.pitch));
+    T acc = g.beta[q][0] * pl[0];
+    if (sx != 0) acc += g.beta[q][1] * ((MASK && ((nb >> (4 + SIGN * sx)) & 1u)) ? *own : pl[SIGN * sx]);
+    if (sy != 0) acc += g.beta[q][2] * ((MASK && ((nb >> (4 + 3 * SIGN * sy)) & 1u)) ? *own : pl[SIGN * sy * txb]);
     if (sx != 0 && sy != 0)
-      acc += g.beta[q][3] * ((MASK && ((nb >> (4 + 3 * sy + sx)) & 1u)) ? own : __ldg(pl + (long long)sy * g.pitch + sx));
-    lam[q] = acc;
+      acc += g.beta[q][3] *
+             ((MASK && ((nb >> (4 + SIGN * (3 * sy + sx))) & 1u)) ? *own : pl[SIGN * (sy * txb + sx)]);
+    out[q] = acc;
   }
 }
 
@@ -194,107 +198,184 @@ __device__ __forceinline__ void cell_adjoint(const R h[VSet<VS>::Q], const R lam
   }
 }
 
-// One adjoint step over the lattice: 32 x 8 cells per block, one cell per thread.
-//   B     post-collision buffer B_{n-1} of the forward run (storage type S)
-//   kin   kappa_{n+1} (unused when LAM is false: the last state, objective only)
+// One adjoint step over the lattice.  Persistent CTAs of 256 threads (one cell each) walk
+// the 32 x 8 tiles (tile t to CTA t mod grid); per tile one TMA box stages B_{n-1} with its
+// one-cell halo and (LAM) a second one kappa_{n+1}, two stages rotating on mbarriers with
+// bounded waits, as in the forward step kernel.
+//   tB    load map of the post-collision buffer B_{n-1} of the forward run
+//   tK    load map of kappa_{n+1} (unused when LAM is false: the last state, objective only)
 //   kout  kappa_n; ghost cells are written like the forward's (periodic copies)
 //   cj    objective weight of S_n (1 / (N N_fluid), or 0 for the first state)
-//   acc   per-block FP64 sums, accumulated over steps: d/d(ln omega0), F adjoint x, y, J
-//   zpart per block row and k_y row r: sum over the block's 8 rows of gF(x, y) EY_r(y)
-template <typename S, int VS, bool MASK, bool FORCE, bool LAM>
+//   acc   per-tile FP64 sums, accumulated over steps: d/d(ln omega0), F adjoint x, y, J
+//   zpart per tile row and k_y row r: sum over the tile's 8 rows of gF(x, y) EY_r(y)
+template <typename S, int VS, bool MASK, bool FORCE, bool LAM, int NST>
 __global__ void __launch_bounds__(256)
-adjoint_kernel(const S *__restrict__ B, const typename RealOf<S>::type *__restrict__ kin,
+adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tK,
                typename RealOf<S>::type *__restrict__ kout, const Geometry<typename RealOf<S>::type> g,
                const Physics<typename RealOf<S>::type> p, const AdjStir<typename RealOf<S>::type> st,
                const typename RealOf<S>::type cj, double *__restrict__ acc, R4<typename RealOf<S>::type> *__restrict__ zpart,
                unsigned *__restrict__ err) {
   using R = typename RealOf<S>::type;
+  using TL = Tile<S, VS>;
+  static_assert(sizeof(S) == sizeof(R), "the adjoint runs on FP32 or FP64 storage");
   constexpr int Q = VSet<VS>::Q;
-  const int lx = threadIdx.x, ly = threadIdx.y;
-  const int x = blockIdx.x * 32 + lx, y = blockIdx.y * 8 + ly;
-  const bool inside = x < g.nx && y < g.ny;
-  unsigned nb = 0;
-  if (MASK && inside) nb = g.nbmask[(long long)y * g.nx + x];
-  const bool fluid = inside && !(MASK && (nb & 16u));
-  R kap[Q];
-  R gom = R(0), gFx = R(0), gFy = R(0), jv = R(0);
-#pragma unroll
-  for (int q = 0; q < Q; ++q) kap[q] = R(0);
-  if (fluid) {
-    R h[Q], lam[Q];
-    pull_global<S, R, VS, MASK>(B, g, x, y, nb, h);
-    if (LAM) {
-      pull_transpose<R, VS, MASK>(kin, g, x, y, nb, lam);
-    } else {
-#pragma unroll
-      for (int q = 0; q < Q; ++q) lam[q] = R(0);
-    }
-    const Mom<R> M = moments_of<R, R, VS, FORCE>(h);
-    const Macro<R> m = cell_macro<R, VS>(h, M, p.vmax2);
-    if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
-    R Fx = p.body_x, Fy = p.body_y;
-    if (FORCE) {
-      for (int r = 0; r < st.nrows; ++r) {
-        const R4<R> G = st.G[(long long)r * g.nx + x];
-        const R2<R> E = ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp, y);
-        Fx = fma(G.x, E.x, fma(-G.y, E.y, Fx));
-        Fy = fma(G.z, E.x, fma(-G.w, E.y, Fy));
-      }
-    }
-    cell_adjoint<R, VS, FORCE>(h, lam, M, m, p.omega0, p.fpref, Fx, Fy, cj, kap, gom, gFx, gFy);
-    jv = cj * R(0.5) * (m.vx * m.vx + m.vy * m.vy);
-  }
-  if (inside) {
-    R *o = kout + (long long)(y + 1) * g.pitch + x + PadLayout<R>::XOFF;
-#pragma unroll
-    for (int q = 0; q < Q; ++q) o[q * g.plane] = kap[q];
-    const int gxv = ghost_col(x, g.nx, g.walls);
-    const int gyv = ghost_row(y, g.ny, g.walls);
-    if (gxv != INT_MIN || gyv != INT_MIN) {
-      const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
-      for (int a = 0; a < 3; ++a) {
-        if (px[a] == INT_MIN || py[a] == INT_MIN) continue;
-        R *d = kout + (long long)(py[a] + 1) * g.pitch + px[a] + PadLayout<R>::XOFF;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) d[q * g.plane] = kap[q];
-      }
-    }
-  }
-  // projections of the force adjoint on the k_y rows of the stirring tables
-  if (FORCE && st.nrows > 0) {
-    __shared__ R2<R> sF[8][32];
-    sF[ly][lx] = R2<R>{gFx, gFy};
-    __syncthreads();
-    for (int r = ly; r < st.nrows; r += 8) {
-      R4<R> z{R(0), R(0), R(0), R(0)};
-      for (int j = 0; j < 8; ++j) {
-        const int yy = blockIdx.y * 8 + j;
-        if (yy >= g.ny) break;
-        const R2<R> E = ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp, yy);
-        const R2<R> F = sF[j][lx];
-        z.x += F.x * E.x;
-        z.y += F.x * E.y;
-        z.z += F.y * E.x;
-        z.w += F.y * E.y;
-      }
-      if (x < g.nx) zpart[((long long)blockIdx.y * st.nrows + r) * g.nx + x] = z;
-    }
-  }
-  // block sums (fixed order) added to this block's accumulators: warp sums in the compute
-  // type (GB300's FP64 rate is 1/64 of FP32), the eight warp sums in FP64
-  R v[4] = {gom, gFx, gFy, jv};
+  constexpr int PL = TL::TYB * TL::TXB;  // elements of a staged plane
+  constexpr int STAGE = TL::IN_STRIDE * (LAM ? 2 : 1);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
+  __shared__ R2<R> sF[8][32];
   __shared__ double red[8][4];
-  const int tid = ly * 32 + lx, lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    if (lane == 0) red[warp][k] = (double)v[k];
+  const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5, lane = tid & 31, warp = tid >> 5;
+  const int wid = blockIdx.x, nworkers = gridDim.x;
+  const int ntx = (g.nx + 31) / 32, ntiles = ntx * ((g.ny + 7) / 8);
+  const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
+  const uint32_t stage_bytes = TL::IN_BYTES * (LAM ? 2 : 1);
+  if (tid == 0) {
+    for (int s2 = 0; s2 < NST; ++s2) mbar_init(&bar[s2], 1);
+    fence_mbar_init();
   }
   __syncthreads();
-  if (tid < 4) {
-    double s = 0.0;
-    for (int w8 = 0; w8 < 8; ++w8) s += red[w8][tid];
-    acc[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] += s;
+  auto issue = [&](int k) {  // thread 0: the k-th tile of this CTA into stage k % NST
+    const int t = wid + k * nworkers;
+    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    unsigned char *st0 = smem + (k % NST) * STAGE;
+    uint64_t *b = &bar[k % NST];
+    mbar_expect_tx(b, stage_bytes);
+    tma_load_3d(st0, &tB, b, x0 + TL::XOFF - TL::V, y0, 0);
+    if (LAM) tma_load_3d(st0 + TL::IN_STRIDE, &tK, b, x0 + TL::XOFF - TL::V, y0, 0);
+  };
+  if (tid == 0)
+    for (int k = 0; k < NST && k < my_tiles; ++k) issue(k);
+  bool alive = true;
+  {
+    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) alive = false;
+  }
+  for (int k = 0; alive && k < my_tiles; ++k) {
+    const int t = wid + k * nworkers;
+    const int tx = t % ntx, ty = t / ntx;
+    const int x = tx * TILE_X + lx, y = ty * TILE_Y + ly;
+    const S *tileB = reinterpret_cast<const S *>(smem + (k % NST) * STAGE);
+    const R *tileK = reinterpret_cast<const R *>(smem + (k % NST) * STAGE + TL::IN_STRIDE);
+    const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
+    const bool inside = x < g.nx && y < g.ny;
+    unsigned nb = 0;
+    if (MASK && inside) nb = g.nbmask[(long long)y * g.nx + x];
+    const bool fluid = inside && !(MASK && (nb & 16u));
+    R kap[Q];
+    R gom = R(0), gFx = R(0), gFy = R(0), jv = R(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) kap[q] = R(0);
+    if (fluid) {
+      R h[Q], lam[Q];
+      pull_staged<R, VS, MASK, -1>(reinterpret_cast<const R *>(tileB), PL, TL::TXB, b0, g, nb, h);
+      if (LAM) {
+        pull_staged<R, VS, MASK, 1>(tileK, PL, TL::TXB, b0, g, nb, lam);
+      } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) lam[q] = R(0);
+      }
+      const Mom<R> M = moments_of<R, R, VS, FORCE>(h);
+      const Macro<R> m = cell_macro<R, VS>(h, M, p.vmax2);
+      if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+      R Fx = p.body_x, Fy = p.body_y;
+      if (FORCE) {
+        // two rows per iteration, in two partial sums: both rows' loads are in flight at once
+        const R *ey = reinterpret_cast<const R *>(st.EY);
+        R Fx2 = R(0), Fy2 = R(0);
+        int r = 0;
+        for (; r + 1 < st.nrows; r += 2) {
+          const R4<R> G0 = st.G[(long long)r * g.nx + x], G1 = st.G[(long long)(r + 1) * g.nx + x];
+          const R2<R> E0 = ey_at<R>(ey + (long long)r * 2 * st.eyp, y);
+          const R2<R> E1 = ey_at<R>(ey + (long long)(r + 1) * 2 * st.eyp, y);
+          Fx = fma(G0.x, E0.x, fma(-G0.y, E0.y, Fx));
+          Fy = fma(G0.z, E0.x, fma(-G0.w, E0.y, Fy));
+          Fx2 = fma(G1.x, E1.x, fma(-G1.y, E1.y, Fx2));
+          Fy2 = fma(G1.z, E1.x, fma(-G1.w, E1.y, Fy2));
+        }
+        if (r < st.nrows) {
+          const R4<R> G0 = st.G[(long long)r * g.nx + x];
+          const R2<R> E0 = ey_at<R>(ey + (long long)r * 2 * st.eyp, y);
+          Fx = fma(G0.x, E0.x, fma(-G0.y, E0.y, Fx));
+          Fy = fma(G0.z, E0.x, fma(-G0.w, E0.y, Fy));
+        }
+        Fx += Fx2;
+        Fy += Fy2;
+      }
+      cell_adjoint<R, VS, FORCE>(h, lam, M, m, p.omega0, p.fpref, Fx, Fy, cj, kap, gom, gFx, gFy);
+      jv = cj * R(0.5) * (m.vx * m.vx + m.vy * m.vy);
+    }
+    if (inside) {
+      R *o = kout + (long long)(y + 1) * g.pitch + x + PadLayout<R>::XOFF;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) o[q * g.plane] = kap[q];
+      const int gxv = ghost_col(x, g.nx, g.walls);
+      const int gyv = ghost_row(y, g.ny, g.walls);
+      if (gxv != INT_MIN || gyv != INT_MIN) {
+        const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
+        for (int a = 0; a < 3; ++a) {
+          if (px[a] == INT_MIN || py[a] == INT_MIN) continue;
+          R *d = kout + (long long)(py[a] + 1) * g.pitch + px[a] + PadLayout<R>::XOFF;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) d[q * g.plane] = kap[q];
+        }
+      }
+    }
+    // projections of the force adjoint on the k_y rows of the stirring tables
+    if (FORCE && st.nrows > 0) {
+      sF[ly][lx] = R2<R>{gFx, gFy};
+      __syncthreads();
+      const int jmax = g.ny - ty * TILE_Y;  // rows of this tile inside the lattice (>= 1)
+      for (int r = ly; r < st.nrows; r += 8) {
+        const R *ey = reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp;
+        R4<R> z{R(0), R(0), R(0), R(0)};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < jmax) {
+            const R2<R> E = ey_at<R>(ey, ty * TILE_Y + j);
+            const R2<R> F = sF[j][lx];
+            z.x += F.x * E.x;
+            z.y += F.x * E.y;
+            z.z += F.y * E.x;
+            z.w += F.y * E.y;
+          }
+        }
+        if (x < g.nx) zpart[((long long)ty * st.nrows + r) * g.nx + x] = z;
+      }
+    }
+    // tile sums (fixed order) added to this tile's accumulators: warp sums in the compute
+    // type (GB300's FP64 rate is 1/64 of FP32), the eight warp sums in FP64
+    R v[4] = {gom, gFx, gFy, jv};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], off);
+      if (lane == 0) red[warp][c] = (double)v[c];
+    }
+    __syncthreads();
+    if (tid < 4) {
+      double sum = 0.0;
+      for (int w8 = 0; w8 < 8; ++w8) sum += red[w8][tid];
+      // one update of this slot per launch, launches in stream order: the same sum as a
+      // plain read-add-write, without waiting for the read
+      atomicAdd(&acc[(long long)t * 4 + tid], sum);
+    }
+    if (NST == 1) {  // the only stage is free once every thread is done with it
+      __syncthreads();
+      if (tid == 0 && k + 1 < my_tiles) issue(k + 1);
+    }
+    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % NST], ((k + 1) / NST) & 1, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {  // (NST = 2: also the barrier after which this stage is free)
+      alive = false;
+      break;
+    }
+    if (NST >= 2 && tid == 0 && k + NST < my_tiles) issue(k + NST);
+  }
+  if (!alive && tid == 0) {
+    // a staged copy did not land in time: latch the error and wait (bounded) once more
+    // for this CTA's copies still in flight before returning
+    atomicOr(err, ERR_TIMEOUT);
+    for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
   }
 }
 
@@ -387,6 +468,37 @@ __global__ void adj_twiddle_kernel(double2 *tw, float2 *twf, int n) {
   twf[t] = make_float2((float)c, (float)s);
 }
 
+template <typename S, int VS, bool MASK, bool FORCE, bool LAM>
+static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typename RealOf<S>::type> &g,
+                                    const Physics<typename RealOf<S>::type> &p,
+                                    const AdjStir<typename RealOf<S>::type> &s, cudaStream_t st) {
+  using R = typename RealOf<S>::type;
+  using TL = Tile<S, VS>;
+  constexpr int NST = 2;
+  auto kern = adjoint_kernel<S, VS, MASK, FORCE, LAM, NST>;
+  const int smem = NST * TL::IN_STRIDE * (LAM ? 2 : 1) + 64 + 128;
+  static int configured_dev = -1, max_blocks = 0, sms = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    configured_dev = dev;
+  }
+  const int ntiles = ((g.nx + TILE_X - 1) / TILE_X) * ((g.ny + TILE_Y - 1) / TILE_Y);
+  int workers = max_blocks * sms;
+  if (workers > ntiles) workers = ntiles;
+  if (workers < 1) workers = 1;
+  const CUtensorMap &mB = *static_cast<const CUtensorMap *>(a.tB);
+  const CUtensorMap &mK = LAM ? *static_cast<const CUtensorMap *>(a.tK) : mB;
+  kern<<<workers, 256, smem, st>>>(mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
+  return cudaGetLastError();
+}
+
 template <typename S, int VS, bool MASK, bool FORCE>
 static cudaError_t launch_adjoint_v(const AdjointArgs &a, const Geometry<typename RealOf<S>::type> &g,
                                     const Physics<typename RealOf<S>::type> &p, cudaStream_t st) {
@@ -396,14 +508,8 @@ static cudaError_t launch_adjoint_v(const AdjointArgs &a, const Geometry<typenam
   s.G = (const R4<R> *)a.G;
   s.EY = (const R2<R> *)a.EY;
   s.eyp = a.eyp;
-  const dim3 block(32, 8), grid((g.nx + 31) / 32, (g.ny + 7) / 8);
-  if (a.kin)
-    adjoint_kernel<S, VS, MASK, FORCE, true><<<grid, block, 0, st>>>((const S *)a.B, (const R *)a.kin, (R *)a.kout, g, p, s,
-                                                                    (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
-  else
-    adjoint_kernel<S, VS, MASK, FORCE, false><<<grid, block, 0, st>>>((const S *)a.B, nullptr, (R *)a.kout, g, p, s,
-                                                                     (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
-  return cudaGetLastError();
+  if (a.kin) return launch_adjoint_k<S, VS, MASK, FORCE, true>(a, g, p, s, st);
+  return launch_adjoint_k<S, VS, MASK, FORCE, false>(a, g, p, s, st);
 }
 
 // dJ/dsigma contributions of nj consecutive steps n0 .. n0 + nj - 1 whose adjoint launches

@@ -1253,6 +1253,12 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
     const std::string m = encode_state_map(c, slot(j), &msl[j]);
     if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
   }
+  // load maps of the two adjoint buffers (compute type = storage type: FP32 or FP64)
+  CUtensorMap mkap[2];
+  for (int i = 0; i < 2; ++i) {
+    const std::string m = encode_state_map(c, w + G.kap[i], &mkap[i]);
+    if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
+  }
   auto gtab = [&](int j) { return w + G.gst + G.table_bytes * (size_t)j; };
   const bool staged_rows = c->L.nrows > 0 && c->L.nrows <= 16;
   if (staged_rows) {
@@ -1318,7 +1324,9 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   int kc = 0;  // kap[kc] holds kappa_{n+1}
   // the last state: objective only (its force terms are multiplied by a zero adjoint)
   a.B = c->ws + c->L.pop[c->cur];
+  a.tB = &c->tmap_in[c->cur];
   a.kin = nullptr;
+  a.tK = nullptr;
   a.kout = w + G.kap[kc];
   a.cj = cj;
   a.G = c->ws + c->L.G[0];
@@ -1349,7 +1357,9 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
     }
     for (int64_t n = hi - 1; n >= lo; --n) {
       a.B = n == lo ? ckpt(k) : slot((int)(n - lo - 1));
+      a.tB = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
       a.kin = w + G.kap[kc];
+      a.tK = &mkap[kc];
       a.kout = w + G.kap[kc ^ 1];
       a.cj = n >= 1 ? cj : 0.0;
       a.G = gtab((int)(n - lo));
