@@ -236,23 +236,37 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int k) {  // thread 0: the k-th tile of this CTA into stage k % NST
+  // thread 0: the k-th tile of this CTA into stage k % NST (B, then kappa, on one barrier)
+  auto issue_B = [&](int k) {
     const int t = wid + k * nworkers;
     const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
-    unsigned char *st0 = smem + (k % NST) * STAGE;
     uint64_t *b = &bar[k % NST];
     mbar_expect_tx(b, stage_bytes);
-    tma_load_3d(st0, &tB, b, x0 + TL::XOFF - TL::V, y0, 0);
-    if (LAM) tma_load_3d(st0 + TL::IN_STRIDE, &tK, b, x0 + TL::XOFF - TL::V, y0, 0);
+    tma_load_3d(smem + (k % NST) * STAGE, &tB, b, x0 + TL::XOFF - TL::V, y0, 0);
   };
+  auto issue_K = [&](int k) {
+    if (!LAM) return;
+    const int t = wid + k * nworkers;
+    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    tma_load_3d(smem + (k % NST) * STAGE + TL::IN_STRIDE, &tK, &bar[k % NST], x0 + TL::XOFF - TL::V, y0, 0);
+  };
+  auto issue = [&](int k) { issue_B(k); issue_K(k); };
+  // B_{n-1} was written before the reverse sweep of its segment began, so its first tiles
+  // are copied at once; a launch chained to the previous reverse step (programmatic
+  // dependent launch) then waits for that step's kappa_{n+1}, and writes nothing before.
   if (tid == 0)
-    for (int k = 0; k < NST && k < my_tiles; ++k) issue(k);
+    for (int k = 0; k < NST && k < my_tiles; ++k) issue_B(k);
+  griddep_wait();
+  if (tid == 0)
+    for (int k = 0; k < NST && k < my_tiles; ++k) issue_K(k);
   bool alive = true;
   {
     const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
     if (__syncthreads_or(!ok)) alive = false;
   }
   for (int k = 0; alive && k < my_tiles; ++k) {
+    // the next reverse step's grid may be scheduled once every CTA is on its last tile
+    if (tid == 0 && k == my_tiles - 1) griddep_launch_dependents();
     const int t = wid + k * nworkers;
     const int tx = t % ntx, ty = t / ntx;
     const int x = tx * TILE_X + lx, y = ty * TILE_Y + ly;
@@ -472,6 +486,7 @@ template <typename S, int VS, bool MASK, bool FORCE, bool LAM>
 static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typename RealOf<S>::type> &g,
                                     const Physics<typename RealOf<S>::type> &p,
                                     const AdjStir<typename RealOf<S>::type> &s, cudaStream_t st) {
+  // only a launch with kappa_{n+1} directly follows another reverse step
   using R = typename RealOf<S>::type;
   using TL = Tile<S, VS>;
   constexpr int NST = 2;
@@ -495,6 +510,19 @@ static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typenam
   if (workers < 1) workers = 1;
   const CUtensorMap &mB = *static_cast<const CUtensorMap *>(a.tB);
   const CUtensorMap &mK = LAM ? *static_cast<const CUtensorMap *>(a.tK) : mB;
+  if (LAM && a.chained) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(workers);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
+  }
   kern<<<workers, 256, smem, st>>>(mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
   return cudaGetLastError();
 }

@@ -1364,6 +1364,7 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
       a.cj = n >= 1 ? cj : 0.0;
       a.G = gtab((int)(n - lo));
       a.zpart = w + G.zpart + G.zpart_bytes * (size_t)(n - lo);
+      a.chained = n < hi - 1;  // the first reverse step of a segment follows its recomputation
       if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
       kc ^= 1;
     }

@@ -102,6 +102,8 @@ struct AdjointArgs {
   const void *B;           // post-collision buffer B_{n-1} (storage type)
   const void *kin;         // kappa_{n+1} (compute type), NULL for the last state
   const void *tB, *tK;     // host CUtensorMap load maps of B and kin (the layout of the state)
+  bool chained;            // the launch directly follows the reverse step of step n + 1 on the
+                           // stream, and B was written before that step (programmatic launch)
   void *kout;              // kappa_n
   double cj;               // objective weight of the state S_n
   double *acc;             // [blocks][4] FP64 accumulators
