@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--shape", default=None,
                    help="ctas,stages,stir_rows: use this launch shape instead of tuning (profiling runs)")
+    p.add_argument("--members", type=int, default=64,
+                   help="ensemble64: number of members (64; fewer only for profiling runs)")
+    p.add_argument("--adjoint-steps", type=int, default=2000,
+                   help="adjoint512: steps of the differentiated run (2000; fewer only for profiling runs)")
     p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512", "graphene", "channel"],
                    help="stirred: one lattice (default); ensemble64: 64 stirred members of uneven sizes "
                         "advanced by one persistent launch per step; adjoint512: gradient of the kinetic "
@@ -406,7 +410,7 @@ def run_ensemble(args):
     from paper_2205_04658_gb300 import rlbm, inputs
     torch.cuda.set_device(0)
     rlbm.lib()
-    sides = inputs.ensemble_sides(64, 4)
+    sides = inputs.ensemble_sides(args.members, 4)
     prec = args.precision
     kw = dict(eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4)
     stream = torch.cuda.Stream()
@@ -469,8 +473,9 @@ def run_ensemble(args):
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": "ensemble of 64 stirred lattices, sides %s (%d cells), %s storage, "
+            "config": {"workload": "ensemble of %d stirred lattices, sides %s (%d cells), %s storage, "
                                    "one persistent launch per step, CUDA-graph replay" % (
+                                       len(sides),
                                        "/".join(str(sides.count(v)) + "x" + str(v) for v in (256, 512, 768, 1024)),
                                        cells, prec.upper()),
                        "l2": "state %.1f GB > L2, no flush" % (cells * ALG_BYTES[prec] / 1e9)},
@@ -496,7 +501,7 @@ def run_adjoint(args):
     torch.cuda.set_device(0)
     rlbm.lib()
     nx = ny = 512
-    N = 2000
+    N = args.adjoint_steps
     prec = args.precision
     kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
     stream = torch.cuda.Stream()
@@ -532,7 +537,7 @@ def run_adjoint(args):
             "n_gpus": 1, "steps": reps, "warmup": max(1, args.warmup // 10), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": {"workload": "gradient of the 512x512 stirred run (shell 4<=|k|<=6, 34 modes, amp 1e-4, "
-                                   "seed 5, eta/s 0.05), 2000 steps, wrt 34 mode multipliers, eta/s, body force",
+                                   "seed 5, eta/s 0.05), %d steps, wrt 34 mode multipliers, eta/s, body force" % N,
                        "checkpoint_segment": int(round(N ** 0.5 + 0.4999)), "workspace_bytes": nbytes,
                        "step_launch_tuned_ms": tuned_ms},
             "forward_only_s": tf, "gradient_over_forward": t / tf,
