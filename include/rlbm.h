@@ -118,7 +118,10 @@ RLBM_API rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size
 
 /* Queue nsteps >= 0 time steps (stream + moments + Landau + equilibrium + collision
  * + force, one fused kernel per step).  Step n uses the stirring draws
- * Philox4x32-10(counter = (n mod 2^32, mode, n div 2^32, 0), key = seed).  Async. */
+ * Philox4x32-10(counter = (n mod 2^32, mode, n div 2^32, 0), key = seed).  Async.
+ * The 2nd .. nsteps-th launches of one call are chained to the previous step
+ * (programmatic dependent launch: each waits for the previous step's writes before it
+ * reads anything); the results are those of nsteps separate calls, bit for bit. */
 RLBM_API rlbm_status rlbm_step(rlbm_ctx *ctx, int64_t nsteps);
 
 /* Moments of the current state f_n: eps, u^x, u^y (host arrays of nx*ny, each may be

@@ -987,6 +987,7 @@ rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers, void *de
     d.mode_kx = c->at<int>(c->L.mode_kx); d.row_start = c->at<int>(c->L.row_start);
     d.seed = c->cfg.seed; d.round_key = c->phys.round_key; d.err = c->at<unsigned>(c->L.err);
     d.ntx = (c->cfg.nx + 31) / 32;
+    d.rcp_ntx = 1.0f / (float)d.ntx;
     const int nt = d.ntx * ((c->cfg.ny + 7) / 8);
     tile0[i + 1] = tile0[i] + nt;
     entry0[i + 1] = entry0[i] + (c->L.nmodes ? (long long)c->L.nrows * c->cfg.nx : 0);

@@ -490,7 +490,7 @@ template <typename R> __device__ __forceinline__ Stir<R> member_stir(const Membe
 }
 
 template <typename S, int VS, bool MASK, bool FORCE, int CPT, int NST>
-__global__ void __launch_bounds__(NTHREADS / CPT)
+__global__ void __launch_bounds__(NTHREADS / CPT, CPT == 2 ? 4 : 1)  // two-cell paths: 4 CTAs/SM
 batch_step_kernel(const BatchTables bt, const Geometry<typename RealOf<S>::type> wts,
                   const Physics<typename RealOf<S>::type> p0, const int srows_in, const double amp,
                   const long long *__restrict__ bstep_ptr) {
@@ -516,7 +516,9 @@ batch_step_kernel(const BatchTables bt, const Geometry<typename RealOf<S>::type>
   __syncthreads();
   // thread 0: stage s takes tile t of the list (handed out by the launch's counter, so a
   // CTA that runs ahead takes more tiles), or, with t past the end, only completes its
-  // barrier; the tile's member is resolved here, once, into the stage's TileInfo
+  // barrier; the tile's member is resolved here, once, into the stage's TileInfo.  A CTA's
+  // tiles only increase, so the member search starts at the previous tile's member.
+  int m_last = 0;
   auto fill = [&](int s, int t) {
     TileInfo &ti = info[s];
     uint64_t *b = &bar[s];
@@ -525,10 +527,17 @@ batch_step_kernel(const BatchTables bt, const Geometry<typename RealOf<S>::type>
       mbar_arrive(b);
       return;
     }
-    const int m = find_member(bt.tile0, bt.n, t);
+    int m = m_last;
+    while (bt.tile0[m + 1] <= t) ++m;  // tile0[n] = ntiles > t ends the search
+    m_last = m;
     const MemberDesc &d = bt.mem[m];
     const int lt = t - bt.tile0[m];
-    const int x0 = (lt % d.ntx) * TILE_X, y0 = (lt / d.ntx) * TILE_Y;
+    // row = lt / ntx, column = lt mod ntx: the float quotient is within a unit or two of
+    // the exact one (lt < 2^24), then corrected exactly
+    int row = (int)((float)lt * d.rcp_ntx), col = lt - row * d.ntx;
+    while (col < 0) { --row; col += d.ntx; }
+    while (col >= d.ntx) { ++row; col -= d.ntx; }
+    const int x0 = col * TILE_X, y0 = row * TILE_Y;
     const long long n = d.step0 + bstep;
     const int cur = (d.cur0 + (int)(bstep & 1)) & 1;
     ti.dims = BatchDims{d.nx, d.ny, d.pitch, d.walls, d.plane, d.nbmask};

@@ -62,6 +62,7 @@ struct alignas(128) MemberDesc {
   unsigned round_key;
   unsigned *err;
   int ntx;                 // tiles per row
+  float rcp_ntx;           // 1 / ntx (tile index -> row and column with one correction)
 };
 
 // Prefix tables of a batch (device): tiles, stirring-table entries and draws per member.

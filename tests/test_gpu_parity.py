@@ -248,3 +248,26 @@ def test_launch_shapes_give_identical_results(R):
     for o in outs[1:]:
         for k in range(3):
             assert np.array_equal(o[k], outs[0][k])
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_chained_steps_match_single_steps(R, precision):
+    """Steps 2..N of one rlbm_step(N) call are chained (programmatic dependent launch);
+    the state is bit-identical to N calls of one step each, for lattices where a CTA takes
+    one tile and where it takes many."""
+    for nx, ny, shape in ((96, 40, (0, 2, 1)), (512, 256, (0, 2, 1)), (512, 256, (0, 1, 1))):
+        kw = dict(eta_over_s=0.05, kmin=3, kmax=6, force_amp=1e-3, seed=9)
+        states = []
+        for single in (False, True):
+            lat = R.Lattice(nx, ny, precision=precision, **kw)
+            lat.set_launch(*shape)
+            if single:
+                for _ in range(30):
+                    lat.step(1)
+            else:
+                lat.step(30)
+            h, step = lat.get_state()
+            assert step == 30
+            states.append(h)
+            lat.close()
+        assert np.array_equal(states[0], states[1])
