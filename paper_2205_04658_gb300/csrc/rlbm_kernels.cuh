@@ -321,10 +321,12 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
   // barriers: one per stage, then one for the mode data; then the tile of each stage
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * stage_stride);
   int *tile_of = reinterpret_cast<int *>(smem + NST * stage_stride + 32);
+  int *tile_xy = tile_of + NST;  // the stage's tile column | row << 16, set with tile_of
 
   const int tid = threadIdx.x;
   const int ntx = (g.nx + TILE_X - 1) / TILE_X, nty = (g.ny + TILE_Y - 1) / TILE_Y;
   const int ntiles = ntx * nty;
+  const float rcp_ntx = 1.0f / (float)ntx;
   const uint32_t stage_bytes = TL::IN_BYTES + srows * (TL::G_ROW + TL::EY_ROW);
   // The mode data of step n+1 (coefficients, k_x, row ranges), copied on its own barrier
   // when it fits in the `prep` area past the barriers.
@@ -358,7 +360,12 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
       griddep_launch_dependents();
       return;
     }
-    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    // row = t / ntx, column = t mod ntx: the float quotient corrected exactly (t < 2^24)
+    int row = (int)((float)t * rcp_ntx), col = t - row * ntx;
+    while (col < 0) { --row; col += ntx; }
+    while (col >= ntx) { ++row; col -= ntx; }
+    tile_xy[s] = col | (row << 16);
+    const int x0 = col * TILE_X, y0 = row * TILE_Y;
     unsigned char *st0 = smem + s * stage_stride;
     mbar_expect_tx(b, stage_bytes);
     tma_load_3d(st0, &tin, b, x0 + TL::XOFF - TL::V, y0, 0);
@@ -408,8 +415,9 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
     const int s = k % NST;
     const int t = tile_of[s];
     if (t < 0) break;
-    tile_cells<S, VS, MASK, FORCE, CPT>(smem + s * stage_stride, ey_off, fout, (t % ntx) * TILE_X,
-                                        (t / ntx) * TILE_Y, tid, g, g, p, st, staged, err);
+    const int xy = tile_xy[s];
+    tile_cells<S, VS, MASK, FORCE, CPT>(smem + s * stage_stride, ey_off, fout, (xy & 0xffff) * TILE_X,
+                                        (xy >> 16) * TILE_Y, tid, g, g, p, st, staged, err);
     if (NST == 1) {  // the only stage is free once every thread is done with it
       __syncthreads();
       if (tid == 0) {
