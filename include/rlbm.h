@@ -127,7 +127,9 @@ RLBM_API rlbm_status rlbm_step(rlbm_ctx *ctx, int64_t nsteps);
 /* Moments of the current state f_n: eps, u^x, u^y (host arrays of nx*ny, each may be
  * NULL; zero at solid cells) and totals (host double[4], may be NULL):
  * sum T^00, sum T^0x, sum T^0y, sum 1/2 |v|^2 over fluid cells, v = u^i / u^0.
- * Runs the streaming and Landau matching of the next step without storing it. Syncs. */
+ * Runs the streaming and Landau matching of the next step without storing it, in the
+ * context's compute type: FP64 for F64; FP32 for the others, with the FP64 re-solve of
+ * the step kernel and the totals' FP32 deviation sums added per block in FP64. Syncs. */
 RLBM_API rlbm_status rlbm_moments(rlbm_ctx *ctx, double *eps, double *ux, double *uy, double *totals);
 
 /* Energy spectrum of the current state's velocity v = u^i / u^0 (Sec. "Turbulence"):

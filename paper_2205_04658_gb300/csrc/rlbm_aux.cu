@@ -124,14 +124,11 @@ __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restric
       const int base = (j / Ns) * Ns * R + jm;
       if (R <= 8) {
         double2 v[8];
-        for (int r = 0; r < R; ++r) {
-          const long long t = ((long long)r * jm * stride) % n;
-          v[r] = cmul(src[j + r * nR], tw[t]);
-        }
+        for (int r = 0; r < R; ++r) v[r] = cmul(src[j + r * nR], tw[r * jm * stride]);  // r jm stride < n
         for (int k = 0; k < R; ++k) {
           double2 acc = v[0];
           for (int r = 1; r < R; ++r) {
-            const long long t = ((long long)r * k % R) * nR;
+            const int t = ((r * k) % R) * nR;
             acc.x += v[r].x * tw[t].x - v[r].y * tw[t].y;
             acc.y += v[r].x * tw[t].y + v[r].y * tw[t].x;
           }
@@ -141,9 +138,8 @@ __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restric
         for (int k = 0; k < R; ++k) {
           double2 acc = make_double2(0.0, 0.0);
           for (int r = 0; r < R; ++r) {
-            const long long t1 = ((long long)r * jm * stride) % n;
-            const double2 v = cmul(src[j + r * nR], tw[t1]);
-            const double2 e = tw[((long long)r * k % R) * nR];
+            const double2 v = cmul(src[j + r * nR], tw[r * jm * stride]);
+            const double2 e = tw[((r * k) % R) * nR];
             acc.x += v.x * e.x - v.y * e.y;
             acc.y += v.x * e.y + v.y * e.x;
           }

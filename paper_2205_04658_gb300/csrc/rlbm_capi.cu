@@ -342,10 +342,10 @@ cudaError_t dispatch_moments(rlbm_ctx *c) {
   const double e0 = c->cfg.eps0;
   cudaError_t r;
   switch (c->cfg.precision) {
-    case RLBM_F64: r = launch_moments_f64(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
-    case RLBM_F32: r = launch_moments_f32(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
-    case RLBM_F16: r = launch_moments_f16(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
-    default: r = launch_moments_bf16(c->cfg.vset, fin, c->geom, e0, e, ux, uy, part, err, c->block, c->stream); break;
+    case RLBM_F64: r = launch_moments_f64(c->cfg.vset, fin, c->geom, e0, c->phys.vmax2, e, ux, uy, part, err, c->block, c->stream); break;
+    case RLBM_F32: r = launch_moments_f32(c->cfg.vset, fin, c->geom, e0, c->phys.vmax2, e, ux, uy, part, err, c->block, c->stream); break;
+    case RLBM_F16: r = launch_moments_f16(c->cfg.vset, fin, c->geom, e0, c->phys.vmax2, e, ux, uy, part, err, c->block, c->stream); break;
+    default: r = launch_moments_bf16(c->cfg.vset, fin, c->geom, e0, c->phys.vmax2, e, ux, uy, part, err, c->block, c->stream); break;
   }
   if (r != cudaSuccess) return r;
   const long long nblocks = (long long)((c->cfg.nx + c->block.x - 1) / c->block.x) * ((c->cfg.ny + c->block.y - 1) / c->block.y);

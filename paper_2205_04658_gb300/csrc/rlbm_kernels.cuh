@@ -686,14 +686,22 @@ __device__ __forceinline__ void pull_global(const S *__restrict__ fin, const Geo
 
 template <typename S, int VS, bool MASK>
 __global__ void __launch_bounds__(256)
-moments_kernel(const S *__restrict__ fin, const Geometry<typename RealOf<S>::type> g, double eps0,
+moments_kernel(const S *__restrict__ fin, const Geometry<typename RealOf<S>::type> g, double eps0, float vmax2,
                double *__restrict__ eps, double *__restrict__ ux, double *__restrict__ uy,
                double *__restrict__ partials, unsigned *__restrict__ err) {
   using R = typename RealOf<S>::type;
   constexpr int Q = VSet<VS>::Q;
+  constexpr bool F64 = sizeof(R) == 8;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  // Per-cell terms of the block totals: T^00, T^0x, T^0y, 1/2 |v|^2.  FP64 storage sums
+  // them in FP64.  The other storage types (FP32 state) match and sum in FP32, as the step
+  // kernel does (GB300's FP64 rate is 1/64 of FP32): the FP32 terms are the deviations
+  // e, m_x, m_y (order u), summed per warp, and the warps' sums are added in FP64 to the
+  // exact count of fluid cells (T^00 = eps0 (1 + e)).
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float accf[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  int fluid = 0;
   if (x < g.nx && y < g.ny) {
     const long long c = (long long)y * g.nx + x;
     unsigned nb = MASK ? g.nbmask[c] : 0u;
@@ -702,36 +710,73 @@ moments_kernel(const S *__restrict__ fin, const Geometry<typename RealOf<S>::typ
     } else {
       R h[Q];
       pull_global<S, R, VS, MASK>(fin, g, x, y, nb, h);
-      const Mom<double> M = moments_of<double, R, VS, false>(h);
-      const Macro<double> m = macro_from<double, VS>(M, 40, 1e-12);
-      if (!m.ok) atomicOr(err, (1.0 + m.eps_m1 > 0.0 && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
-      eps[c] = eps0 * (1.0 + m.eps_m1);
-      ux[c] = m.ux;
-      uy[c] = m.uy;
-      acc[0] = eps0 * (1.0 + M.e);
-      acc[1] = eps0 * M.mx;
-      acc[2] = eps0 * M.my;
-      acc[3] = 0.5 * (m.vx * m.vx + m.vy * m.vy);
+      if constexpr (F64) {
+        const Mom<double> M = moments_of<double, R, VS, false>(h);
+        const Macro<double> m = macro_from<double, VS>(M, 40, 1e-12);
+        if (!m.ok) atomicOr(err, (1.0 + m.eps_m1 > 0.0 && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+        eps[c] = eps0 * (1.0 + m.eps_m1);
+        ux[c] = m.ux;
+        uy[c] = m.uy;
+        acc[0] = eps0 * (1.0 + M.e);
+        acc[1] = eps0 * M.mx;
+        acc[2] = eps0 * M.my;
+        acc[3] = 0.5 * (m.vx * m.vx + m.vy * m.vy);
+      } else {
+        // Landau in FP32, re-solved in FP64 where it has not converged or |v| > vmax
+        const Mom<float> M = moments_of<float, float, VS, false>(h);
+        const Macro<float> m = cell_macro<float, VS>(h, M, vmax2);
+        if (!m.ok) atomicOr(err, (1.0f + m.eps_m1 > 0.0f && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+        eps[c] = eps0 * (1.0 + (double)m.eps_m1);
+        ux[c] = m.ux;
+        uy[c] = m.uy;
+        accf[0] = M.e;
+        accf[1] = M.mx;
+        accf[2] = M.my;
+        accf[3] = 0.5f * (m.vx * m.vx + m.vy * m.vy);
+        fluid = 1;
+      }
     }
   }
   __shared__ double red[4][32];
+  __shared__ int cnt[32];
   const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
   const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if constexpr (F64) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    double v = acc[k];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) red[k][warp] = v;
+    for (int k = 0; k < 4; ++k) {
+      double v = acc[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[k][warp] = v;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float v = accf[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[k][warp] = (double)v;
+    }
+    const int nf = __popc(__ballot_sync(0xffffffffu, fluid));
+    if (lane == 0) cnt[warp] = nf;
   }
   __syncthreads();
   const int nwarps = (blockDim.x * blockDim.y + 31) / 32;
   if (warp == 0) {
+    double tot[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       double v = lane < nwarps ? red[k][lane] : 0.0;
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 4 + k] = v;
+      tot[k] = v;
     }
+    if (!F64) {
+      int nf = lane < nwarps ? cnt[lane] : 0;
+      for (int off = 16; off > 0; off >>= 1) nf += __shfl_down_sync(0xffffffffu, nf, off);
+      tot[0] = eps0 * ((double)nf + tot[0]);
+      tot[1] *= eps0;
+      tot[2] *= eps0;
+    }
+    if (lane == 0)
+      for (int k = 0; k < 4; ++k) partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 4 + k] = tot[k];
   }
 }
 
@@ -1009,20 +1054,20 @@ static cudaError_t launch_batch_t(int vset, const BatchTables &bt, const HostGeo
 }
 
 template <typename S>
-static cudaError_t launch_moments_t(int vset, const void *fin, const HostGeom &hg, double eps0, double *eps,
-                                    double *ux, double *uy, double *partials, unsigned *err, dim3 block,
-                                    cudaStream_t stream) {
+static cudaError_t launch_moments_t(int vset, const void *fin, const HostGeom &hg, double eps0, double vmax2,
+                                    double *eps, double *ux, double *uy, double *partials, unsigned *err,
+                                    dim3 block, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
   const Geometry<R> g = to_geom<R>(hg);
   const dim3 grid((hg.nx + block.x - 1) / block.x, (hg.ny + block.y - 1) / block.y);
   const bool mask = hg.nbmask != nullptr;
   const S *a = (const S *)fin;
   if (vset == 3) {
-    if (mask) moments_kernel<S, 3, true><<<grid, block, 0, stream>>>(a, g, eps0, eps, ux, uy, partials, err);
-    else moments_kernel<S, 3, false><<<grid, block, 0, stream>>>(a, g, eps0, eps, ux, uy, partials, err);
+    if (mask) moments_kernel<S, 3, true><<<grid, block, 0, stream>>>(a, g, eps0, (float)vmax2, eps, ux, uy, partials, err);
+    else moments_kernel<S, 3, false><<<grid, block, 0, stream>>>(a, g, eps0, (float)vmax2, eps, ux, uy, partials, err);
   } else {
-    if (mask) moments_kernel<S, 2, true><<<grid, block, 0, stream>>>(a, g, eps0, eps, ux, uy, partials, err);
-    else moments_kernel<S, 2, false><<<grid, block, 0, stream>>>(a, g, eps0, eps, ux, uy, partials, err);
+    if (mask) moments_kernel<S, 2, true><<<grid, block, 0, stream>>>(a, g, eps0, (float)vmax2, eps, ux, uy, partials, err);
+    else moments_kernel<S, 2, false><<<grid, block, 0, stream>>>(a, g, eps0, (float)vmax2, eps, ux, uy, partials, err);
   }
   return cudaGetLastError();
 }
@@ -1093,10 +1138,10 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
                                       int grid_limit, int ntiles, cudaStream_t st) {                        \
     return launch_batch_t<S>(vset, bt, w, p, srows, amp, bstep, mask, stages, grid_limit, ntiles, st);    \
   }                                                                                                      \
-  cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
-                                   double *ux, double *uy, double *part, unsigned *err, dim3 b,         \
-                                   cudaStream_t st) {                                                    \
-    return launch_moments_t<S>(vset, fin, g, eps0, e, ux, uy, part, err, b, st);                         \
+  cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double vmax2, \
+                                   double *e, double *ux, double *uy, double *part, unsigned *err,       \
+                                   dim3 b, cudaStream_t st) {                                            \
+    return launch_moments_t<S>(vset, fin, g, eps0, vmax2, e, ux, uy, part, err, b, st);                  \
   }                                                                                                      \
   cudaError_t launch_init_##SUF(int vset, void *fout, const HostGeom &g, double eps0, const double *e,  \
                                 const double *ux, const double *uy, cudaStream_t st) {                   \

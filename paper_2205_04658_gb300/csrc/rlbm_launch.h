@@ -84,9 +84,9 @@ struct BatchTables {
   cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
                                       int srows, double amp, const long long *bstep, bool mask, int stages, \
                                       int grid_limit, int ntiles, cudaStream_t st);                       \
-  cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double *e, \
-                                   double *ux, double *uy, double *part, unsigned *err, dim3 b,         \
-                                   cudaStream_t st);                                                     \
+  cudaError_t launch_moments_##SUF(int vset, const void *fin, const HostGeom &g, double eps0, double vmax2, \
+                                   double *e, double *ux, double *uy, double *part, unsigned *err,       \
+                                   dim3 b, cudaStream_t st);                                             \
   cudaError_t launch_init_##SUF(int vset, void *fout, const HostGeom &g, double eps0, const double *e,  \
                                 const double *ux, const double *uy, cudaStream_t st);                   \
   cudaError_t launch_open_ghosts_##SUF(int vset, void *f, const HostGeom &g, double ux_in, cudaStream_t st); \
