@@ -451,9 +451,9 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
 // The tiles of all members form one list (member m owns tiles tile0[m] .. tile0[m+1]);
 // CTAs walk it exactly as the single-lattice kernel walks one lattice (tiles handed out
 // by a counter, cleared between launches by the kernel that advances the step), and take
-// each tile's member (binary search), buffers and TMA descriptors from the member table;
-// the thread that stages a tile resolves it once and leaves what the tile needs in
-// shared memory beside the stage.
+// each tile's member (searched forward from the CTA's previous tile's member), buffers and
+// TMA descriptors from the member table; the thread that stages a tile resolves it once
+// and leaves what the tile needs in shared memory beside the stage.
 // The per-member step is step0 + *bstep, so a captured CUDA graph of launches can
 // replay with the counter advanced by a one-thread kernel between launches.  All members
 // share the velocity set, storage type, dt/a, eta/s, eps0, the force shell and the
