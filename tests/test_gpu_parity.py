@@ -271,3 +271,23 @@ def test_chained_steps_match_single_steps(R, precision):
             states.append(h)
             lat.close()
         assert np.array_equal(states[0], states[1])
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-11), ("f32", 2e-6)])
+def test_totals_match_oracle_with_walls_and_discs(R, precision, tol):
+    """Totals (sum T^00, T^0x, T^0y over fluid cells, 1/2 sum |v|^2) on a ragged lattice with
+    walls, discs and a body force.  FP32 states take them as FP32 deviation sums per warp
+    added in FP64 to the exact count of fluid cells; FP64 states sum in FP64."""
+    nx, ny = 72, 40
+    mask, _ = inputs.disc_mask(nx, ny, radius=2, fraction=0.08, seed=3, walls_y=True)
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=12, eps_amp=0.02, u_amp=0.04, kmax=3)
+    cfg = dict(nx=nx, ny=ny, walls_y=1, solid=mask, eta_over_s=0.05, body_force=(2e-3, -1e-3),
+               kmin=2, kmax=4, force_amp=1e-3, seed=6, init_eps=e, init_ux=ux, init_uy=uy)
+    ref = O.run(cfg, 30)[3]
+    lat = R.Lattice(nx, ny, precision=precision, **{k: v for k, v in cfg.items() if k not in ("nx", "ny")})
+    lat.step(30)
+    tot = lat.totals()
+    lat.close()
+    assert abs(tot[0] - ref[0]) <= tol * ref[0], (tot[0], ref[0])
+    assert np.abs(tot[1:3] - ref[1:3]).max() <= tol * ref[0], (tot[1:3], ref[1:3])
+    assert abs(tot[3] - ref[3]) <= (1e-9 if precision == "f64" else 1e-4) * ref[3], (tot[3], ref[3])
