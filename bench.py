@@ -66,6 +66,24 @@ def parse():
 E2E_JOB_STEPS, E2E_SPECTRUM_EVERY = 20000, 500
 
 
+def slowest(duration, world, device):
+    """The job time of N replicas: the largest of the ranks' durations (all-reduce max over
+    the process group; `device` is where the group's tensors live: "cuda" for NCCL, "cpu"
+    for gloo).  One rank: the duration itself."""
+    if world <= 1:
+        return float(duration)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(duration)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(world, cells, steps, seconds):
+    """Whole-job throughput of N replicas of `cells` cells each, `steps` steps in `seconds`."""
+    return world * cells * steps / seconds / 1e6
+
+
 def workload(args, rank):
     return dict(eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4, seed=2 + rank)
 
@@ -314,13 +332,9 @@ def run_gb300(args):
     clk = clocks.stop()
     lat.sync()
     times = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = slowest(sum(times), world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * cells * args.steps / (total_ms / 1e3) / 1e6
+    value = replica_mlups(world, cells, args.steps, total_ms / 1e3)
     peak, peak_kind = measured_peak()
     achieved = ALG_BYTES[prec] * cells / (statistics.mean(times) / 1e3) / 1e9
     traffic = committed_traffic(args)
@@ -361,12 +375,8 @@ def run_gb300(args):
         rlbm.rlbm_moments(ctx, pin[3].numpy(), pin[4].numpy(), pin[5].numpy(), tot.numpy())
         t1 = time.perf_counter()
         rlbm.rlbm_free(ctx)
-        dt = t1 - t0
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * cells * job / dt / 1e6, "unit": "MLUPS",
+        dt = slowest(t1 - t0, world, "cuda")
+        e2e = {"value": replica_mlups(world, cells, job, dt), "unit": "MLUPS",
                "h2d_bytes_per_step": 3 * 8 * cells / job,
                "d2h_bytes_per_step": (spec.numel() * 8 + 3 * 8 * cells + 32) / job,
                "job_steps": job, "seconds": dt,
