@@ -106,9 +106,24 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// DFT of length 4 (W = exp(-+2 pi i / 4) from the twiddle table, W^2 = -1) by two levels of
+// sums and differences: X_0 = a0 + a2, X_1 = a1 + a3, X_2 = a0 - a2, X_3 = a1 - a3.
+__device__ __forceinline__ void dft4(double2 v0, double2 v1, double2 v2, double2 v3, double2 W, double2 X[4]) {
+  const double2 a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = cmul(csub(v1, v3), W);
+  X[0] = cadd(a0, a2);
+  X[1] = cadd(a1, a3);
+  X[2] = csub(a0, a2);
+  X[3] = csub(a1, a3);
+}
+
 // One block transforms one row of length n in place (ping-pong between a and b);
 // tw[t] = exp(-2 pi i t / n).  Stage with radix R after radices of product Ns:
 //   v_r = x[j + r n/R] * w^(r (j mod Ns) n/(Ns R)),  y[(j div Ns) Ns R + (j mod Ns) + k Ns] = DFT_R(v)_k.
+// Radices 2, 4 and 8 use their butterflies (8 = two length-4 transforms of the even and
+// odd inputs joined by W_8^k); the others evaluate the length-R sums directly.
 __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restrict__ tw,
                                 FftPlan plan) {
   const int n = plan.n;
@@ -122,7 +137,28 @@ __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restric
     for (int j = threadIdx.x; j < nR; j += blockDim.x) {
       const int jm = j % Ns;
       const int base = (j / Ns) * Ns * R + jm;
-      if (R <= 8) {
+      if (R == 2 || R == 4 || R == 8) {
+        double2 v[8];
+        for (int r = 0; r < R; ++r) v[r] = cmul(src[j + r * nR], tw[r * jm * stride]);  // r jm stride < n
+        if (R == 2) {
+          dst[base] = cadd(v[0], v[1]);
+          dst[base + Ns] = csub(v[0], v[1]);
+        } else if (R == 4) {
+          double2 X[4];
+          dft4(v[0], v[1], v[2], v[3], tw[nR], X);
+          for (int k = 0; k < 4; ++k) dst[base + k * Ns] = X[k];
+        } else {
+          double2 E[4], O[4];
+          const double2 W4 = tw[2 * nR];  // W_8^2
+          dft4(v[0], v[2], v[4], v[6], W4, E);
+          dft4(v[1], v[3], v[5], v[7], W4, O);
+          for (int k = 0; k < 4; ++k) {
+            const double2 t = k == 0 ? O[0] : cmul(O[k], tw[k * nR]);  // W_8^k O_k
+            dst[base + k * Ns] = cadd(E[k], t);
+            dst[base + (k + 4) * Ns] = csub(E[k], t);
+          }
+        }
+      } else if (R <= 8) {
         double2 v[8];
         for (int r = 0; r < R; ++r) v[r] = cmul(src[j + r * nR], tw[r * jm * stride]);  // r jm stride < n
         for (int k = 0; k < R; ++k) {
