@@ -409,7 +409,7 @@ def band_energy(ux, uy, k2lo, k2hi=0):
 
 
 # --------------------------------------------------------------------------
-# Driver
+# Time stepping over a window of the lattice
 # --------------------------------------------------------------------------
 DEFAULTS = dict(walls_y=0, vset=3, a=0.1, dt=0.05, eta_over_s=0.1, eps0=1.0,
                 body_force=(0.0, 0.0), kmin=0, kmax=0, force_amp=0.0, seed=0,
