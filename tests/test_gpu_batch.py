@@ -82,3 +82,29 @@ def test_batch_rejects_mismatched_physics(R):
     assert e.value.status == R.RLBM_E_INVAL
     a.close()
     c.close()
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_many_small_members_and_a_single_member(R, precision):
+    """40 members of two to nine tiles each (the staging thread's member search steps over
+    several members per tile; each CTA's share of the next-step tables spans several
+    members), and a batch of one member: both equal the members stepped alone."""
+    import torch
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(5)
+    shapes = [(int(rng.integers(1, 4)) * 32 - int(rng.integers(0, 20)), int(rng.integers(1, 3)) * 8 + 8)
+              for _ in range(40)]
+    for group in (shapes, [(200, 136)]):
+        alone = [make(R, precision, stream, nx, ny, 100 + i, False) for i, (nx, ny) in enumerate(group)]
+        batched = [make(R, precision, stream, nx, ny, 100 + i, False) for i, (nx, ny) in enumerate(group)]
+        for lat in alone:
+            lat.step(12)
+        b = R.Batch(batched, stream=stream)
+        b.step(12)
+        for a, c in zip(alone, batched):
+            ma, mc = a.moments(), c.moments()
+            for k in range(3):
+                assert np.array_equal(ma[k], mc[k])
+        b.close()
+        for lat in alone + batched:
+            lat.close()
