@@ -208,13 +208,16 @@ __device__ __forceinline__ void cell_adjoint(const R h[VSet<VS>::Q], const R lam
 //   cj    objective weight of S_n (1 / (N N_fluid), or 0 for the first state)
 //   acc   per-tile FP64 sums, accumulated over steps: d/d(ln omega0), F adjoint x, y, J
 //   zpart per tile row and k_y row r: sum over the tile's 8 rows of gF(x, y) EY_r(y)
+//   macro the step's eps/eps0 - 1, v_x, v_y, F_x, F_y per cell (5 planes of nx * ny) as the
+//         forward step kernel computed them when it recomputed the step, or NULL: Landau
+//         matching and the force synthesis are then done here
 template <typename S, int VS, bool MASK, bool FORCE, bool LAM, int NST>
 __global__ void __launch_bounds__(256)
 adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tK,
                typename RealOf<S>::type *__restrict__ kout, const Geometry<typename RealOf<S>::type> g,
                const Physics<typename RealOf<S>::type> p, const AdjStir<typename RealOf<S>::type> st,
                const typename RealOf<S>::type cj, double *__restrict__ acc, R4<typename RealOf<S>::type> *__restrict__ zpart,
-               unsigned *__restrict__ err) {
+               unsigned *__restrict__ err, const typename RealOf<S>::type *__restrict__ macro) {
   using R = typename RealOf<S>::type;
   using TL = Tile<S, VS>;
   static_assert(sizeof(S) == sizeof(R), "the adjoint runs on FP32 or FP64 storage");
@@ -283,6 +286,14 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
     for (int q = 0; q < Q; ++q) kap[q] = R(0);
     if (fluid) {
       R h[Q], lam[Q];
+      // the forward's Landau solution and force of this cell, loaded first so that the
+      // loads overlap the pulls
+      R mv[5] = {R(0), R(0), R(0), R(0), R(0)};
+      if (macro) {
+        const long long nc = (long long)g.nx * g.ny, c = (long long)y * g.nx + x;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) mv[k] = macro[k * nc + c];
+      }
       pull_staged<R, VS, MASK, -1>(reinterpret_cast<const R *>(tileB), PL, TL::TXB, b0, g, nb, h);
       if (LAM) {
         pull_staged<R, VS, MASK, 1>(tileK, PL, TL::TXB, b0, g, nb, lam);
@@ -291,10 +302,25 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
         for (int q = 0; q < Q; ++q) lam[q] = R(0);
       }
       const Mom<R> M = moments_of<R, R, VS, FORCE>(h);
-      const Macro<R> m = cell_macro<R, VS>(h, M, p.vmax2);
-      if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+      Macro<R> m;
       R Fx = p.body_x, Fy = p.body_y;
-      if (FORCE) {
+      if (macro) {
+        // u^mu = gamma (1, v) as the step kernel forms it from v
+        const R gam = FM<R>::rsqrt(R(1) - fma(mv[1], mv[1], mv[2] * mv[2]));
+        m.eps_m1 = mv[0];
+        m.vx = mv[1];
+        m.vy = mv[2];
+        m.u0 = gam;
+        m.ux = gam * mv[1];
+        m.uy = gam * mv[2];
+        m.ok = true;
+        Fx = mv[3];
+        Fy = mv[4];
+      } else {
+        m = cell_macro<R, VS>(h, M, p.vmax2);
+        if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+      }
+      if (FORCE && !macro) {
         // two rows per iteration, in two partial sums: both rows' loads are in flight at once
         const R *ey = reinterpret_cast<const R *>(st.EY);
         R Fx2 = R(0), Fy2 = R(0);
@@ -521,9 +547,11 @@ static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typenam
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
+    return cudaLaunchKernelEx(&cfg, kern, mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err,
+                              (const R *)a.macro);
   }
-  kern<<<workers, 256, smem, st>>>(mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err);
+  kern<<<workers, 256, smem, st>>>(mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err,
+                                   (const R *)a.macro);
   return cudaGetLastError();
 }
 

@@ -206,18 +206,19 @@ namespace {
 // Step n from the buffer behind `ti` into `fout`; its stirring rows come from s.G_cur and,
 // when staged by TMA, through `tgmap` (NULL: the context's table of step parity n & 1).
 // `chained`: the launch directly follows the step kernel of step n - 1 on the stream
-// (programmatic dependent launch).
+// (programmatic dependent launch).  `macro_out` (compute type, 5 planes of nx * ny, may be
+// NULL): each fluid cell's eps/eps0 - 1, v_x, v_y, F_x, F_y of the step, for the reverse sweep.
 cudaError_t dispatch_step_raw(rlbm_ctx *c, const CUtensorMap *ti, void *fout, int64_t n, const HostStir &s,
-                              const CUtensorMap *tgmap = nullptr, bool chained = false) {
+                              const CUtensorMap *tgmap = nullptr, bool chained = false, void *macro_out = nullptr) {
   unsigned *err = c->at<unsigned>(c->L.err);
   const void *tg = tgmap ? tgmap : &c->tmap_G[n & 1], *te = &c->tmap_EY;
   int *ctr = c->at<int>(c->L.ctr);
   const unsigned seq = c->launch_seq++;
   switch (c->cfg.precision) {
-    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
-    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
-    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
-    default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, c->stream);
+    case RLBM_F64: return launch_step_f64(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, macro_out, c->stream);
+    case RLBM_F32: return launch_step_f32(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, macro_out, c->stream);
+    case RLBM_F16: return launch_step_f16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, macro_out, c->stream);
+    default: return launch_step_bf16(c->cfg.vset, ti, tg, te, fout, c->geom, c->phys, s, err, c->grid_limit, c->stages, c->stir_rows, ctr, seq, chained, macro_out, c->stream);
   }
 }
 
@@ -1137,7 +1138,8 @@ struct GradLayout {
   int64_t N;
   int seg, K, nslots;
   size_t state_bytes, kap_bytes, table_bytes, zpart_bytes;
-  size_t ckpt, slots, kap[2], acc, gst, zpart, zsum, tw, twf, gstep, gsig, out, total;
+  size_t ckpt, slots, kap[2], acc, gst, zpart, zsum, tw, twf, gstep, gsig, out, macro, scratch, gscratch, total;
+  size_t macro_bytes;
   long long nblocks;
   int nby;
 };
@@ -1172,6 +1174,11 @@ GradLayout grad_layout(const rlbm_ctx *c, int64_t N, int32_t segment) {
   G.gstep = take(8 * (size_t)c->L.nmodes * (size_t)N);
   G.gsig = take(8 * (size_t)c->L.nmodes);
   G.out = take(64);
+  // each recomputed step's eps/eps0 - 1, v_x, v_y, F_x, F_y per cell, for the reverse sweep
+  G.macro_bytes = align_up(5 * rb * (size_t)c->cfg.nx * c->cfg.ny);
+  G.macro = take(G.macro_bytes * G.seg);
+  G.scratch = take(G.state_bytes);   // output of the last recomputed step of a segment (unused)
+  G.gscratch = take(G.table_bytes);  // and the stirring rows it prepares for the next step
   G.total = off;
   return G;
 }
@@ -1328,6 +1335,7 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   a.tB = &c->tmap_in[c->cur];
   a.kin = nullptr;
   a.tK = nullptr;
+  a.macro = nullptr;  // S_N is no step's input: matched and forced here
   a.kout = w + G.kap[kc];
   a.cj = cj;
   a.G = c->ws + c->L.G[0];
@@ -1344,16 +1352,19 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
                                        : launch_stir_prime_f32(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream);
       if (e != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
     }
-    for (int64_t n = lo; n <= hi - 2; ++n) {
+    // steps lo .. hi-1 again, each keeping its cells' Landau solution and force for the
+    // reverse step of the same index (the last one's state and next rows are not needed)
+    for (int64_t n = lo; n <= hi - 1; ++n) {
       const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
       HostStir st = stir_for_step(c, s0 + n);
       if (c->L.nmodes) {
         st.G_cur = gtab((int)(n - lo));
-        st.G_next = gtab((int)(n - lo + 1));
+        st.G_next = n == hi - 1 ? w + G.gscratch : gtab((int)(n - lo + 1));
       }
       c->phys.step = s0 + n;
-      if ((e = dispatch_step_raw(c, ti, slot((int)(n - lo)), s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr,
-                                 n > lo)) != cudaSuccess)
+      void *fout = n == hi - 1 ? w + G.scratch : slot((int)(n - lo));
+      if ((e = dispatch_step_raw(c, ti, fout, s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr, n > lo,
+                                 w + G.macro + G.macro_bytes * (size_t)(n - lo))) != cudaSuccess)
         return c->cuda_fail(e, "step kernel launch (recompute)");
     }
     for (int64_t n = hi - 1; n >= lo; --n) {
@@ -1365,6 +1376,7 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
       a.cj = n >= 1 ? cj : 0.0;
       a.G = gtab((int)(n - lo));
       a.zpart = w + G.zpart + G.zpart_bytes * (size_t)(n - lo);
+      a.macro = w + G.macro + G.macro_bytes * (size_t)(n - lo);
       a.chained = n < hi - 1;  // the first reverse step of a segment follows its recomputation
       if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
       kc ^= 1;

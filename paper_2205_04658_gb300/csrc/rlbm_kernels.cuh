@@ -52,7 +52,7 @@ template <typename S, int VS, bool MASK, bool FORCE, int CPT, class G, class W>
 __device__ __forceinline__ typename std::enable_if<CPT == 1>::type
 tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid, const G &g, const W &wts,
            const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &st, bool staged,
-           unsigned *err) {
+           unsigned *err, typename RealOf<S>::type *macro_out) {
   using R = typename RealOf<S>::type;
   using V = VSet<VS>;
   using TL = Tile<S, VS>;
@@ -129,6 +129,14 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
           }
         }
       }
+      if (macro_out) {  // the cell's Landau solution and force, kept for the reverse sweep
+        const long long nc = (long long)g.nx * g.ny, c = (long long)y * g.nx + x;
+        macro_out[c] = m.eps_m1;
+        macro_out[nc + c] = m.vx;
+        macro_out[2 * nc + c] = m.vy;
+        macro_out[3 * nc + c] = Fx;
+        macro_out[4 * nc + c] = Fy;
+      }
       const Coll<R> cf = coll_coeffs<R, VS, FORCE>(M, m, p.omega0, p.fpref, Fx, Fy);
       collide_all<R, VS, FORCE>(cf, h, hn);
     } else {
@@ -161,7 +169,7 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
 template <typename S, int VS, bool MASK, bool FORCE, int CPT, class G, class W>
 __device__ __forceinline__ typename std::enable_if<CPT == 2>::type
 tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid, const G &g, const W &wts,
-           const Physics<float> &p, const Stir<float> &st, bool staged, unsigned *err) {
+           const Physics<float> &p, const Stir<float> &st, bool staged, unsigned *err, float *macro_out) {
   using V = VSet<VS>;
   using TL = Tile<S, VS>;
   using T = F2;
@@ -241,6 +249,25 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         }
       }
     }
+    if (macro_out) {  // the cells' Landau solutions and forces, kept for the reverse sweep
+      const long long nc = (long long)g.nx * g.ny;
+      if (flA) {
+        const long long c = (long long)yA * g.nx + x;
+        macro_out[c] = m.eps_m1.v.x;
+        macro_out[nc + c] = m.vx.v.x;
+        macro_out[2 * nc + c] = m.vy.v.x;
+        macro_out[3 * nc + c] = Fx.v.x;
+        macro_out[4 * nc + c] = Fy.v.x;
+      }
+      if (flB) {
+        const long long c = (long long)yB * g.nx + x;
+        macro_out[c] = m.eps_m1.v.y;
+        macro_out[nc + c] = m.vx.v.y;
+        macro_out[2 * nc + c] = m.vy.v.y;
+        macro_out[3 * nc + c] = Fx.v.y;
+        macro_out[4 * nc + c] = Fy.v.y;
+      }
+    }
     const Coll<T> cf = coll_coeffs<T, VS, FORCE>(M, m, T(p.omega0), T(p.fpref), Fx, Fy);
     collide_all<T, VS, FORCE>(cf, h, hn);
   }
@@ -300,13 +327,13 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
 // relaxes, adds the force and stores the Q results with coalesced stores, refreshing
 // the ghost copies of boundary cells.
 // ---------------------------------------------------------------------------
-template <typename S, int VS, bool MASK, bool FORCE, int CPT, int NST>
+template <typename S, int VS, bool MASK, bool FORCE, int CPT, int NST, bool STORE>
 __global__ void __launch_bounds__(NTHREADS / CPT)
 step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tG,
             const __grid_constant__ CUtensorMap tEY, S *__restrict__ fout,
             const Geometry<typename RealOf<S>::type> g, const Physics<typename RealOf<S>::type> p,
             const Stir<typename RealOf<S>::type> st, int prep_bytes, int srows_in, int *__restrict__ tile_ctr,
-            unsigned seq, unsigned *__restrict__ err) {
+            unsigned seq, unsigned *__restrict__ err, typename RealOf<S>::type *__restrict__ macro_out) {
   using R = typename RealOf<S>::type;
   using TL = Tile<S, VS>;
   constexpr int NT = NTHREADS / CPT;
@@ -417,7 +444,8 @@ step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUt
     if (t < 0) break;
     const int xy = tile_xy[s];
     tile_cells<S, VS, MASK, FORCE, CPT>(smem + s * stage_stride, ey_off, fout, (xy & 0xffff) * TILE_X,
-                                        (xy >> 16) * TILE_Y, tid, g, g, p, st, staged, err);
+                                        (xy >> 16) * TILE_Y, tid, g, g, p, st, staged, err,
+                                        STORE ? macro_out : static_cast<R *>(nullptr));
     if (NST == 1) {  // the only stage is free once every thread is done with it
       __syncthreads();
       if (tid == 0) {
@@ -586,7 +614,7 @@ batch_step_kernel(const BatchTables bt, const Geometry<typename RealOf<S>::type>
     if (FORCE && staged) st.nrows = srows;
     else if (FORCE) st = member_stir<R>(bt.mem[ti.m], ti.n);
     tile_cells<S, VS, MASK, FORCE, CPT>(smem + s * stage_stride, ey_off, (S *)ti.fout, ti.x0, ti.y0, tid, ti.dims,
-                                        wts, p, st, staged, ti.err);
+                                        wts, p, st, staged, ti.err, static_cast<R *>(nullptr));
     if (NST == 1) {  // the only stage is free once every thread is done with it
       __syncthreads();
       if (tid == 0) {
@@ -895,15 +923,19 @@ template <typename R> static Stir<R> to_stir(const HostStir &h) {
   return s;
 }
 
-template <typename S, int VS, bool MASK, bool FORCE, int NST>
-static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, const CUtensorMap &tEY, void *fout,
+// STORE: the variant that also keeps each fluid cell's Landau solution and force (the
+// gradient's recomputation); the regular kernel is compiled without that store.
+template <typename S, int VS, bool MASK, bool FORCE, int NST, bool STORE>
+static cudaError_t launch_step_k(const CUtensorMap &tin, const CUtensorMap &tG, const CUtensorMap &tEY, void *fout,
                                  const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,
                                  const Stir<typename RealOf<S>::type> &s, unsigned *err, int grid_limit,
-                                 int stir_rows, int *tile_ctr, unsigned seq, bool chained, cudaStream_t stream) {
+                                 int stir_rows, int *tile_ctr, unsigned seq, bool chained, void *macro_out,
+                                 cudaStream_t stream) {
   using TL = Tile<S, VS>;
+  using R = typename RealOf<S>::type;
   constexpr int CPT = sizeof(S) == 8 ? 1 : 2;
   constexpr int NT = NTHREADS / CPT;
-  auto kern = step_kernel<S, VS, MASK, FORCE, CPT, NST>;
+  auto kern = step_kernel<S, VS, MASK, FORCE, CPT, NST, STORE>;
   const int srows = (FORCE && s.nrows > 0 && s.nrows <= TL::MAX_SROWS && stir_rows != 2) ? s.nrows : 0;
   // room to stage the stirring modes of the next step (coefficients, k_x, row ranges)
   const int prep_bytes =
@@ -943,10 +975,27 @@ static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, 
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, srows, tile_ctr, seq, err);
+    return cudaLaunchKernelEx(&cfg, kern, tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, srows, tile_ctr, seq, err,
+                              static_cast<R *>(macro_out));
   }
-  kern<<<workers, NT, smem, stream>>>(tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, srows, tile_ctr, seq, err);
+  kern<<<workers, NT, smem, stream>>>(tin, tG, tEY, (S *)fout, g, p, s, prep_bytes, srows, tile_ctr, seq, err,
+                                      static_cast<R *>(macro_out));
   return cudaGetLastError();
+}
+
+template <typename S, int VS, bool MASK, bool FORCE, int NST>
+static cudaError_t launch_step_v(const CUtensorMap &tin, const CUtensorMap &tG, const CUtensorMap &tEY, void *fout,
+                                 const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,
+                                 const Stir<typename RealOf<S>::type> &s, unsigned *err, int grid_limit,
+                                 int stir_rows, int *tile_ctr, unsigned seq, bool chained, void *macro_out,
+                                 cudaStream_t stream) {
+  if constexpr (sizeof(S) >= 4) {  // the gradient runs on FP32 and FP64 states only
+    if (macro_out)
+      return launch_step_k<S, VS, MASK, FORCE, NST, true>(tin, tG, tEY, fout, g, p, s, err, grid_limit, stir_rows,
+                                                           tile_ctr, seq, chained, macro_out, stream);
+  }
+  return launch_step_k<S, VS, MASK, FORCE, NST, false>(tin, tG, tEY, fout, g, p, s, err, grid_limit, stir_rows,
+                                                        tile_ctr, seq, chained, nullptr, stream);
 }
 
 template <typename S, int NST>
@@ -954,24 +1003,24 @@ static cudaError_t launch_step_n(int vset, const CUtensorMap &mi, const CUtensor
                                  void *fout, const Geometry<typename RealOf<S>::type> &g,
                                  const Physics<typename RealOf<S>::type> &p, const Stir<typename RealOf<S>::type> &s,
                                  bool mask, bool force, unsigned *err, int grid_limit, int stir_rows,
-                                 int *ctr, unsigned seq, bool chained, cudaStream_t stream) {
+                                 int *ctr, unsigned seq, bool chained, void *macro_out, cudaStream_t stream) {
   if (vset == 3) {
     if (force) {
-      if (mask) return launch_step_v<S, 3, true, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
-      return launch_step_v<S, 3, false, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+      if (mask) return launch_step_v<S, 3, true, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
+      return launch_step_v<S, 3, false, true, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
     }
-    if (mask) return launch_step_v<S, 3, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
-    return launch_step_v<S, 3, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+    if (mask) return launch_step_v<S, 3, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
+    return launch_step_v<S, 3, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
   }
-  if (mask) return launch_step_v<S, 2, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
-  return launch_step_v<S, 2, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+  if (mask) return launch_step_v<S, 2, true, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
+  return launch_step_v<S, 2, false, false, NST>(mi, mg, me, fout, g, p, s, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
 }
 
 template <typename S>
 static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, const void *tey, void *fout,
                                  const HostGeom &hg, const HostPhys &hp, const HostStir &hs, unsigned *err,
                                  int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,
-                                 bool chained, cudaStream_t stream) {
+                                 bool chained, void *macro_out, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
   const Geometry<R> g = to_geom<R>(hg);
   Physics<R> p;
@@ -984,8 +1033,8 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, cons
   const CUtensorMap &mi = *(const CUtensorMap *)tin, &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
   const bool mask = hg.nbmask != nullptr, force = hp.has_force != 0;
   if (stages == 1)
-    return launch_step_n<S, 1>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, chained, stream);
-  return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, chained, stream);
+    return launch_step_n<S, 1>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
+  return launch_step_n<S, 2>(vset, mi, mg, me, fout, g, p, s, mask, force, err, grid_limit, stir_rows, ctr, seq, chained, macro_out, stream);
 }
 
 template <typename S, int VS, bool MASK, bool FORCE, int NST>
@@ -1129,9 +1178,9 @@ static cudaError_t launch_stir_prime_t(const HostStir &hs, void *coef_n, void *c
   cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
                                 int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,      \
-                                bool chained, cudaStream_t st) {                                         \
+                                bool chained, void *macro_out, cudaStream_t st) {                        \
     return launch_step_t<S>(vset, tin, tg, tey, fout, g, p, s, err, grid_limit, stages, stir_rows, ctr, seq, \
-                            chained, st);                                                               \
+                            chained, macro_out, st);                                                    \
   }                                                                                                      \
   cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
                                       int srows, double amp, const long long *bstep, bool mask, int stages, \

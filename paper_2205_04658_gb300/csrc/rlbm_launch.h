@@ -79,7 +79,7 @@ struct BatchTables {
   cudaError_t launch_step_##SUF(int vset, const void *tin, const void *tg, const void *tey, void *fout,     \
                                 const HostGeom &g, const HostPhys &p, const HostStir &s, unsigned *err, \
                                 int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,      \
-                                bool chained, cudaStream_t st);                                          \
+                                bool chained, void *macro_out, cudaStream_t st);                         \
   cudaError_t launch_ghosts_##SUF(int vset, void *f, const HostGeom &g, cudaStream_t st);               \
   cudaError_t launch_batch_step_##SUF(int vset, const BatchTables &bt, const HostGeom &w, const HostPhys &p, \
                                       int srows, double amp, const long long *bstep, bool mask, int stages, \
@@ -105,6 +105,8 @@ struct AdjointArgs {
   const void *tB, *tK;     // host CUtensorMap load maps of B and kin (the layout of the state)
   bool chained;            // the launch directly follows the reverse step of step n + 1 on the
                            // stream, and B was written before that step (programmatic launch)
+  const void *macro;       // the step's eps/eps0 - 1, v_x, v_y, F_x, F_y per cell from the forward
+                           // recomputation (5 planes of nx * ny), or NULL
   void *kout;              // kappa_n
   double cj;               // objective weight of the state S_n
   double *acc;             // [blocks][4] FP64 accumulators
