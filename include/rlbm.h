@@ -138,10 +138,6 @@ RLBM_API rlbm_status rlbm_moments(rlbm_ctx *ctx, double *eps, double *ux, double
  * nbins doubles.  Syncs. */
 RLBM_API rlbm_status rlbm_spectrum(rlbm_ctx *ctx, int32_t nbins, double *E);
 
-/* Copy the stored populations out or in (checkpoint / resume).  host: (planes x ny x nx)
- * values of h_i = f*_i / (w_i eps0) - 1 in double, plane order of the library's folded
- * velocity classes (rlbm_num_planes gives the count).  set_state also sets the step
- * counter.  Both sync.  The paper has no counterpart (it records moments only). */
 /* Energy of a band of wave vectors of the current state's velocity field (v = u^i / u^0):
  * (1/2) sum over k2lo <= k_x^2 + k_y^2 < k2hi of |v^(k)|^2 / (nx ny)^2, integer wave-number
  * indices; k2hi <= 0 means no upper bound.  With k2lo = 0 and k2hi = kmin^2 it is the mean
@@ -158,6 +154,10 @@ RLBM_API rlbm_status rlbm_band_energy(rlbm_ctx *ctx, int64_t k2lo, int64_t k2hi,
  * Syncs. */
 RLBM_API rlbm_status rlbm_column_means(rlbm_ctx *ctx, double *jx, double *jy);
 
+/* Copy the stored populations out or in (checkpoint / resume).  host: (planes x ny x nx)
+ * values of h_i = f*_i / (w_i eps0) - 1 in double, plane order of the library's folded
+ * velocity classes (rlbm_num_planes gives the count).  set_state also sets the step
+ * counter.  Both sync.  The paper has no counterpart (it records moments only). */
 RLBM_API rlbm_status rlbm_get_state(rlbm_ctx *ctx, double *host, int64_t *step);
 RLBM_API rlbm_status rlbm_set_state(rlbm_ctx *ctx, const double *host, int64_t step);
 RLBM_API int32_t rlbm_num_planes(const rlbm_ctx *ctx);
@@ -272,7 +272,8 @@ RLBM_API rlbm_status rlbm_set_mode_scale(rlbm_ctx *ctx, const double *sigma, int
  * after rlbm_step(ctx, nsteps)), keeping the post-collision state every `segment` steps
  * (0: ceil(sqrt(nsteps))), then the hand-written adjoint backwards, recomputing each
  * segment from its checkpoint: about 2 sqrt(nsteps) states of memory and one extra
- * forward pass.  It returns J and dJ/dsigma_m (host, rlbm_num_modes values; may be NULL),
+ * forward pass.  The recomputation also keeps, for every step of the segment in hand, the
+ * step's Landau solution and force (5 values per cell), which the reverse steps read.  It returns J and dJ/dsigma_m (host, rlbm_num_modes values; may be NULL),
  * dJ/d(eta/s) (host, 1; may be NULL) and dJ/dF_body (host, 2; may be NULL; zero for the
  * eight-direction set, which has no force term), evaluated at
  * the current sigma, eta/s and body force.  FP64 and FP32 storage only (E_INVAL for the
