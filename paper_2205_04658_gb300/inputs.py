@@ -17,22 +17,52 @@ def shear_wave(nx, ny, amp=0.01):
     return np.ones((ny, nx)), amp * np.sin(2.0 * np.pi * y / ny), np.zeros((ny, nx))
 
 
+def _real_field_from_rows(rows, coef, nx, ny):
+    """The inverse real 2-D DFT (numpy's irfft2 convention) of a half spectrum whose only
+    non-zero rows are `rows` (k_y mod N_y) with columns k_x = 0 .. coef.shape[1] - 1:
+        g(x, y) = Re sum_{k_x} h_{k_x} / N_x  C(y, k_x) e^{2 pi i k_x x / N_x},
+        C(y, k_x) = (1 / N_y) sum_rows S(row, k_x) e^{2 pi i row y / N_y},
+    with h = 1 at k_x = 0 and at the Nyquist column, 2 elsewhere.  A product of a
+    (N_y x rows) and a (columns x N_x) factor: no transform of the whole lattice."""
+    y = np.arange(ny, dtype=np.int64)
+    Ey = np.exp(2j * np.pi * (np.outer(y, rows) % ny) / ny) / ny
+    C = Ey @ coef
+    kx = np.arange(coef.shape[1], dtype=np.int64)
+    h = np.where((kx == 0) | ((nx % 2 == 0) & (kx == nx // 2)), 1.0, 2.0) / nx
+    ang = 2.0 * np.pi * (np.outer(kx, np.arange(nx, dtype=np.int64)) % nx) / nx
+    Cr, Ci = np.ascontiguousarray(C.real), np.ascontiguousarray(C.imag)  # BLAS wants contiguous factors
+    g = Cr @ (h[:, None] * np.cos(ang))
+    g -= Ci @ (h[:, None] * np.sin(ang))
+    return g
+
+
 def smooth_random_fields(nx, ny, seed, eps_amp=0.05, u_amp=0.05, kmax=4):
     """eps = 1 + eps_amp * g1, u^x = u_amp * g2, u^y = u_amp * g3, where each g is a real
     periodic field with Gaussian random Fourier coefficients on the wave numbers
-    |k_x|, |k_y| <= kmax (k != 0), normalised to unit maximum modulus."""
+    |k_x|, |k_y| <= kmax (k != 0), normalised to unit maximum modulus.  Each g is the
+    inverse real DFT of its half spectrum (k_y taken mod N_y; a later draw replaces an
+    earlier one at the same index), evaluated from the non-zero rows only."""
     rng = np.random.default_rng(seed)
+    ncols = min(kmax + 1, nx // 2 + 1)
     out = []
     for _ in range(3):
-        S = np.zeros((ny, nx // 2 + 1), dtype=np.complex128)
+        spec = {}
         for ky in range(-kmax, kmax + 1):
             for kx in range(0, kmax + 1):
                 if kx == 0 and ky <= 0:
                     continue
-                S[ky % ny, kx] = rng.standard_normal() + 1j * rng.standard_normal()
-        g = np.fft.irfft2(S, s=(ny, nx))
-        out.append(g / np.abs(g).max())
-    return 1.0 + eps_amp * out[0], u_amp * out[1], u_amp * out[2]
+                v = rng.standard_normal() + 1j * rng.standard_normal()
+                spec.setdefault(ky % ny, np.zeros(ncols, dtype=np.complex128))[kx] = v
+        rows = np.array(sorted(spec), dtype=np.int64)
+        g = _real_field_from_rows(rows, np.array([spec[r] for r in rows]), nx, ny)
+        g /= max(g.max(), -g.min())
+        out.append(g)
+    eps, ux, uy = out
+    eps *= eps_amp
+    eps += 1.0
+    ux *= u_amp
+    uy *= u_amp
+    return eps, ux, uy
 
 
 def disc_mask(nx, ny, radius, fraction, seed, walls_y=True, max_trials=1_000_000):

@@ -228,6 +228,15 @@ def test_maximum_size_4096_fp32_sampled(R):
     _sampled_check(R, 4096, 4096, 2, "f32", 12, 2)
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_maximum_width_ragged_height_sampled(R, precision):
+    """The largest lattice width the library accepts (32768) with a height that leaves a
+    partial last tile row (4100 = 512 x 8 + 4): 17 planes of about 32768 x 4102 padded
+    cells put the later planes at element offsets beyond 2^31, so every index on the
+    path has to be 64-bit.  Sampled cells include the four corners."""
+    _sampled_check(R, 32768, 4100, 2, precision, 12, 3)
+
+
 def test_launch_shapes_give_identical_results(R):
     """The launch shape (pipeline depth, CTA count) and the autotuner change nothing in
     the results: every cell is computed by the same arithmetic wherever it runs."""
