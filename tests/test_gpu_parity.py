@@ -71,6 +71,22 @@ def test_stirred_ragged_lattice(R, precision):
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_smallest_lattices_and_zero_steps(R, precision):
+    """The smallest accepted lattices, narrower than one 32 x 8 tile: 8 x 8 periodic and
+    8 x 13 between walls (one full and one partial tile row), stirred 1 <= |k| <= 3, after
+    0 steps (rlbm_step(0) queues nothing), 1 step and 40 steps."""
+    for nx, ny, walls in ((8, 8, 0), (8, 13, 1)):
+        e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=nx * ny, eps_amp=0.02, u_amp=0.04, kmax=2)
+        cfg = dict(nx=nx, ny=ny, walls_y=walls, eta_over_s=0.05, kmin=1, kmax=3, force_amp=1e-2, seed=6,
+                   init_eps=e, init_ux=ux, init_uy=uy)
+        for n in (0, 1, 40):
+            ref = O.run(cfg, n)
+            gpu = gpu_run(R, cfg, n, precision)
+            ee, ue = errors(gpu, ref)
+            assert ee <= TOL[precision] and ue <= TOL[precision], (nx, ny, n, ee, ue)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_walls_discs_body_force(R, precision):
     nx, ny = 72, 40
     mask, _ = inputs.disc_mask(nx, ny, radius=3, fraction=0.08, seed=31, walls_y=True)
