@@ -187,43 +187,66 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_mlups(nx, ny, rows, steps, kw):
-    """Time the FP64 oracle on a band of `rows` rows of the lattice for `steps` steps."""
+def oracle_mlups(nx, ny, rows, steps, kw, cols=None):
+    """Time the FP64 oracle on a periodic window of `cols` x `rows` cells of the lattice
+    (cols = nx: a band of whole rows) for `steps` steps."""
     import numpy as np
     from oracle import rlbm_oracle as O
+    cols = nx if cols is None else cols
     cfg = dict(nx=nx, ny=ny, **kw)
-    o = O.Oracle(cfg, xs=np.arange(nx), ys=np.arange(rows))
+    o = O.Oracle(cfg, xs=np.arange(cols), ys=np.arange(rows))
     t0 = time.perf_counter()
     o.run(steps)
     dt = time.perf_counter() - t0
-    return nx * rows * steps / dt / 1e6, dt
+    return cols * rows * steps / dt / 1e6, dt
 
 
 def _oracle_band_worker(a):
-    """One host core: the oracle on a periodic band of `rows` rows, `warm` untimed then
-    `steps` timed steps; returns the timed seconds."""
-    nx, ny, rows, steps, kw, warm = a
+    """One host core: the oracle on a periodic window of cols x rows cells, `warm` untimed
+    then `steps` timed steps; returns the timed seconds."""
+    nx, ny, cols, rows, steps, kw, warm = a
     import numpy as np
     from oracle import rlbm_oracle as O
-    o = O.Oracle(dict(nx=nx, ny=ny, **kw), xs=np.arange(nx), ys=np.arange(rows))
+    o = O.Oracle(dict(nx=nx, ny=ny, **kw), xs=np.arange(cols), ys=np.arange(rows))
     o.run(warm)
     t0 = time.perf_counter()
     o.run(steps)
     return time.perf_counter() - t0
 
 
-def oracle_mlups_all_cores(nx, ny, rows, steps, kw, warm=0):
+def oracle_mlups_all_cores(nx, ny, rows, steps, kw, warm=0, cols=None):
     """The oracle as it stands on every host core at once: one process per core (spawned,
-    one BLAS thread each), each on its own band of `rows` rows.  Returns (MLUPS over the
-    slowest process's time, cores, seconds)."""
+    one BLAS thread each), each on its own window of cols x rows cells (cols = nx: a band
+    of whole rows).  Returns (MLUPS over the slowest process's time, cores, seconds)."""
     import multiprocessing as mp
+    cols = nx if cols is None else cols
     n = os.cpu_count() or 1
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
     with mp.get_context("spawn").Pool(n) as pool:
-        times = pool.map(_oracle_band_worker, [(nx, ny, rows, steps, kw, warm)] * n)
+        times = pool.map(_oracle_band_worker, [(nx, ny, cols, rows, steps, kw, warm)] * n)
     t = max(times)
-    return n * nx * rows * steps / t / 1e6, n, t
+    return n * cols * rows * steps / t / 1e6, n, t
+
+
+REFERENCE_SECONDS = 120.0  # host time the reference arm aims at for its warm-up + timed steps
+
+
+def reference_window(nx, ny, nsteps, kw, seconds=REFERENCE_SECONDS):
+    """Window (cols, rows) of the lattice that one host core steps nsteps times in about
+    `seconds`: whole rows (at least 8) while they fit, else a square periodic window, at
+    least 8 x 8, the smallest lattice.  A step of the oracle has a fixed cost besides its
+    per-cell cost, so the window is sized from probes of both."""
+    _, t_band = oracle_mlups(nx, ny, 8, 1, kw)             # 8 whole rows, one step
+    per_step = seconds / max(1, nsteps)
+    if per_step >= t_band:
+        return nx, int(min(ny, 8 * per_step / t_band))
+    _, t_min = oracle_mlups(nx, ny, 8, 2, kw, cols=8)       # fixed cost: an 8 x 8 window
+    t_min /= 2
+    per_cell = max(1e-12, (t_band - t_min) / (8 * nx - 64))
+    side = int((max(0.0, per_step - t_min) / per_cell + 64) ** 0.5)
+    side = max(8, min(side, nx, ny))
+    return side, side
 
 
 def run_reference(args):
@@ -231,17 +254,15 @@ def run_reference(args):
     if rank != 0:
         return
     kw = workload(args, 0)
-    # size the bands so that warm-up + timed steps take about two minutes on every core
-    probe, dtp = oracle_mlups(args.nx, args.ny, 8, 1, kw)
-    per_cell = dtp / (args.nx * 8)
-    rows = int(max(8, min(args.ny, 120.0 / max(1, args.steps + args.warmup) / (per_cell * args.nx))))
-    value, cores, dt = oracle_mlups_all_cores(args.nx, args.ny, rows, args.steps, kw, warm=args.warmup)
-    sample = ("%d host cores, each a %d x %d periodic band of the %dx%d lattice, %d steps after %d warm-up"
-              % (cores, args.nx, rows, args.nx, args.ny, args.steps, args.warmup))
+    # each step a bounded sample: warm-up + timed steps take about two minutes on every core
+    cols, rows = reference_window(args.nx, args.ny, args.steps + args.warmup, kw)
+    value, cores, dt = oracle_mlups_all_cores(args.nx, args.ny, rows, args.steps, kw, warm=args.warmup, cols=cols)
+    sample = ("%d host cores, each a %d x %d periodic window of the %dx%d lattice, %d steps after %d warm-up"
+              % (cores, cols, rows, args.nx, args.ny, args.steps, args.warmup))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args), "lattice": [args.nx, args.ny], "sample_rows": rows},
+            "config": {"workload": workload_name(args), "lattice": [args.nx, args.ny], "sample_window": [cols, rows]},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
