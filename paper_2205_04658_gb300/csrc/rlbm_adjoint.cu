@@ -14,7 +14,10 @@
 // cell's own reversed plane, so it has the form of the forward pull), runs the cell's
 // reverse and writes kappa_n.  Landau matching R(v) = m - T v - (T^00 - m.v) v = 0 is
 // differentiated implicitly: the adjoint w solves (dR/dv)^T w = vbar and the moments
-// receive -(dR/dp)^T w.
+// receive -(dR/dp)^T w.  The recomputed forward of a segment keeps each step's Landau
+// solution (eps - 1, v) and force (F_x, F_y) per cell; the reverse step reads them instead
+// of solving Landau matching and synthesising the stirring force again (the force
+// adjoint's row projections still use the step's tables).
 #include "rlbm_kernels.cuh"
 
 namespace rlbm {
