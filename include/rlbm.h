@@ -29,8 +29,8 @@
  *   - Work is queued on the CUDA stream given to rlbm_init (0 = legacy default
  *     stream).  rlbm_step is asynchronous; rlbm_moments, rlbm_spectrum, rlbm_sync and
  *     rlbm_get_state synchronise that stream and report conditions the kernels
- *     latched in a device error word (RLBM_E_UNSTABLE, RLBM_E_UNPHYSICAL).  After
- *     such an error the context accepts only rlbm_free.
+ *     latched in a device error word (RLBM_E_UNSTABLE, RLBM_E_UNPHYSICAL,
+ *     RLBM_E_TIMEOUT).  After such an error the context accepts only rlbm_free.
  *   - Lattice arrays are row-major with x fastest: index = y * nx + x.
  *   - The workspace is reused by every call on the context; calls on one context
  *     must not overlap from several host threads.
@@ -288,6 +288,14 @@ RLBM_API rlbm_status rlbm_gradient(rlbm_ctx *ctx, int64_t nsteps, int32_t segmen
 
 /* Wait for queued work and report latched device errors. */
 RLBM_API rlbm_status rlbm_sync(rlbm_ctx *ctx);
+
+/* Self-test of the failure path (the paper has no counterpart).  Queues one kernel whose
+ * thread waits on an mbarrier that nothing arrives on, with the bounded wait the step
+ * kernels put on their TMA copies, for max_cycles SM clocks (1 <= max_cycles <= 2^31, about
+ * 1 s at 2 GHz).  The wait runs out and latches the timeout in the context's device error
+ * word, so the next syncing call returns RLBM_E_TIMEOUT and the context then accepts only
+ * rlbm_free.  Nothing faults and nothing is left in flight.  Async. */
+RLBM_API rlbm_status rlbm_wait_selftest(rlbm_ctx *ctx, int64_t max_cycles);
 
 /* Number of steps taken since rlbm_init (or set by rlbm_set_state); -1 if ctx is NULL. */
 RLBM_API int64_t rlbm_current_step(const rlbm_ctx *ctx);

@@ -6,7 +6,9 @@
 // shell sum of |Z|^2: one complex 2-D transform serves both components.  The
 // transform is a mixed-radix Stockham FFT (radices 2-8 in registers, any larger prime
 // factor as a direct DFT stage), rows then a tiled transpose then rows, FP64.
+#include "rlbm_device.cuh"
 #include "rlbm_launch.h"
+#include "rlbm_tma.cuh"
 
 namespace rlbm {
 
@@ -39,6 +41,25 @@ __global__ void counter_inc_kernel(long long *c, int *tile_ctr) {
 // clears the tile counter for the next launch.
 cudaError_t launch_counter_inc(long long *counter, int *tile_ctr, cudaStream_t st) {
   counter_inc_kernel<<<1, 1, 0, st>>>(counter, tile_ctr);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the failure path of the bounded waits: one thread waits on an mbarrier that
+// nothing arrives on, with the bounded wait the step kernels use on their TMA copies; when
+// it runs out after max_cycles SM clocks the timeout is latched in the error word, as a
+// step kernel does.  No copy is in flight, so the thread returns at once.
+// ---------------------------------------------------------------------------
+__global__ void wait_selftest_kernel(unsigned *err, long long max_cycles) {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait_bounded(&bar, 0, max_cycles)) atomicOr(err, ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(unsigned *err, long long max_cycles, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(err, max_cycles);
   return cudaGetLastError();
 }
 

@@ -411,6 +411,11 @@ rlbm_status check_device(rlbm_ctx *c) {
     c->latched = RLBM_E_UNPHYSICAL;
     return c->fail(RLBM_E_UNPHYSICAL, "Landau matching found no timelike eigenvector in some cell");
   }
+  if (w & ERR_TIMEOUT) {
+    c->latched = RLBM_E_TIMEOUT;
+    return c->fail(RLBM_E_TIMEOUT, "a bounded device-side wait expired (a copy did not complete in time); "
+                                   "the results of the queued work are incomplete");
+  }
   return RLBM_OK;
 }
 
@@ -452,6 +457,8 @@ template <typename S> void pack_state(const rlbm_ctx *c, const double *src, uint
 namespace rlbm {
 // Lets the allocation-free entry point (rlbm_noalloc.cu) report through rlbm_last_error(NULL).
 void set_thread_error(const std::string &msg) { g_thread_error = msg; }
+// The bounded-wait self-test kernel (rlbm_aux.cu).
+cudaError_t launch_wait_selftest(unsigned *err, long long max_cycles, cudaStream_t st);
 }  // namespace rlbm
 
 extern "C" {
@@ -830,6 +837,17 @@ rlbm_status rlbm_autotune(rlbm_ctx *c, int32_t reps, double *ms_out) {
   }
   if (ms_out) *ms_out = best / reps;
   return check_device(c);
+}
+
+rlbm_status rlbm_wait_selftest(rlbm_ctx *c, int64_t max_cycles) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (max_cycles < 1 || max_cycles > (int64_t(1) << 31))
+    return c->fail(RLBM_E_INVAL, "max_cycles must lie in [1, 2^31]");
+  Scoped dev(c->device);
+  const cudaError_t e = launch_wait_selftest(c->at<unsigned>(c->L.err), max_cycles, c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, "self-test kernel launch");
+  return RLBM_OK;
 }
 
 rlbm_status rlbm_sync(rlbm_ctx *c) {

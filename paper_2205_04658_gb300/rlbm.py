@@ -78,6 +78,7 @@ def lib():
             "rlbm_gradient_query_workspace": (c_i32, [P, c_i64, c_i32, ctypes.POINTER(c_sz)]),
             "rlbm_gradient": (c_i32, [P, c_i64, c_i32, P, c_sz, dp, dp, dp, dp]),
             "rlbm_sync": (c_i32, [P]),
+            "rlbm_wait_selftest": (c_i32, [P, c_i64]),
             "rlbm_current_step": (c_i64, [P]),
             "rlbm_last_error": (ctypes.c_char_p, [P]),
             "rlbm_free": (None, [P]),
@@ -234,6 +235,11 @@ def rlbm_gradient(ctx, nsteps, segment, dev_workspace, nbytes):
 
 def rlbm_sync(ctx):
     _check(lib().rlbm_sync(ctx), ctx)
+
+
+def rlbm_wait_selftest(ctx, max_cycles):
+    """Queue the bounded-wait self-test: the next syncing call raises RLBM_E_TIMEOUT."""
+    _check(lib().rlbm_wait_selftest(ctx, int(max_cycles)), ctx)
 
 
 def rlbm_current_step(ctx):

@@ -94,6 +94,7 @@ def test_init_rejects_bad_workspace_without_touching_the_gpu():
 def test_null_context_calls_fail_cleanly():
     L = R.lib()
     assert L.rlbm_step(None, 1) == R.RLBM_E_INVAL
+    assert L.rlbm_wait_selftest(None, 1000) == R.RLBM_E_INVAL
     assert L.rlbm_current_step(None) == -1
     assert L.rlbm_num_planes(None) == -1
     L.rlbm_free(None)

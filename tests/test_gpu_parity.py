@@ -218,6 +218,28 @@ def test_unstable_state_is_reported_then_context_is_locked(R):
     lat.close()
 
 
+def test_expired_bounded_wait_is_reported_then_context_is_locked(R):
+    """A bounded device wait that runs out (an mbarrier that nothing arrives on, about 1 ms)
+    is reported as RLBM_E_TIMEOUT by the next syncing call; the context then refuses work,
+    and the device stays usable for a new context."""
+    lat = R.Lattice(64, 32, precision="f32", eta_over_s=0.05, kmin=2, kmax=4, force_amp=1e-3, seed=3)
+    lat.step(3)
+    lat.sync()
+    R.rlbm_wait_selftest(lat.ctx, 2_000_000)
+    with pytest.raises(R.RlbmError) as e:
+        lat.sync()
+    assert e.value.status == R.RLBM_E_TIMEOUT and "wait expired" in str(e.value)
+    with pytest.raises(R.RlbmError) as e:
+        lat.step(1)
+    assert e.value.status == R.RLBM_E_STATE
+    lat.close()
+    fresh = R.Lattice(64, 32, precision="f32", eta_over_s=0.05)
+    fresh.step(3)
+    fresh.sync()
+    assert fresh.current_step == 3
+    fresh.close()
+
+
 def _sampled_check(R, nx, ny, nsteps, precision, npts, seed):
     e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=seed, eps_amp=0.02, u_amp=0.03, kmax=8)
     cfg = dict(nx=nx, ny=ny, eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4, seed=2,
