@@ -99,3 +99,46 @@ def test_null_context_calls_fail_cleanly():
     assert L.rlbm_num_planes(None) == -1
     L.rlbm_free(None)
     assert isinstance(R.rlbm_last_error(None), str)
+
+
+def declared_prototypes():
+    protos = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            for name, args in re.findall(r"RLBM_API\s+[\w\s\*]+?\b(rlbm_\w+)\s*\(([^)]*)\)", src, flags=re.S):
+                args = args.strip()
+                protos[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return protos
+
+
+def test_binding_signatures_match_the_header():
+    """Every declared entry point has a ctypes signature with the header's argument count."""
+    L = R.lib()
+    for name, nargs in declared_prototypes().items():
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == nargs, (name, len(fn.argtypes), nargs)
+
+
+def test_config_struct_layout_matches_the_header(tmp_path):
+    """rlbm_config as ctypes lays out exactly as the C compiler lays out the header's struct."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in R.rlbm_config._fields_]
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "rlbm.h"', "int main(void) {",
+            '  printf("%zu\\n", sizeof(rlbm_config));']
+    prog += ['  printf("%%zu\\n", offsetof(rlbm_config, %s));' % f for f in fields]
+    prog += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(R.rlbm_config)
+    for f, off in zip(fields, vals[1:]):
+        assert getattr(R.rlbm_config, f).offset == off, f
