@@ -142,3 +142,28 @@ def test_config_struct_layout_matches_the_header(tmp_path):
     assert vals[0] == ctypes.sizeof(R.rlbm_config)
     for f, off in zip(fields, vals[1:]):
         assert getattr(R.rlbm_config, f).offset == off, f
+
+
+@pytest.mark.parametrize("vset", [3, 2])
+def test_velocity_classes_fold_the_oracle_set(vset):
+    """The library's folded classes (built by the library on the host) equal the oracle's
+    directions grouped by their in-plane part: summed weights and the common v_z^2."""
+    import numpy as np
+    from oracle import rlbm_oracle as O
+    C = R.rlbm_velocity_classes(vset)
+    v, w = O.velocity_set(vset)
+    groups = {}
+    for vi, wi in zip(v, w):
+        key = (round(vi[0], 12), round(vi[1], 12))
+        vz2 = vi[2] ** 2 if v.shape[1] == 3 else 0.0
+        g = groups.setdefault(key, [0.0, vz2])
+        g[0] += wi
+        assert abs(g[1] - vz2) < 1e-15
+    assert C.shape == (len(groups), 4)
+    seen = set()
+    for vx, vy, vz2, wq in C:
+        key = (round(vx, 12), round(vy, 12))
+        assert key in groups and key not in seen, key
+        seen.add(key)
+        assert abs(groups[key][0] - wq) < 1e-15 and abs(groups[key][1] - vz2) < 1e-15, key
+    assert R.lib().rlbm_velocity_classes(5, None) == -1
