@@ -527,6 +527,18 @@ class Oracle:
             self.step()
         return self
 
+    def crop(self, k=1):
+        """Drop the outer k rings of cells of the window.  After a step, a cell within k
+        cells of the window's edge may have pulled values across the window's own periodic
+        wrap, which the lattice does not have; the cells further in are exact."""
+        if self.cfg["open_x"]:
+            raise ValueError("an open channel is run on the whole lattice width")
+        self.fstar = self.fstar[:, k:-k, k:-k]
+        self.win.X = self.win.X[k:-k, k:-k]
+        self.win.Y = self.win.Y[k:-k, k:-k]
+        self.win.solid = self.win.solid[k:-k, k:-k]
+        return self
+
     def fields(self):
         """eps, u^x, u^y of the current state f_n = stream(f*_n) (zero at solid
         cells) and the totals (sum T^00, sum T^0x, sum T^0y, sum 1/2 |v|^2) over
@@ -552,16 +564,53 @@ def run(cfg, nsteps):
     return E, UX, UY, tot
 
 
-def run_sampled(cfg, nsteps, points):
-    """eps, u^x, u^y after nsteps at the cells `points` [(x, y), ...] of a lattice of
-    any size, each computed on its own periodic window of radius nsteps + 1 (the
-    update's domain of dependence grows by one cell per step)."""
-    r = nsteps + 1
+def window_populations(cfg, fstar, x, y, r):
+    """The populations of the window of radius r around cell (x, y), taken from a state
+    fstar (Q, N_y, N_x) of the whole lattice: x wraps; y wraps unless the lattice has
+    walls, whose ghost rows (and anything beyond them) hold zero, as solid cells do."""
+    c = dict(DEFAULTS)
+    c.update(cfg)
+    nx, ny = c["nx"], c["ny"]
+    xs = np.arange(x - r, x + r + 1) % nx
+    ys = np.arange(y - r, y + r + 1)
+    out = np.zeros((fstar.shape[0], len(ys), len(xs)))
+    if c["walls_y"]:
+        inside = (ys >= 0) & (ys < ny)
+        out[:, inside, :] = fstar[:, ys[inside]][:, :, xs]
+    else:
+        out[:] = fstar[:, ys % ny][:, :, xs]
+    return out
+
+
+def sample_block(cfg, x, y, nsteps, half=0, fstar_window=None, step0=0):
+    """eps, u^x, u^y after nsteps steps of the (2 half + 1) x (2 half + 1) block of cells
+    centred on (x, y), computed on a window of radius nsteps + half + 1 around it (the
+    update's domain of dependence grows by one cell per step).  The window starts from
+    the initial fields of cfg, or from the post-collision populations fstar_window of step
+    step0 (as window_populations returns them); after every step it drops its outer ring,
+    whose cells are no longer exact (Oracle.crop), and ends at radius half + 1: the block
+    and the ring the final stream reads."""
+    r = nsteps + half + 1
+    o = Oracle(cfg, np.arange(x - r, x + r + 1), np.arange(y - r, y + r + 1))
+    if fstar_window is not None:
+        o.fstar = np.array(fstar_window, dtype=np.float64)
+        o.fstar[:, o.win.solid] = 0.0
+        o.step_index = step0
+    for _ in range(nsteps):
+        o.step()
+        o.crop(1)
+    E, UX, UY, _ = o.fields()
+    return E[1:-1, 1:-1], UX[1:-1, 1:-1], UY[1:-1, 1:-1]
+
+
+def run_sampled(cfg, nsteps, points, fstar=None, step0=0):
+    """eps, u^x, u^y after nsteps steps at the cells `points` [(x, y), ...] of a lattice of
+    any size, each computed on its own shrinking window (sample_block with half = 0).
+    With fstar (the post-collision populations (Q, N_y, N_x) of the whole lattice at step
+    step0) the run starts from that state instead of the initial fields."""
     out = []
     for (x, y) in points:
-        xs = np.arange(x - r, x + r + 1)
-        ys = np.arange(y - r, y + r + 1)
-        o = Oracle(cfg, xs, ys).run(nsteps)
-        E, UX, UY, _ = o.fields()
-        out.append((E[r, r], UX[r, r], UY[r, r]))
+        fw = None if fstar is None else window_populations(cfg, fstar, x, y, nsteps + 1)
+        E, UX, UY = sample_block(cfg, x, y, nsteps, 0, fw, step0)
+        out.append((E[0, 0], UX[0, 0], UY[0, 0]))
     return np.array(out)
