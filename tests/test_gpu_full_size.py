@@ -1,0 +1,131 @@
+"""Parity over 200 steps at the workloads' own shapes, at sampled blocks of cells.
+
+Two shapes (Part I and Part II, "Model and Methods"):
+  * the stirred turbulence lattice: 1024 x 1024 periodic, shell 8 <= |k| <= 10 (62
+    modes), amplitude 1e-4, seed 2, eta/s 0.05;
+  * the graphene-like sample: 2048 x 512, x periodic, bounce-back walls in y, uniform body
+    force 1e-6 along x, discs of radius 6 at 15 % area (geometry seed 315), eta/s 0.05.
+
+Each starts from a state the FP64 oracle develops itself: seeded smooth fields at the
+workload's velocity scale (stirred: |u| up to 3e-3 on |k| <= 10; graphene-like: a plug
+flow u^x = 2e-3, the speed the 50 000-step run reaches under its body force, with 5 %
+perturbations) relaxed by 24 oracle steps on the whole lattice.  That state is folded into
+the library's planes and rounded to values FP16, BF16 and FP32 all hold exactly; the
+result is the common start of the oracle and of every storage type.  After 200 more steps
+the oracle evaluates blocks of 9 x 9 cells, each on its own shrinking window: one around
+the corner cell (0, 0) (on the periodic lattice it holds all four corner cells; on the
+channel, the corner at a wall), and three seeded ones (on the channel, one at the top wall
+and one beside a disc).
+
+Bars (velocity error = |u - u_ref| / max |u| of the start; eps relative per cell):
+FP64 1e-10, FP32 1e-5, FP16 1e-3.  BF16 (an 8-bit significand) misses the 1e-3 bar on
+these states; its cases are expected failures at that bar (strict), and the measured
+error is printed."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle_pool as P
+from paper_2205_04658_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+STEPS, HALF, DEV = 200, 4, 24
+TOL = {"f64": 1e-10, "f32": 1e-5, "f16": 1e-3, "bf16": 1e-3}
+BF16_MISS = pytest.mark.xfail(strict=True, raises=AssertionError, reason="BF16 deviation storage misses 1e-3 of max|u| at 200 steps")
+
+
+def _stirred():
+    nx = ny = 1024
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=21, eps_amp=1e-3, u_amp=3e-3, kmax=10)
+    phys = dict(eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4, seed=2)
+    rng = np.random.default_rng(22)
+    centres = [(0, 0)] + [(int(rng.integers(nx)), int(rng.integers(ny))) for _ in range(3)]
+    return nx, ny, phys, dict(init_eps=e, init_ux=ux, init_uy=uy), centres
+
+
+def _graphene():
+    nx, ny = 2048, 512
+    mask, discs = inputs.disc_mask(nx, ny, radius=6, fraction=0.15, seed=315, walls_y=True)
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=31, eps_amp=1e-4, u_amp=1e-4, kmax=6)
+    ux += 2e-3
+    phys = dict(walls_y=1, solid=mask, body_force=(1e-6, 0.0), eta_over_s=0.05)
+    cx, cy = discs[len(discs) // 2]
+    rng = np.random.default_rng(32)
+    centres = [(0, 0), (nx - 1, ny - 1), ((cx + 8) % nx, cy), (int(rng.integers(nx)), int(rng.integers(ny)))]
+    return nx, ny, phys, dict(init_eps=e, init_ux=ux, init_uy=uy), centres
+
+
+SHAPES = {"stirred1024": _stirred, "graphene2048x512": _graphene}
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_04658_gb300 import build as B
+    from paper_2205_04658_gb300 import rlbm
+    if not os.path.exists(rlbm.LIB_PATH):
+        B.build()
+    return rlbm
+
+
+@pytest.fixture(scope="module")
+def work(R):
+    """The common starts and the oracle's blocks of both shapes (all oracle work runs in
+    parallel on the host cores)."""
+    shapes = {k: f() for k, f in SHAPES.items()}
+    dev = {k: P.develop_async(dict(nx=s[0], ny=s[1], **s[2], **s[3]), DEV) for k, s in shapes.items()}
+    out = {}
+    pending = {}
+    for k, (nx, ny, phys, _, centres) in shapes.items():
+        f, E, UX, UY = P.assemble(dev[k].get(), ny)
+        h = P.common_start(P.fold(R, f))
+        del f
+        start = P.unfold(R, h)
+        fluid = E > 0.0
+        umax = max(np.abs(UX[fluid]).max(), np.abs(UY[fluid]).max())
+        cfg = dict(nx=nx, ny=ny, **phys)
+        pending[k] = P.blocks_async(cfg, STEPS, centres, HALF, fstar=start, step0=DEV)
+        out[k] = dict(nx=nx, ny=ny, phys=phys, centres=centres, h=h, umax=umax)
+        del start
+    for k in shapes:
+        out[k]["blocks"] = pending[k].get()
+    yield out
+    P.close()
+
+
+def _compare(R, w, precision):
+    nx, ny, phys = w["nx"], w["ny"], w["phys"]
+    lat = R.Lattice(nx, ny, precision=precision, **phys)
+    lat.set_state(w["h"], DEV)
+    lat.step(STEPS)
+    E, UX, UY, _ = lat.moments()
+    assert lat.current_step == DEV + STEPS
+    lat.close()
+    e_err = u_err = 0.0
+    ncells = 0
+    for c, (Eb, UXb, UYb) in zip(w["centres"], w["blocks"]):
+        for j, row in enumerate(P.block_cells(c, HALF, nx, ny, phys.get("walls_y", 0))):
+            for i, cell in enumerate(row):
+                if cell is None or Eb[j, i] == 0.0:  # beyond a wall, or a solid cell
+                    assert cell is None or E[cell] == 0.0
+                    continue
+                ncells += 1
+                e_err = max(e_err, abs(E[cell] - Eb[j, i]) / Eb[j, i])
+                u_err = max(u_err, abs(UX[cell] - UXb[j, i]), abs(UY[cell] - UYb[j, i]))
+    return e_err, u_err / w["umax"], ncells
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16", pytest.param("bf16", marks=BF16_MISS)])
+@pytest.mark.parametrize("shape", list(SHAPES))
+def test_200_steps_from_oracle_developed_start(R, work, shape, precision):
+    w = work[shape]
+    e_err, u_err, ncells = _compare(R, w, precision)
+    print("%s %s: %d fluid cells, eps error %.2e, velocity error / max|u| %.2e (max|u| %.2e)"
+          % (shape, precision, ncells, e_err, u_err, w["umax"]))
+    assert ncells >= 200
+    assert u_err <= TOL[precision], (u_err, TOL[precision])
+    assert e_err <= TOL[precision], (e_err, TOL[precision])

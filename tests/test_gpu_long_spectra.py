@@ -49,13 +49,17 @@ def ref(R):
     return _mean_spectrum(R, "f32")
 
 
-@pytest.mark.parametrize("precision,bound", [("f16", 0.02), ("bf16", 1.0)])
-def test_time_averaged_inertial_spectrum_within_2_percent(R, ref, precision, bound):
+BF16_MISS = pytest.mark.xfail(strict=True, raises=AssertionError,
+                              reason="BF16 deviation storage misses the 2 % bar on the time-averaged spectrum")
+
+
+@pytest.mark.parametrize("precision", ["f16", pytest.param("bf16", marks=BF16_MISS)])
+def test_time_averaged_inertial_spectrum_within_2_percent(R, ref, precision):
     got = _mean_spectrum(R, precision)
     rel = np.abs(got[2:8] / ref[2:8] - 1.0)
     print("%s: mean E(n), n = 2..7, relative to FP32: %s" % (precision, np.array2string(rel, precision=4)))
     assert np.all(ref[2:8] > 0.0)
-    assert rel.max() <= bound
+    assert rel.max() <= 0.02
 
 
 def test_long_run_analysis_pipeline(R):

@@ -1,21 +1,31 @@
 """Accuracy of the 16-bit deviation storage (FP16 / BF16, relaxed in FP32) against the
 FP64 oracle over 200-step slices, as the velocity error relative to max |u|:
 
-  (i)  the decaying shear wave (64 x 64, u = 0.01) from its initial state;
-  (ii) a stirred flow developed for 400 steps by the oracle, quantised once to FP16 and
-       used as the common start of both runs.
+  (i)   the decaying shear wave (64 x 64, u = 0.01) from its initial state;
+  (ii)  a stirred flow developed for 400 steps by the oracle;
+  (iii) the graphene-like shape at reduced size (walls, discs, body force), a plug flow
+        with perturbations relaxed for 40 steps by the oracle.
 
-FP16 with stochastic rounding meets 1e-3; BF16 (8-bit mantissa) does not, and its
-measured error is asserted against a looser bound so that it stays reported."""
+In (ii) and (iii) the oracle's state is folded into the library's planes and rounded once
+to values both 16-bit types hold exactly: the common start of both runs.
+
+FP16 with stochastic rounding meets 1e-3.  BF16 (an 8-bit significand) does not: its
+cases are expected failures at the same 1e-3 bar (strict, so a pass would be reported),
+and the measured error is printed."""
 import os
 
 import numpy as np
 import pytest
 
+import oracle_pool as P
 from oracle import rlbm_oracle as O
 from paper_2205_04658_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+BAR = 1e-3
+BF16_MISS = pytest.mark.xfail(strict=True, raises=AssertionError, reason="BF16 deviation storage misses 1e-3 of max|u| at 200 steps")
+PRECISIONS = ["f16", pytest.param("bf16", marks=BF16_MISS)]
 
 
 @pytest.fixture(scope="module")
@@ -35,36 +45,8 @@ def u_error(gpu, ref):
     return max(np.abs(gpu[1] - ref[1]).max(), np.abs(gpu[2] - ref[2]).max()) / umax
 
 
-def class_map(R, v):
-    """Index of the library's folded class of each of the oracle's 26 directions,
-    matched on (v_x, v_y, v_z^2)."""
-    C = R.rlbm_velocity_classes(3)
-    idx = np.empty(len(v), dtype=int)
-    for i, d in enumerate(v):
-        key = np.array([d[0], d[1], d[2] ** 2])
-        j = np.argmin(np.abs(C[:, :3] - key).sum(axis=1))
-        assert np.abs(C[j, :3] - key).sum() < 1e-12
-        idx[i] = j
-    return idx, C
-
-
-def fold(R, o):
-    """Oracle populations f*_i (26 directions) -> library planes h_q = f_q / (w_q eps0) - 1."""
-    idx, C = class_map(R, o.v)
-    f = np.zeros((len(C),) + o.fstar.shape[1:])
-    for i, q in enumerate(idx):
-        f[q] += o.fstar[i]
-    return f / C[:, 3][:, None, None] - 1.0
-
-
-def unfold(R, o, h):
-    idx, C = class_map(R, o.v)
-    fq = (1.0 + h) * C[:, 3][:, None, None]
-    return np.stack([fq[q] * (o.w[i] / C[q, 3]) for i, q in enumerate(idx)])
-
-
-@pytest.mark.parametrize("precision,bound", [("f16", 1e-3), ("bf16", 1e-2)])
-def test_shear_wave_200_steps(R, precision, bound):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_shear_wave_200_steps(R, precision):
     e, ux, uy = inputs.shear_wave(64, 64, 0.01)
     cfg = dict(nx=64, ny=64, eta_over_s=0.1, init_eps=e, init_ux=ux, init_uy=uy)
     ref = O.run(cfg, 200)
@@ -74,72 +56,68 @@ def test_shear_wave_200_steps(R, precision, bound):
     lat.close()
     err = u_error(gpu, ref)
     print("shear wave %s: u error / max|u| = %.2e" % (precision, err))
-    assert err <= bound
-    assert np.abs(gpu[0] / ref[0] - 1.0).max() <= 1e-3
+    assert np.abs(gpu[0] / ref[0] - 1.0).max() <= BAR
+    assert err <= BAR
 
 
-@pytest.mark.parametrize("precision,bound", [("f16", 1e-3), ("bf16", 1e-2)])
-def test_developed_stirred_slice_200_steps(R, precision, bound):
-    n = 64
-    cfg = dict(nx=n, ny=n, eta_over_s=0.05, kmin=4, kmax=6, force_amp=2e-3, seed=3)
-    dev = O.Oracle(cfg).run(400)
-    h = fold(R, dev)
-    h = h.astype(np.float16).astype(np.float64)  # the common, 16-bit representable start
+def _slice(R, precision, cfg, dev, h, walls):
+    """200 steps of the oracle and of the library in `precision` from the common start h
+    (library planes) at step dev; returns the velocity error and max|u| of the reference."""
+    nx, ny = cfg["nx"], cfg["ny"]
     o = O.Oracle(cfg)
-    o.fstar = unfold(R, o, h)
-    o.step_index = dev.step_index
+    start = P.unfold(R, h)
+    if walls:  # the oracle's whole-domain window carries the wall rows y = -1, ny
+        o.fstar = np.zeros((start.shape[0], ny + 2, nx))
+        o.fstar[:, 1:-1] = start
+    else:
+        o.fstar = start
+    o.fstar[:, o.win.solid] = 0.0
+    o.step_index = dev
     o.run(200)
-    ref = o.fields()
-    lat = R.Lattice(n, n, precision=precision, **{k: v for k, v in cfg.items() if k not in ("nx", "ny")})
-    lat.set_state(h, dev.step_index)
+    E, UX, UY, _ = o.fields()
+    ref = (E[1:-1], UX[1:-1], UY[1:-1]) if walls else (E, UX, UY)
+    lat = R.Lattice(nx, ny, precision=precision, **{k: v for k, v in cfg.items() if k not in ("nx", "ny")})
+    lat.set_state(h, dev)
     lat.step(200)
     gpu = lat.moments()
     lat.close()
-    err = u_error(gpu, ref)
-    print("stirred slice %s: u error / max|u| = %.2e (max|u| = %.2e)" % (precision, err, np.abs(ref[1]).max()))
-    assert err <= bound
-    # the folded FP64 start itself reproduces the oracle closely in FP32 storage
-    if precision == "f16":
+    return u_error(gpu, ref), np.abs(ref[1]).max(), gpu, ref
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_developed_stirred_slice_200_steps(R, precision):
+    n = 64
+    cfg = dict(nx=n, ny=n, eta_over_s=0.05, kmin=4, kmax=6, force_amp=2e-3, seed=3)
+    dev = O.Oracle(cfg).run(400)
+    h = P.common_start(P.fold(R, dev.fstar))
+    err, umax, _, ref = _slice(R, precision, cfg, dev.step_index, h, False)
+    print("stirred slice %s: u error / max|u| = %.2e (max|u| = %.2e)" % (precision, err, umax))
+    if precision == "f16":  # the same start in FP32 storage reproduces the oracle closely
         lat = R.Lattice(n, n, precision="f32", **{k: v for k, v in cfg.items() if k not in ("nx", "ny")})
         lat.set_state(h, dev.step_index)
         lat.step(200)
         assert u_error(lat.moments(), ref) <= 1e-5
         lat.close()
+    assert err <= BAR
 
 
-@pytest.mark.parametrize("precision,bound", [("f16", 1e-3), ("bf16", 1e-2)])
-def test_walls_discs_body_force_slice_200_steps(R, precision, bound):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_walls_discs_body_force_slice_200_steps(R, precision):
     """The graphene-like shape at reduced size: x periodic, bounce-back walls in y, discs
-    of radius 6 at 5 % area, a uniform body force along x; the flow is developed for 1000
-    steps by the FP64 library path (itself checked against the oracle to 1e-10 with walls
-    and discs), quantised to FP16, and the 200-step slice from it is compared with the
-    oracle run from the same start."""
+    of radius 6 at 5 % area, a uniform body force along x.  The start: a plug flow
+    u^x = 7.5e-3 (what the body force 2e-4 builds in 1000 steps) with 5 % perturbations,
+    relaxed for 40 steps by the oracle."""
     nx, ny = 192, 64
     mask, _ = inputs.disc_mask(nx, ny, radius=6, fraction=0.05, seed=35, walls_y=True)
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=36, eps_amp=3e-4, u_amp=3.75e-4, kmax=4)
+    ux += 7.5e-3
     cfg = dict(nx=nx, ny=ny, walls_y=1, solid=mask, body_force=(2e-4, 0.0), eta_over_s=0.05)
-    kw = {k: v for k, v in cfg.items() if k not in ("nx", "ny")}
-    dev = R.Lattice(nx, ny, precision="f64", **kw)
-    dev.step(1000)
-    h, step = dev.get_state()
-    dev.close()
-    h = h.astype(np.float16).astype(np.float64)
-    o = O.Oracle(cfg)
-    hp = np.zeros((h.shape[0], ny + 2, nx))  # the oracle's window carries the wall rows y = -1, ny
-    hp[:, 1:-1] = h
-    o.fstar = unfold(R, o, hp)
-    o.fstar[:, o.win.solid] = 0.0
-    o.step_index = step
-    o.run(200)
-    E, UX, UY, _ = o.fields()
-    ref = (E[1:-1], UX[1:-1], UY[1:-1])
-    lat = R.Lattice(nx, ny, precision=precision, **kw)
-    lat.set_state(h, step)
-    lat.step(200)
-    gpu = lat.moments()
-    lat.close()
-    err = u_error(gpu, ref)
-    print("walls+discs slice %s: u error / max|u| = %.2e (max|u| = %.2e)" % (precision, err, np.abs(ref[1]).max()))
-    assert err <= bound
+    dev = O.Oracle(dict(cfg, init_eps=e, init_ux=ux, init_uy=uy)).run(40)
+    h = P.common_start(P.fold(R, dev.fstar[:, 1:-1]))
+    err, umax, gpu, _ = _slice(R, precision, cfg, dev.step_index, h, True)
+    print("walls+discs slice %s: u error / max|u| = %.2e (max|u| = %.2e)" % (precision, err, umax))
+    assert np.all(gpu[0][mask != 0] == 0.0)
+    assert err <= BAR
 
 
 def test_stochastic_rounding_repeats_exactly(R):
