@@ -192,10 +192,13 @@ RLBM_API rlbm_status rlbm_autotune(rlbm_ctx *ctx, int32_t reps, double *ms_out);
  *
  * Limits: 8 <= nx, ny <= 16384, nx * ny <= 131072 (2^17) cells, 1 <= nbins <= 8200;
  * larger requests return RLBM_E_INVAL with a message in rlbm_last_error(NULL).  The
- * work buffers are one fixed array of about 4.3 MB in the library's own device memory
- * (every GPU that loads the library holds it until the process exits).  The first call
- * on each device looks up that array's device address (cudaGetSymbolAddress), so make
- * the first call on a device before any stream capture.  All calls share the array and
+ * work buffers are one fixed array of 4 784 192 bytes (about 4.8 MB) in the library's own
+ * device memory (every GPU that loads the library holds it until the process exits).  The
+ * first call on each device looks up that array's device address (cudaGetSymbolAddress),
+ * so make the first call on a device before any stream capture; a lookup that fails
+ * returns RLBM_E_CUDA and is tried again by the next call.  A length with a prime factor
+ * p above 8 is transformed by direct sums of length p (O(n p) work per row or column,
+ * spread over the threads of a block): lengths with small prime factors are fastest.  All calls share the array and
  * it keeps the last call's contents (the bins are cleared at the start of each call):
  * calls that overlap on the GPU, from several streams or threads, race and must be
  * serialised by the caller. */

@@ -144,7 +144,8 @@ __device__ __forceinline__ void dft4(double2 v0, double2 v1, double2 v2, double2
 // tw[t] = exp(-2 pi i t / n).  Stage with radix R after radices of product Ns:
 //   v_r = x[j + r n/R] * w^(r (j mod Ns) n/(Ns R)),  y[(j div Ns) Ns R + (j mod Ns) + k Ns] = DFT_R(v)_k.
 // Radices 2, 4 and 8 use their butterflies (8 = two length-4 transforms of the even and
-// odd inputs joined by W_8^k); the others evaluate the length-R sums directly.
+// odd inputs joined by W_8^k); the others evaluate the length-R sums directly (O(n R) work
+// for the stage; a prime factor above 8 shares its outputs over the block's threads).
 __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restrict__ tw,
                                 FftPlan plan) {
   const int n = plan.n;
@@ -155,6 +156,27 @@ __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restric
     const int R = plan.radix[s];
     const int nR = n / R;
     const int stride = n / (Ns * R);
+    if (R > 8) {
+      // a prime factor above 8: direct sums of length R, one output (j, k) per thread, so a
+      // prime length (nR = 1) spreads over the block instead of falling to one thread
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int j = t / R, k = t - j * R;
+        const int jm = j % Ns;
+        const int base = (j / Ns) * Ns * R + jm;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int r = 0; r < R; ++r) {
+          const double2 v = cmul(src[j + r * nR], tw[r * jm * stride]);
+          const double2 e = tw[((r * k) % R) * nR];
+          acc.x += v.x * e.x - v.y * e.y;
+          acc.y += v.x * e.y + v.y * e.x;
+        }
+        dst[base + k * Ns] = acc;
+      }
+      __syncthreads();
+      double2 *tmp = src; src = dst; dst = tmp;
+      Ns *= R;
+      continue;
+    }
     for (int j = threadIdx.x; j < nR; j += blockDim.x) {
       const int jm = j % Ns;
       const int base = (j / Ns) * Ns * R + jm;
@@ -179,7 +201,7 @@ __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restric
             dst[base + (k + 4) * Ns] = csub(E[k], t);
           }
         }
-      } else if (R <= 8) {
+      } else {  // radix 3, 5 or 7: the length-R sums
         double2 v[8];
         for (int r = 0; r < R; ++r) v[r] = cmul(src[j + r * nR], tw[r * jm * stride]);  // r jm stride < n
         for (int k = 0; k < R; ++k) {
@@ -188,17 +210,6 @@ __global__ void fft_rows_kernel(double2 *a, double2 *b, const double2 *__restric
             const int t = ((r * k) % R) * nR;
             acc.x += v[r].x * tw[t].x - v[r].y * tw[t].y;
             acc.y += v[r].x * tw[t].y + v[r].y * tw[t].x;
-          }
-          dst[base + k * Ns] = acc;
-        }
-      } else {
-        for (int k = 0; k < R; ++k) {
-          double2 acc = make_double2(0.0, 0.0);
-          for (int r = 0; r < R; ++r) {
-            const double2 v = cmul(src[j + r * nR], tw[r * jm * stride]);
-            const double2 e = tw[((r * k) % R) * nR];
-            acc.x += v.x * e.x - v.y * e.y;
-            acc.y += v.x * e.y + v.y * e.x;
           }
           dst[base + k * Ns] = acc;
         }

@@ -28,15 +28,33 @@ constexpr size_t kZBytes = sizeof(double2) * kMaxCells;
 constexpr size_t kTwBytes = sizeof(double2) * kMaxDim;
 constexpr size_t kScratchBytes = 2 * kZBytes + 2 * kTwBytes + sizeof(double) * kMaxBins;
 
-// The scratch: two complex work arrays, the twiddles of both directions and the bins.
-// Every GPU that loads the library holds these ~4.3 MB until the process exits.  In host
-// code the name is only a stand-in; its device address comes from cudaGetSymbolAddress.
+// The scratch: two complex work arrays, the twiddles of both directions and the bins,
+// kScratchBytes = 4 784 192 bytes (about 4.8 MB, 4.56 MiB).  Every GPU that loads the
+// library holds it until the process exits.  In host code the name is only a stand-in; its
+// device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+static_assert(kScratchBytes == 4784192, "the size the header states");
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-void *g_ptr[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices];
+std::mutex g_setup_mutex;
+void *g_ptr[kMaxDevices];  // device address of the scratch per device, once looked up
+
+// The scratch's device address on device `dev` (current), looked up on the first call that
+// succeeds: a failed lookup is not kept, so a later call tries again.
+cudaError_t scratch_address(int dev, void **out) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_ptr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();  // clear the error this lookup left, so that it is not reported again later
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
+    g_ptr[dev] = p;
+  }
+  *out = g_ptr[dev];
+  return cudaSuccess;
+}
 
 
 // exp(-2 pi i t / n) for t < n
@@ -69,13 +87,13 @@ extern "C" RLBM_API rlbm_status rlbm_spectrum_noalloc(const double *d_ux, const 
     rlbm::set_thread_error(std::string("no usable current device: ") + cudaGetErrorString(e));
     return RLBM_E_CUDA;
   }
-  // set-up, once per device, with that device current
-  std::call_once(g_once[dev], [dev]() { g_setup_err[dev] = cudaGetSymbolAddress(&g_ptr[dev], g_scratch); });
-  if (g_setup_err[dev] != cudaSuccess || !g_ptr[dev]) {
-    rlbm::set_thread_error(std::string("cudaGetSymbolAddress of the scratch failed: ") + cudaGetErrorString(g_setup_err[dev]));
+  // set-up, once per device, with that device current (retried on the next call if it fails)
+  void *scratch = nullptr;
+  if ((e = scratch_address(dev, &scratch)) != cudaSuccess) {
+    rlbm::set_thread_error(std::string("cudaGetSymbolAddress of the scratch failed: ") + cudaGetErrorString(e));
     return RLBM_E_CUDA;
   }
-  unsigned char *base = static_cast<unsigned char *>(g_ptr[dev]);
+  unsigned char *base = static_cast<unsigned char *>(scratch);
   double2 *z0 = reinterpret_cast<double2 *>(base);
   double2 *z1 = reinterpret_cast<double2 *>(base + kZBytes);
   double2 *twx = reinterpret_cast<double2 *>(base + 2 * kZBytes);

@@ -56,3 +56,35 @@ def test_matches_the_context_spectrum_on_two_calls_in_a_row(R):
         torch.cuda.synchronize()
         got = d_E.cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-10 * ref.max(), call
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny,nbins", [(512, 256, 400), (16384, 8, 8200), (16381, 8, 8200)])
+def test_matches_the_context_spectrum_at_its_limits(R, nx, ny, nbins):
+    """The edges of what the entry point accepts: all 2^17 cells (512 x 256), a row of 16384
+    with every bin up to the top one (|k| = 8192 lands in bin 8192 of 8200), and a prime row
+    length (16381: its transform is one stage of direct sums shared by a block's threads).
+    Each against rlbm_spectrum of a context of the same shape holding the same fields."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=nx + ny, u_amp=0.05, kmax=3)
+    rng = np.random.default_rng(nx)
+    ux = ux + 1e-3 * rng.standard_normal((ny, nx))  # energy in every bin, the top one included
+    uy = uy + 1e-3 * rng.standard_normal((ny, nx))
+    lat = R.Lattice(nx, ny, precision="f64", eta_over_s=0.05, init_eps=e, init_ux=ux, init_uy=uy)
+    _, UX, UY, _ = lat.moments()
+    ref = lat.spectrum(nbins)
+    lat.close()
+    d_ux = torch.from_numpy(UX).cuda()
+    d_uy = torch.from_numpy(UY).cuda()
+    d_E = torch.full((nbins,), -1.0, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        R.rlbm_spectrum_noalloc(d_ux.data_ptr(), d_uy.data_ptr(), nx, ny, nbins, d_E.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        got = d_E.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-10 * ref.max()
+    top = int(round(np.hypot(nx // 2, ny // 2)))
+    assert ref[top] > 0.0 and np.all(ref[top + 1:] == 0.0)
