@@ -18,9 +18,10 @@ channel, the corner at a wall), and three seeded ones (on the channel, one at th
 and one beside a disc).
 
 Bars (velocity error = |u - u_ref| / max |u| of the start; eps relative per cell):
-FP64 1e-10, FP32 1e-5, FP16 1e-3.  BF16 (an 8-bit significand) misses the 1e-3 bar on
-these states; its cases are expected failures at that bar (strict), and the measured
-error is printed."""
+FP64 1e-10, FP32 1e-5, FP16 1e-3.  BF16 is not checked here: its error at a few hundred
+sampled cells (5.8e-4 and 8.8e-4 of max|u| on these two shapes) says nothing about the
+maximum over the lattice, which is what the bar bounds; the full-field slices of
+tests/test_gpu_reduced_precision.py show its miss."""
 import os
 
 import numpy as np
@@ -32,8 +33,7 @@ from paper_2205_04658_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 STEPS, HALF, DEV = 200, 4, 24
-TOL = {"f64": 1e-10, "f32": 1e-5, "f16": 1e-3, "bf16": 1e-3}
-BF16_MISS = pytest.mark.xfail(strict=True, raises=AssertionError, reason="BF16 deviation storage misses 1e-3 of max|u| at 200 steps")
+TOL = {"f64": 1e-10, "f32": 1e-5, "f16": 1e-3}
 
 
 def _stirred():
@@ -119,7 +119,7 @@ def _compare(R, w, precision):
     return e_err, u_err / w["umax"], ncells
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16", pytest.param("bf16", marks=BF16_MISS)])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
 @pytest.mark.parametrize("shape", list(SHAPES))
 def test_200_steps_from_oracle_developed_start(R, work, shape, precision):
     w = work[shape]
