@@ -8,12 +8,18 @@ the next step.  Default workload: 1024 x 1024 periodic lattice, FP32, eps0 = 1 a
 rest, stirring shell 8 <= |k| <= 10 with amplitude 1e-4 redrawn every step, eta/s =
 0.05, dt = 0.05, a = 0.1.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms]
 
 With N > 1 (torchrun), every rank advances its own independently seeded lattice
 (replicas: the update has no cross-lattice exchange), and `value` counts the cell
 updates of all ranks over the slowest rank's time.  L2 is flushed (a 256 MiB write)
 before every timed step; only the step launches are inside the CUDA-event windows.
+
+The line also carries `forms` (rank 0 of a one-GPU run): the same workload as it runs
+(chained 500-step blocks between spectra), a 4096^2 lattice, the graphene-like sample in
+FP16 and FP32, the 64-member ensemble batched in FP16 and BF16 against the plain FP32
+form run member by member, and the time per gradient of the adjoint, each with its
+roofline and its velocity error on a 200-step slice against the FP64 path.
 """
 import argparse
 import hashlib
@@ -32,6 +38,7 @@ METRIC = "MLUPS & HBM GB/s fraction of peak, plain vs mixed/batched at stated er
 ALG_BYTES = {"f64": 272, "f32": 136, "f16": 68, "bf16": 68}  # 2 x 17 planes x storage bytes per cell update
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_step_kernel_stirred1024_f32.txt")
+CHAINED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_step_kernel_stirred1024_f32_chained.txt")
 
 
 def parse():
@@ -46,6 +53,7 @@ def parse():
                    help="storage type (default: f32; f16 for the graphene and ensemble workloads)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the other forms (C2 chained, C2', C3, C4, C5)")
     p.add_argument("--shape", default=None,
                    help="ctas,stages,stir_rows: use this launch shape instead of tuning (profiling runs)")
     p.add_argument("--members", type=int, default=64,
@@ -114,22 +122,28 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def committed_traffic(args):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source and this workload; else None."""
+def traffic_from(path, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
+    step-kernel sources and on `workload`; else None."""
     try:
         kv = {}
-        for line in open(TRAFFIC_FILE):
+        for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
         if kv.get("source_digest") != csrc_digest():
             return None
-        if kv.get("workload") != "%dx%d %s" % (args.nx, args.ny, args.precision):
+        if kv.get("workload") != workload:
             return None
         return float(kv["dram_bytes_per_launch"])
     except Exception:
         return None
+
+
+def committed_traffic(args):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary, if it was
+    taken on the current kernel source and this workload; else None."""
+    return traffic_from(TRAFFIC_FILE, "%dx%d %s" % (args.nx, args.ny, args.precision))
 
 
 class Clocks:
@@ -140,14 +154,14 @@ class Clocks:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device):
-        self.device = device
+        self.device = device  # index or "GPU-<uuid>"
         self.lines = []
         self.proc = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "--id=%d" % self.device, "--query-gpu=" + self.FIELDS,
+                ["nvidia-smi", "--id=%s" % self.device, "--query-gpu=" + self.FIELDS,
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
@@ -185,6 +199,85 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+class NvmlClocks:
+    """The SM clock and the active clock-event reasons of one GPU, read through NVML (the
+    driver's libnvidia-ml) every `period` seconds by a host thread: dense enough to sample a
+    timed region of a few milliseconds.  Only reads; nothing on the GPU changes."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x40: "sw_thermal_slowdown",
+               0x80: "hw_thermal_slowdown", 0x100: "hw_power_brake_slowdown"}
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, uuid=None, index=0, period=0.0005):
+        import ctypes
+        self.period = period
+        self.samples = []
+        self.ok = False
+        self.thread = None
+        try:
+            L = ctypes.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            r = L.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) if uuid else -1
+            if r != 0:
+                r = L.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h))
+            if r != 0:
+                return
+            self.reasons_fn = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                L.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint(0)
+            self.max_mhz = float(mx.value) if L.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0 \
+                and mx.value else None
+            self.L, self.h = L, h
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _run(self):
+        import ctypes
+        c, r = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if self.L.nvmlDeviceGetClockInfo(self.h, self.NVML_CLOCK_SM, ctypes.byref(c)) == 0 and \
+                    self.reasons_fn(self.h, ctypes.byref(r)) == 0:
+                self.samples.append((t, float(c.value), int(r.value)))
+            time.sleep(self.period)
+
+    def start(self):
+        if self.ok:
+            self._stop = threading.Event()
+            self.thread = threading.Thread(target=self._run, daemon=True)
+            self.thread.start()
+
+    def stop(self):
+        if self.thread is not None:
+            self._stop.set()
+            self.thread.join(timeout=5)
+            self.thread = None
+
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, max clock and the reasons seen in the samples taken between host
+        times t0 and t1 (all samples when no window is given or none falls in it)."""
+        return summarise_clock_samples(self.samples, getattr(self, "max_mhz", None), t0, t1, self.period)
+
+
+def summarise_clock_samples(samples, max_mhz, t0=None, t1=None, period=0.0005):
+    """samples: [(host time, SM MHz, NVML clock-event reason bits)]."""
+    inside = [s for s in samples if t0 is not None and t0 <= s[0] <= t1]
+    use = inside or samples
+    if not use:
+        return None
+    reasons = set()
+    for _, _, bits in use:
+        for b, name in NvmlClocks.REASONS.items():
+            if bits & b:
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(s[1] for s in use), "sm_max_mhz": max_mhz, "reasons": sorted(reasons),
+            "samples": len(use), "in_timed_region": bool(inside),
+            "source": "NVML every %.1f ms" % (1e3 * period)}
 
 
 def oracle_mlups(nx, ny, rows, steps, kw, cols=None):
@@ -279,21 +372,301 @@ def tune_flushed(lat, flush, torch, reps=12):
         for stages in (2, 1):
             for ctas in (0, 2 * sms, 3 * sms, 4 * sms):
                 lat.set_launch(ctas, stages, rows)
-                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-                with torch.cuda.stream(lat.stream):
-                    flush.zero_()
-                    lat.step(1)
-                    for a, b in ev:
-                        flush.zero_()
-                        a.record(lat.stream)
-                        lat.step(1)
-                        b.record(lat.stream)
-                torch.cuda.synchronize()
-                t = statistics.median(a.elapsed_time(b) for a, b in ev)
+                t = statistics.median(time_flushed(lat, flush, torch, reps))
                 if best is None or t < best[0]:
                     best = (t, ctas, stages, rows)
     lat.set_launch(best[1], best[2], best[3])
     return {"ctas": best[1], "stages": best[2], "stir_rows": best[3], "ms": best[0]}
+
+
+def time_flushed(lat, flush, torch, steps, warm=1):
+    """Per-step times (ms) of `steps` single-step launches, each after an L2 flush (a write
+    of a buffer larger than L2), CUDA events on the lattice's stream around the launch only."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(lat.stream):
+        for _ in range(warm):
+            flush.zero_()
+            lat.step(1)
+        for a, b in ev:
+            flush.zero_()
+            a.record(lat.stream)
+            lat.step(1)
+            b.record(lat.stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def time_chained(lat, torch, steps):
+    """ms per step of one rlbm_step(steps) call (consecutive launches chained), CUDA events
+    on the lattice's stream around the call."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(lat.stream):
+        a.record(lat.stream)
+        lat.step(steps)
+        b.record(lat.stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def roofline_entry(alg_bytes_per_cell, cells, ms, traffic=None):
+    peak, kind = measured_peak()
+    achieved = alg_bytes_per_cell * cells / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": kind, "alg_bytes_per_cell": alg_bytes_per_cell}
+
+
+def common_16bit(h):
+    """h rounded (to nearest) until FP16, BF16 and FP32 all hold it exactly: a start that
+    every storage type takes without rounding."""
+    import numpy as np
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64))
+    for _ in range(8):
+        y = x.to(torch.float32).to(torch.bfloat16).to(torch.float32).to(torch.float16).to(torch.float64)
+        if torch.equal(x, y):
+            return x.numpy()
+        x = y
+    raise RuntimeError("no common 16-bit representation reached")
+
+
+def slice_errors(rlbm, nx, ny, phys, fields, precisions, dev_steps=24, steps=200, stream=None):
+    """Velocity error of each storage type on a 200-step slice against the FP64 path of the
+    library (pinned to the FP64 oracle at 1e-10 by the parity tests): the FP64 path develops
+    the seeded fields for dev_steps steps, the state is rounded to a common 16-bit start,
+    and every type runs `steps` more steps from it.  Error = max |u - u_64| / max |u_64|
+    (and eps relative per cell) over all cells."""
+    import numpy as np
+    ref = rlbm.Lattice(nx, ny, stream=stream, precision="f64", **phys, **fields)
+    ref.step(dev_steps)
+    h, step = ref.get_state()
+    h = common_16bit(h)
+    ref.set_state(h, step)
+    ref.step(steps)
+    Er, UXr, UYr, _ = ref.moments()
+    ref.close()
+    fluid = Er > 0.0
+    umax = max(np.abs(UXr).max(), np.abs(UYr).max())
+    out = {}
+    for p in precisions:
+        lat = rlbm.Lattice(nx, ny, stream=stream, precision=p, **phys)
+        lat.set_state(h, step)
+        lat.step(steps)
+        E, UX, UY, _ = lat.moments()
+        lat.close()
+        out[p] = {"value": float(max(np.abs(UX - UXr).max(), np.abs(UY - UYr).max()) / umax), "unit": "max|u|",
+                  "eps_rel": float(np.max(np.abs(E[fluid] - Er[fluid]) / Er[fluid])),
+                  "vs": "FP64 library path (parity with the FP64 oracle 1e-10), %dx%d, %d-step slice from a common "
+                        "16-bit start developed %d FP64 steps" % (nx, ny, steps, dev_steps),
+                  "bar": 1e-5 if p == "f32" else 1e-3}
+        out[p]["meets_bar"] = out[p]["value"] <= out[p]["bar"]
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# The forms: each returns a dict with its value, roofline and error
+# --------------------------------------------------------------------------------------
+def stirred_fields(nx, ny, seed):
+    """Seeded smooth fields at the stirred workload's velocity scale (|u| up to 3e-3 on
+    |k| <= 10): the start of its error slices."""
+    from paper_2205_04658_gb300 import inputs
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=seed, eps_amp=1e-3, u_amp=3e-3, kmax=10)
+    return dict(init_eps=e, init_ux=ux, init_uy=uy)
+
+
+def form_stirred_chained(args, torch, rlbm):
+    """The stirred 1024^2 workload as it runs: blocks of 500 chained steps (one rlbm_step
+    call each), an energy spectrum between blocks, outside the event windows.  The state
+    (2 x 71 MB) is near L2's 129 MB, so consecutive steps reuse some of it from L2: the
+    committed ncu summary of chained steps gives the DRAM bytes per step beside it."""
+    nx = ny = 1024
+    lat = rlbm.Lattice(nx, ny, precision="f32", **workload(args, 0))
+    lat.autotune(20)
+    lat.step(50)
+    blocks = []
+    for _ in range(4):
+        blocks.append(time_chained(lat, torch, 500))
+        lat.spectrum(512)
+    lat.close()
+    ms = statistics.median(blocks)
+    return {"value": nx * ny / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "dtype": "f32",
+            "workload": "stirred 1024x1024 FP32, 4 blocks of 500 chained steps (median block), spectrum between",
+            "roofline": roofline_entry(ALG_BYTES["f32"], nx * ny, ms,
+                                       traffic_from(CHAINED_TRAFFIC_FILE, "1024x1024 f32 chained")),
+            "l2": "not flushed between chained steps (the workload's own pattern)"}
+
+
+def form_stirred_4096(args, torch, rlbm):
+    """The stirred workload on 4096^2 (2 x 1.1 GB, far above L2): 200 chained steps."""
+    nx = ny = 4096
+    lat = rlbm.Lattice(nx, ny, precision="f32", **workload(args, 0))
+    lat.autotune(5)
+    lat.step(10)
+    ms = time_chained(lat, torch, 200)
+    lat.close()
+    return {"value": nx * ny / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "dtype": "f32",
+            "workload": "stirred 4096x4096 FP32, 200 chained steps", "l2": "state 2.3 GB > L2, no flush",
+            "roofline": roofline_entry(ALG_BYTES["f32"], nx * ny, ms)}
+
+
+def graphene_setup(frac=0.15, gseed=315):
+    from paper_2205_04658_gb300 import inputs
+    nx, ny = 2048, 512
+    mask, _ = inputs.disc_mask(nx, ny, radius=6, fraction=frac, seed=gseed, walls_y=True)
+    phys = dict(walls_y=1, solid=mask, body_force=(1e-6, 0.0), eta_over_s=0.05)
+    return nx, ny, mask, phys
+
+
+def form_graphene(args, torch, rlbm, flush, prec, steps=40, frac=0.15, gseed=315):
+    """The graphene-like sample (2048 x 512, walls, body force 1e-6, discs r = 6): single
+    steps after an L2 flush (the FP16 state, 2 x 36 MB, fits in L2)."""
+    import numpy as np
+    nx, ny, mask, phys = graphene_setup(frac, gseed)
+    lat = rlbm.Lattice(nx, ny, precision=prec, **phys)
+    lat.autotune(10)
+    times = time_flushed(lat, flush, torch, steps, warm=max(3, args.warmup))
+    lat.close()
+    ms = float(np.mean(times))
+    cells = nx * ny
+    alg = ALG_BYTES[prec] + 2  # populations + the 16-bit neighbour mask
+    return {"value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "dtype": prec,
+            "workload": "graphene-like 2048x512, walls, body force 1e-6, discs r=6 at %d %% (%d fluid cells), %s "
+                        "storage, %d flushed single steps" % (round(100 * frac), int((mask == 0).sum()),
+                                                              prec.upper(), steps),
+            "l2": "flushed before every timed step (256 MiB write)", "roofline": roofline_entry(alg, cells, ms)}
+
+
+def graphene_errors(rlbm, precisions):
+    from paper_2205_04658_gb300 import inputs
+    nx, ny, _, phys = graphene_setup()
+    e, ux, uy = inputs.smooth_random_fields(nx, ny, seed=31, eps_amp=1e-4, u_amp=1e-4, kmax=6)
+    ux = ux + 2e-3  # the plug flow the 50 000-step run reaches under its body force
+    return slice_errors(rlbm, nx, ny, phys, dict(init_eps=e, init_ux=ux, init_uy=uy), precisions)
+
+
+ENSEMBLE_KW = dict(eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4)
+
+
+def form_ensemble(args, torch, rlbm, prec, steps, members=64):
+    """The 64-member ensemble (sides uniform over 256..1024 by seed 4, member seeds 1000 + m)
+    advanced by one persistent launch per step, chunks of steps replayed from CUDA graphs.
+    The state (> 2 GB) is far larger than L2, so no flush is needed between steps."""
+    from paper_2205_04658_gb300 import inputs
+    sides = inputs.ensemble_sides(members, 4)
+    stream = torch.cuda.Stream()
+    lats = [rlbm.Lattice(n, n, stream=stream, precision=prec, seed=1000 + m, **ENSEMBLE_KW) for m, n in enumerate(sides)]
+    cells = sum(n * n for n in sides)
+    batch = rlbm.Batch(lats, stream=stream)
+    tuned_ms = batch.autotune(5)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        batch.step(max(args.warmup, 3))
+        torch.cuda.synchronize()
+        a.record(stream)
+        batch.step(steps)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    for lat in lats:
+        lat.sync()
+    batch.close()
+    for lat in lats:
+        lat.close()
+    mix = "/".join(str(sides.count(v)) + "x" + str(v) for v in (256, 512, 768, 1024))
+    return {"value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "dtype": prec,
+            "workload": "ensemble of %d stirred lattices (%s, %d cells), %s storage, one persistent launch per step, "
+                        "CUDA-graph replay, %d steps" % (len(sides), mix, cells, prec.upper(), steps),
+            "l2": "state %.1f GB > L2, no flush" % (cells * ALG_BYTES[prec] / 1e9), "autotuned_ms": tuned_ms,
+            "roofline": roofline_entry(ALG_BYTES[prec], cells, ms), "cells": cells, "sides": sides}
+
+
+def form_plain_members(args, torch, rlbm, sides, steps=50):
+    """The plain FP32 form run member by member: each distinct side timed alone (chained
+    steps), summed over the members."""
+    stream = torch.cuda.Stream()
+    per_side = {}
+    for n in sorted(set(sides)):
+        lat = rlbm.Lattice(n, n, stream=stream, precision="f32", seed=1000, **ENSEMBLE_KW)
+        lat.autotune(10)
+        lat.step(5)
+        per_side[n] = time_chained(lat, torch, steps)
+        lat.close()
+    ms = sum(per_side[n] for n in sides)
+    cells = sum(n * n for n in sides)
+    return {"value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "dtype": "f32",
+            "workload": "the same %d lattices, plain FP32 step kernel, one lattice at a time (%d chained steps per "
+                        "side)" % (len(sides), steps),
+            "roofline": roofline_entry(ALG_BYTES["f32"], cells, ms),
+            "ms_per_side": {str(k): v for k, v in per_side.items()}}
+
+
+def ensemble_errors(rlbm, precisions):
+    """A 256^2 member of the ensemble's physics (seed 1000) from seeded fields at the stirred
+    velocity scale."""
+    phys = dict(ENSEMBLE_KW, seed=1000)
+    return slice_errors(rlbm, 256, 256, phys, stirred_fields(256, 256, 1000), precisions)
+
+
+def form_adjoint(args, torch, rlbm, nsteps=2000, reps=3):
+    """Time per gradient of J = time-averaged mean |v|^2 / 2 of the 512^2 stirred run (shell
+    4 <= |k| <= 6, 34 modes, amplitude 1e-4, seed 5, eta/s 0.05) with respect to the 34
+    mode multipliers, eta/s and the body force: forward with sqrt(N) checkpoints, segment
+    recomputation and the reverse sweep, all inside the timed call; compared with the
+    forward alone."""
+    nx = ny = 512
+    kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
+    stream = torch.cuda.Stream()
+    lat = rlbm.Lattice(nx, ny, stream=stream, precision="f32", **kw)
+    tuned_ms = lat.autotune(20)
+    nbytes = rlbm.rlbm_gradient_query_workspace(lat.ctx, nsteps, 0)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    ptr = (ws.data_ptr() + 255) // 256 * 256
+    with torch.cuda.stream(stream):
+        rlbm.rlbm_gradient(lat.ctx, nsteps, 0, ptr, nbytes)  # warm-up
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            J, gs, ge, gb = rlbm.rlbm_gradient(lat.ctx, nsteps, 0, ptr, nbytes)  # returns after a stream sync
+            times.append(time.perf_counter() - t0)
+    fwd = [time_chained(lat, torch, nsteps) * nsteps / 1e3 for _ in range(reps)]
+    lat.close()
+    del ws
+    t, tf = statistics.median(times), statistics.median(fwd)
+    return {"value": t, "unit": "s per gradient", "higher_is_better": False, "dtype": "f32",
+            "workload": "gradient of the 512x512 stirred run (shell 4<=|k|<=6, 34 modes, amp 1e-4, seed 5, "
+                        "eta/s 0.05), %d steps, wrt 34 mode multipliers, eta/s, body force" % nsteps,
+            "checkpoint_segment": int(round(nsteps ** 0.5 + 0.4999)), "workspace_bytes": nbytes,
+            "forward_only_s": tf, "gradient_over_forward": t / tf, "gradient_mlups": nx * ny * nsteps / t / 1e6,
+            "J": J, "grad_eta_over_s": ge, "step_launch_tuned_ms": tuned_ms,
+            "error": {"vs": "central finite differences of the FP64 forward, h = 1e-4 (tests/test_gpu_adjoint.py)",
+                      "bar": 1e-4}}
+
+
+def run_forms(args, torch, rlbm, flush):
+    """Every form of the metric on this GPU (a few tens of seconds)."""
+    forms = {}
+    forms["c2_stirred1024_f32_chained"] = form_stirred_chained(args, torch, rlbm)
+    forms["c2prime_stirred4096_f32"] = form_stirred_4096(args, torch, rlbm)
+    errs = graphene_errors(rlbm, ["f32", "f16", "bf16"])
+    for p in ("f16", "f32", "bf16"):
+        forms["c3_graphene2048x512_%s" % p] = dict(form_graphene(args, torch, rlbm, flush, p), error=errs[p])
+    errs = ensemble_errors(rlbm, ["f32", "f16", "bf16"])
+    plain = form_plain_members(args, torch, rlbm, form_sides())
+    plain["error"] = errs["f32"]
+    for p in ("f16", "bf16", "f32"):
+        f = form_ensemble(args, torch, rlbm, p, 100)
+        f.pop("sides")
+        f["speedup_vs_plain_f32_member_by_member"] = plain["ms_per_step"] / f["ms_per_step"]
+        f["error"] = errs[p]
+        forms["c4_ensemble64_%s_batched" % p] = f
+    forms["c4_ensemble64_f32_member_by_member"] = plain
+    forms["c5_adjoint512_f32"] = form_adjoint(args, torch, rlbm)
+    return forms
+
+
+def form_sides():
+    from paper_2205_04658_gb300 import inputs
+    return inputs.ensemble_sides(64, 4)
 
 
 def run_gb300(args):
@@ -312,6 +685,11 @@ def run_gb300(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     rlbm.lib()  # fails loudly when the library is missing
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    uuid = "GPU-%s" % uuid if uuid is not None else None
+    run_clocks = Clocks(uuid or dev)  # nvidia-smi every 200 ms over the whole run
+    run_clocks.start()
+    nvml = NvmlClocks(uuid=uuid, index=dev)  # dense samples around the timed region
 
     def barrier():
         if world > 1:
@@ -331,6 +709,7 @@ def run_gb300(args):
     else:
         tuned_ms = lat.autotune(20)  # launch shape (pipeline depth, CTA count); the state is not advanced
         shape = tune_flushed(lat, flush, torch)  # the same candidates, timed under the timed region's L2 flush
+    nvml.start()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
@@ -338,9 +717,8 @@ def run_gb300(args):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(dev)
-    clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_on = time.perf_counter()
     with torch.cuda.stream(stream):
         for a, b in ev:
             flush.zero_()
@@ -348,10 +726,12 @@ def run_gb300(args):
             lat.step(1)
             b.record(stream)
     torch.cuda.synchronize()
+    t_off = time.perf_counter()
+    nvml.stop()
     barrier()
     torch.cuda.synchronize()
-    clk = clocks.stop()
     lat.sync()
+    clk = nvml.summary(t_on, t_off)
     times = [a.elapsed_time(b) for a, b in ev]
     total_ms = slowest(sum(times), world, "cuda")
     ms_per_step = total_ms / args.steps
@@ -364,7 +744,6 @@ def run_gb300(args):
                 "kernel": "step_kernel (fused stream+collide)", "alg_bytes_per_cell": ALG_BYTES[prec],
                 "autotuned_ms": tuned_ms, "launch_shape": shape}
     lat.close()
-    del flush
 
     # end to end through the C ABI with host buffers, the workload's whole job: initial
     # fields H2D (rlbm_init), launch-shape tuning, 20 000 steps with the energy spectrum read
@@ -405,6 +784,15 @@ def run_gb300(args):
                        "to pinned host every %d steps + rlbm_moments to pinned host" % (job, nbins, every)}
         del ws
 
+    # the error of this form on a 200-step slice of the workload's own shape
+    error = None
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        error = slice_errors(rlbm, nx, ny, dict(kw), stirred_fields(nx, ny, 21), [prec])[prec] \
+            if prec != "f64" else None
+        forms = run_forms(args, torch, rlbm, flush)
+    del flush
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rows, csteps = 512, 3  # about 10 s of oracle work per host core
@@ -417,6 +805,7 @@ def run_gb300(args):
 
     if world > 1:
         dist.barrier()
+    run_clk = run_clocks.stop()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -425,204 +814,59 @@ def run_gb300(args):
                            "l2": "flushed before every timed step (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-                "clocks": clk}
+                "clocks": clk if clk is not None else run_clk, "clocks_whole_run": run_clk,
+                "error": error, "forms": forms}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
+def standalone_line(f, args):
+    """One JSON line of a single form (the --workload runs)."""
+    line = {"metric": METRIC if f.get("unit") == "MLUPS" else "time per gradient (adjoint, sqrt(N) checkpoints)",
+            "value": f["value"], "unit": "MLUPS" if f.get("unit") == "MLUPS" else "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f.get("ms_per_step"),
+            "higher_is_better": f.get("higher_is_better", True), "scaling": "weak", "vs_baseline": None,
+            "dtype": f["dtype"], "data": "synthetic", "config": {"workload": f["workload"], "l2": f.get("l2")}}
+    line.update({k: v for k, v in f.items() if k not in line and k not in ("workload", "l2")})
+    return line
+
+
 def run_ensemble(args):
-    """64 stirred realisations, sides uniform over {256, 512, 768, 1024} (seed 4), member
-    seeds 1000 + m, advanced together (one launch per step, CUDA-graph replay) in the
-    requested storage type; compared with the plain FP32 form stepped member by member.
-    The state (> 2 GB) is far larger than L2, so no flush is needed between steps."""
-    import numpy as np
-    import torch
-    from paper_2205_04658_gb300 import rlbm, inputs
-    torch.cuda.set_device(0)
-    rlbm.lib()
-    sides = inputs.ensemble_sides(args.members, 4)
-    prec = args.precision
-    kw = dict(eta_over_s=0.05, kmin=8, kmax=10, force_amp=1e-4)
-    stream = torch.cuda.Stream()
-    lats = [rlbm.Lattice(n, n, stream=stream, precision=prec, seed=1000 + m, **kw) for m, n in enumerate(sides)]
-    cells = sum(n * n for n in sides)
-    batch = rlbm.Batch(lats, stream=stream)
-    tuned_ms = batch.autotune(5)  # launch shape of the batched kernel; the members are not advanced
-    with torch.cuda.stream(stream):
-        batch.step(args.warmup)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        batch.step(args.steps)
-        b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.steps
-    for lat in lats:
-        lat.sync()
-    batch.close()
-    for lat in lats:
-        lat.close()
-    # plain FP32, one member at a time (one launch per member and step)
-    per_side = {}
-    for n in sorted(set(sides)):
-        lat = rlbm.Lattice(n, n, stream=stream, precision="f32", seed=1000, **kw)
-        lat.autotune(10)
-        with torch.cuda.stream(stream):
-            lat.step(5)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            lat.step(50)
-            b.record(stream)
-        torch.cuda.synchronize()
-        per_side[n] = a.elapsed_time(b) / 50
-        lat.close()
-    ms_plain = sum(per_side[n] for n in sides)
-    value = cells / (ms / 1e3) / 1e6
-    # velocity error of the storage type: a 256^2 member developed for 400 steps in FP64,
-    # then 200 more steps from that (representable) state in both types
-    err = None
-    if prec != "f64":
-        ref = rlbm.Lattice(256, 256, stream=stream, precision="f64", seed=1000, **dict(kw, force_amp=2e-3, kmin=4, kmax=6))
-        ref.step(400)
-        h, step = ref.get_state()
-        h = h.astype({"f32": np.float32, "f16": np.float16, "bf16": np.float32}[prec]).astype(np.float64)
-        if prec == "bf16":
-            h = (np.frombuffer(h.astype(np.float32).tobytes(), np.uint32) & 0xFFFF0000).view(np.float32).reshape(h.shape).astype(np.float64)
-        ref.set_state(h, step)
-        ref.step(200)
-        r = ref.moments()
-        ref.close()
-        lat = rlbm.Lattice(256, 256, stream=stream, precision=prec, seed=1000, **dict(kw, force_amp=2e-3, kmin=4, kmax=6))
-        lat.set_state(h, step)
-        lat.step(200)
-        g = lat.moments()
-        lat.close()
-        umax = max(np.abs(r[1]).max(), np.abs(r[2]).max())
-        err = max(np.abs(g[1] - r[1]).max(), np.abs(g[2] - r[2]).max()) / umax
-    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": "ensemble of %d stirred lattices, sides %s (%d cells), %s storage, "
-                                   "one persistent launch per step, CUDA-graph replay" % (
-                                       len(sides),
-                                       "/".join(str(sides.count(v)) + "x" + str(v) for v in (256, 512, 768, 1024)),
-                                       cells, prec.upper()),
-                       "l2": "state %.1f GB > L2, no flush" % (cells * ALG_BYTES[prec] / 1e9)},
-            "roofline": {"bound": "hbm", "achieved": ALG_BYTES[prec] * cells / (ms / 1e3) / 1e9,
-                         "peak": measured_peak()[0], "unit": "GB/s",
-                         "frac": ALG_BYTES[prec] * cells / (ms / 1e3) / 1e9 / measured_peak()[0]},
-            "plain_f32_member_by_member": {"value": cells / (ms_plain / 1e3) / 1e6, "unit": "MLUPS",
-                                           "ms_per_step": ms_plain},
-            "speedup_vs_plain_f32": ms_plain / ms, "autotuned_ms": tuned_ms,
-            "velocity_error": {"value": err, "vs": "FP64 path, 256x256 developed stirred flow, 200 steps",
-                               "measure": "max |u - u_ref| / max |u_ref|"}}
-    print(json.dumps(line), flush=True)
-
-
-def run_adjoint(args):
-    """Time per gradient of J = time-averaged mean |v|^2 / 2 of the 512^2 stirred run
-    (shell 4 <= |k| <= 6, 34 modes, amplitude 1e-4, seed 5, eta/s 0.05, 2000 steps) with
-    respect to the 34 mode multipliers, eta/s and the body force: forward with sqrt(N)
-    checkpoints, segment recomputation and the reverse sweep, all inside the timed call.
-    Compared with the forward alone (2000 steps)."""
+    """The 64-member ensemble in the requested storage type against the plain FP32 form
+    run member by member, with the velocity error of the storage type on a member slice."""
     import torch
     from paper_2205_04658_gb300 import rlbm
     torch.cuda.set_device(0)
     rlbm.lib()
-    nx = ny = 512
-    N = args.adjoint_steps
-    prec = args.precision
-    kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
-    stream = torch.cuda.Stream()
-    lat = rlbm.Lattice(nx, ny, stream=stream, precision=prec, **kw)
-    # launch shape of the step kernel that the gradient's forward and recomputation use
-    # (timed on the current state, which it does not advance)
-    tuned_ms = lat.autotune(20)
-    nbytes = rlbm.rlbm_gradient_query_workspace(lat.ctx, N, 0)
-    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
-    ptr = (ws.data_ptr() + 255) // 256 * 256
-    for _ in range(max(1, args.warmup // 10)):
-        rlbm.rlbm_gradient(lat.ctx, N, 0, ptr, nbytes)
-    reps = max(1, min(args.steps, 5))
-    times = []
-    for _ in range(reps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        J, gs, ge, gb = rlbm.rlbm_gradient(lat.ctx, N, 0, ptr, nbytes)  # returns after a stream sync
-        times.append(time.perf_counter() - t0)
-    fwd = []
-    for _ in range(reps):
-        with torch.cuda.stream(stream):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            lat.step(N)
-            b.record(stream)
-        torch.cuda.synchronize()
-        fwd.append(a.elapsed_time(b) / 1e3)
-    lat.close()
-    t = statistics.median(times)
-    tf = statistics.median(fwd)
-    line = {"metric": "time per gradient (adjoint, sqrt(N) checkpoints)", "value": t, "unit": "s",
-            "n_gpus": 1, "steps": reps, "warmup": max(1, args.warmup // 10), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": "gradient of the 512x512 stirred run (shell 4<=|k|<=6, 34 modes, amp 1e-4, "
-                                   "seed 5, eta/s 0.05), %d steps, wrt 34 mode multipliers, eta/s, body force" % N,
-                       "checkpoint_segment": int(round(N ** 0.5 + 0.4999)), "workspace_bytes": nbytes,
-                       "step_launch_tuned_ms": tuned_ms},
-            "forward_only_s": tf, "gradient_over_forward": t / tf,
-            "gradient_mlups": nx * ny * N / t / 1e6, "J": J, "grad_eta_over_s": ge}
-    print(json.dumps(line), flush=True)
+    f = form_ensemble(args, torch, rlbm, args.precision, args.steps, args.members)
+    plain = form_plain_members(args, torch, rlbm, f.pop("sides"))
+    f["plain_f32_member_by_member"] = plain
+    f["speedup_vs_plain_f32"] = plain["ms_per_step"] / f["ms_per_step"]
+    if args.precision != "f64":
+        f["error"] = ensemble_errors(rlbm, [args.precision])[args.precision]
+    print(json.dumps(standalone_line(f, args)), flush=True)
+
+
+def run_adjoint(args):
+    import torch
+    from paper_2205_04658_gb300 import rlbm
+    torch.cuda.set_device(0)
+    rlbm.lib()
+    f = form_adjoint(args, torch, rlbm, args.adjoint_steps, max(1, min(args.steps, 5)))
+    print(json.dumps(standalone_line(f, args)), flush=True)
 
 
 def run_graphene(args):
-    """The graphene-like sample: 2048 x 512, x periodic, bounce-back walls in y, uniform
-    body force 1e-6 along x, discs of radius 6 at 1 %, 5 % and 15 % area (geometry seeds
-    31, 35, 315), eta/s 0.05, in the requested storage type (default FP16 with stochastic
-    rounding).  One line per area fraction.  The two population buffers (2 x 71 MB in
-    FP16) fit in L2, so L2 is flushed (a 256 MiB write) before every timed step."""
-    import numpy as np
+    """One line per area fraction (1 %, 5 %, 15 %; geometry seeds 31, 35, 315)."""
     import torch
-    from paper_2205_04658_gb300 import rlbm, inputs
+    from paper_2205_04658_gb300 import rlbm
     torch.cuda.set_device(0)
     rlbm.lib()
-    prec = args.precision
-    nx, ny = 2048, 512
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for frac, gseed in ((0.01, 31), (0.05, 35), (0.15, 315)):
-        mask, _ = inputs.disc_mask(nx, ny, radius=6, fraction=frac, seed=gseed, walls_y=True)
-        lat = rlbm.Lattice(nx, ny, precision=prec, walls_y=1, solid=mask, body_force=(1e-6, 0.0), eta_over_s=0.05)
-        lat.autotune(10)
-        stream = lat.stream
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                flush.zero_()
-                lat.step(1)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-            for a, b in ev:
-                flush.zero_()
-                a.record(stream)
-                lat.step(1)
-                b.record(stream)
-        torch.cuda.synchronize()
-        lat.sync()
-        times = [a.elapsed_time(b) for a, b in ev]
-        lat.close()
-        ms = float(np.mean(times))
-        cells = nx * ny
-        fluid = int((mask == 0).sum())
-        alg = ALG_BYTES[prec] * cells + 2 * cells  # populations + the 16-bit neighbour mask
-        line = {"metric": METRIC, "value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-                "config": {"workload": "graphene-like 2048x512, walls in y, body force 1e-6, discs r=6 at %d %% "
-                                       "(%d fluid cells), %s storage" % (round(100 * frac), fluid, prec.upper()),
-                           "l2": "flushed before every timed step (256 MiB write)"},
-                "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": measured_peak()[0],
-                             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / measured_peak()[0],
-                             "alg_bytes_per_cell": alg / cells}}
-        print(json.dumps(line), flush=True)
+        f = form_graphene(args, torch, rlbm, flush, args.precision, args.steps, frac, gseed)
+        print(json.dumps(standalone_line(f, args)), flush=True)
 
 
 def run_channel(args):
@@ -645,34 +889,17 @@ def run_channel(args):
         lat = rlbm.Lattice(nx, ny, precision=args.precision, open_x=1, inflow_ux=w["inflow_ux"], solid=mask,
                            eta_over_s=es, init_ux=np.full((ny, nx), w["inflow_ux"]))
         lat.autotune(10)
-        stream = lat.stream
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                flush.zero_()
-                lat.step(1)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-            for a, b in ev:
-                flush.zero_()
-                a.record(stream)
-                lat.step(1)
-                b.record(stream)
-        torch.cuda.synchronize()
-        times = [a.elapsed_time(b) for a, b in ev]
+        times = time_flushed(lat, flush, torch, args.steps, warm=args.warmup)
         jx, _ = lat.column_means()
         lat.close()
         ms = float(np.mean(times))
         cells = nx * ny
-        alg = ALG_BYTES[args.precision] * cells + 2 * cells
-        line = {"metric": METRIC, "value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": "open channel 1024x256 (Part II sample), inflow 0.1, %d impurit%s of 13 nodes, "
-                                       "eta/s %.4f (Re 6.37)" % (count, "y" if count == 1 else "ies", es),
-                           "l2": "flushed before every timed step (256 MiB write)"},
-                "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": measured_peak()[0],
-                             "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / measured_peak()[0]},
-                "j_outflow": float(jx[-1])}
-        print(json.dumps(line), flush=True)
+        f = {"value": cells / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "dtype": args.precision,
+             "workload": "open channel 1024x256 (Part II sample), inflow 0.1, %d impurit%s of 13 nodes, "
+                         "eta/s %.4f (Re 6.37)" % (count, "y" if count == 1 else "ies", es),
+             "l2": "flushed before every timed step (256 MiB write)",
+             "roofline": roofline_entry(ALG_BYTES[args.precision] + 2, cells, ms), "j_outflow": float(jx[-1])}
+        print(json.dumps(standalone_line(f, args)), flush=True)
 
 
 def main():

@@ -85,3 +85,16 @@ def test_clock_samples_summary(bench):
     assert c.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c.lines = []
     assert c.stop() is None
+
+
+def test_nvml_clock_samples_summary(bench):
+    """Dense NVML samples: the median and the reasons of the samples inside the timed
+    region; all samples when none falls inside."""
+    s = [(0.9, 2070.0, 0), (1.0, 2055.0, 0x4), (1.5, 2070.0, 0x1), (2.5, 1500.0, 0x8)]
+    out = bench.summarise_clock_samples(s, 2070.0, 1.0, 2.0)
+    assert out["sm_mhz"] == 2062.5 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 2
+    assert out["reasons"] == ["sw_power_cap"] and out["in_timed_region"]
+    out = bench.summarise_clock_samples(s, 2070.0, 3.0, 4.0)
+    assert out["samples"] == 4 and not out["in_timed_region"]
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.summarise_clock_samples([], None) is None
