@@ -100,6 +100,18 @@ typedef struct {
                               last one repeats it).  y stays periodic unless walls_y. */
   double inflow_ux;        /* open_x: spatial u^x of the inflow (in units of the particle
                               speed); |inflow_ux| < 1 */
+  /* Strip of a larger lattice (a domain decomposition in y; see rlbm_halo_pack).
+   * strip_ny_total = 0: the context is the whole lattice (the default).  Otherwise it
+   * holds rows strip_y0 .. strip_y0 + ny - 1 of a lattice of strip_ny_total rows whose y
+   * boundary walls_y describes (periodic, or walls below row 0 and above the last row):
+   * the stirring phases and the rounding of 16-bit stores use the lattice's own rows, and
+   * a face of the strip that is not a wall takes its ghost row from the neighbouring
+   * strip (rlbm_halo_unpack).  kmax < min(nx, strip_ny_total) / 2.  Not with open_x. */
+  int32_t strip_y0;        /* first lattice row of the strip, 0 <= strip_y0 < strip_ny_total */
+  int32_t strip_ny_total;  /* rows of the whole lattice, strip_y0 + ny <= strip_ny_total; 0 = off */
+  const uint8_t *strip_solid_halo; /* host, 2 * nx or NULL (= fluid): solid mask of lattice row
+                              strip_y0 - 1, then of row strip_y0 + ny (rows wrap when y is
+                              periodic); ignored at a face that is a wall */
 } rlbm_config;
 
 /* Device bytes the workspace must hold for this configuration (the populations,
@@ -211,6 +223,45 @@ RLBM_API rlbm_status rlbm_spectrum_noalloc(const double *d_ux, const double *d_u
  * Returns the class count (and writes nothing when out is NULL), or -1 for a bad vset.
  * The paper has no counterpart (a layout query). */
 RLBM_API int32_t rlbm_velocity_classes(int32_t vset, double *out);
+
+/* ---- Strips: one lattice decomposed into horizontal strips --------------------------
+ * The update reads, at each cell, only the cell's own populations and those of its eight
+ * neighbours (the streaming pull moves populations by at most one cell, dt/a <= 1; Sec.
+ * "Boltzmann to Lattice Boltzmann", and Sec. "The Standard/Classical LBM", whose collision
+ * is local).  A lattice split into strips of whole rows therefore steps exactly as one
+ * lattice if, before every step, each strip's ghost rows hold its neighbours' boundary
+ * rows: the populations that cross each face, one padded row per crossing plane (6 of
+ * the 17 planes for vset 3, 3 of 8 for vset 2).
+ *
+ * Per step, for strips created with strip_ny_total > 0 (on one device or on several):
+ *   rlbm_halo_pack(strip, 0, buf_lo); rlbm_halo_pack(strip, 1, buf_hi);   every strip
+ *   move buf_lo of each strip to the strip below, buf_hi to the strip above (device
+ *     copies on one GPU, point-to-point sends between GPUs or hosts)
+ *   rlbm_halo_unpack(strip, 0, from_below); rlbm_halo_unpack(strip, 1, from_above);
+ *   rlbm_step(strip, 1)
+ * A face that is a wall (walls_y, at the first or last row of the lattice) is neither
+ * packed for nor unpacked.  Do the exchange once after rlbm_init (before the first step)
+ * and after the last step before rlbm_moments: the moments read the ghost rows too.
+ * rlbm_moments reports the strip's own fields and totals (sum the totals over strips);
+ * rlbm_spectrum, rlbm_band_energy, rlbm_column_means and rlbm_gradient refuse a strip
+ * (RLBM_E_INVAL): they need the whole lattice.  The paper has no counterpart (its runs
+ * were one lattice per process). */
+
+/* Bytes of one face's halo message of a strip context (*bytes = 0 for a whole lattice). */
+RLBM_API rlbm_status rlbm_halo_bytes(const rlbm_ctx *ctx, size_t *bytes);
+
+/* Queue on the context's stream a copy of the strip's boundary row that a neighbour needs
+ * into dev_out (device, rlbm_halo_bytes): face 0 = row 0 (planes moving down, v_y < 0), for
+ * the strip below; face 1 = row ny - 1 (planes moving up), for the strip above.  Padded rows
+ * of the storage type, x ghost columns included.  RLBM_E_INVAL for a whole lattice, a face
+ * other than 0 or 1, or a face that is a wall. */
+RLBM_API rlbm_status rlbm_halo_pack(rlbm_ctx *ctx, int32_t face, void *dev_out);
+
+/* Queue on the context's stream the copy of a neighbour's message dev_in (device, the
+ * neighbour's rlbm_halo_pack output) into this strip's ghost row: face 0 = the row below
+ * row 0 (from the lower strip's face 1), face 1 = the row above row ny - 1 (from the upper
+ * strip's face 0).  Same refusals as rlbm_halo_pack. */
+RLBM_API rlbm_status rlbm_halo_unpack(rlbm_ctx *ctx, int32_t face, const void *dev_in);
 
 /* ---- Batches: many lattices advanced by one persistent launch per step -------------
  * An ensemble (stirred realisations, impurity samples) of uneven sizes steps as one job:

@@ -97,6 +97,28 @@ cudaError_t launch_column_means(const double *ux, const double *uy, int nx, int 
   return cudaGetLastError();
 }
 
+// Halo rows of a strip: block p copies the padded row of plane p between the population
+// buffer and the message buffer, 16 bytes per thread and step (rows start on 128-byte lines
+// of the buffer; the message buffer is 16-byte aligned).
+__global__ void halo_copy_kernel(char *__restrict__ pop, const HaloRows rows, long long row_bytes,
+                                 char *__restrict__ buf, bool pack) {
+  const int p = blockIdx.x;
+  uint4 *a = reinterpret_cast<uint4 *>(pop + rows.off[p]);
+  uint4 *b = reinterpret_cast<uint4 *>(buf + p * row_bytes);
+  const long long n = row_bytes / 16;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    if (pack) b[i] = a[i];
+    else a[i] = b[i];
+  }
+}
+
+cudaError_t launch_halo_copy(char *pop, const HaloRows &rows, long long row_bytes, char *buf, bool pack,
+                             cudaStream_t st) {
+  if (rows.nplanes < 1) return cudaSuccess;
+  halo_copy_kernel<<<rows.nplanes, 256, 0, st>>>(pop, rows, row_bytes, buf, pack);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_partials(const double *partials, long long nblocks, double *totals, cudaStream_t st) {
   reduce_partials_kernel<<<1, 256, 0, st>>>(partials, nblocks, totals);
   return cudaGetLastError();

@@ -58,6 +58,20 @@ Modes shell_modes(int kmin, int kmax) {
 
 bool stirring_on(const rlbm_config &c) { return c.force_amp != 0.0; }
 
+// A strip of a larger lattice (rlbm_config::strip_ny_total > 0); its lattice's row count.
+bool is_strip(const rlbm_config &c) { return c.strip_ny_total > 0; }
+int total_rows(const rlbm_config &c) { return is_strip(c) ? c.strip_ny_total : c.ny; }
+// Faces of a strip whose ghost rows come from a neighbour (bit 0: below row 0, bit 1: above
+// row ny - 1); a face at the first or last row of a lattice with walls is a wall.
+int halo_faces(const rlbm_config &c) {
+  if (!is_strip(c)) return 0;
+  int f = 3;
+  if (c.walls_y && c.strip_y0 == 0) f &= ~1;
+  if (c.walls_y && c.strip_y0 + c.ny == c.strip_ny_total) f &= ~2;
+  return f;
+}
+bool needs_mask(const rlbm_config &c) { return c.solid || c.walls_y || (is_strip(c) && c.strip_solid_halo); }
+
 struct Layout {
   size_t pop[2], nbmask, err, ctr, EY, G[2], coef[2], mode_kx, row_start, mode_scale;
   size_t eps, ux, uy, partials, totals, twx, twy, z0, z1, bins, cols, total;
@@ -86,7 +100,7 @@ Layout make_layout(const rlbm_config &c) {
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1)); return o; };
   L.pop[0] = take(sb * L.Q * L.plane);
   L.pop[1] = take(sb * L.Q * L.plane);
-  L.nbmask = take((c.solid || c.walls_y) ? 2 * ncell : 0);
+  L.nbmask = take(needs_mask(c) ? 2 * ncell : 0);
   L.err = take(16);
   L.ctr = take(16);  // tile counters of the step kernel (two, used by alternate launches)
   L.eyp = (c.ny + 7) / 8 * 8;  // EY rows padded to 8 entries (16-byte TMA strides)
@@ -127,9 +141,16 @@ std::string validate(const rlbm_config *c) {
   if (!(c->eps0 > 0.0) || !std::isfinite(c->eps0)) return "eps0 must be positive and finite";
   if (!std::isfinite(c->body_force[0]) || !std::isfinite(c->body_force[1])) return "body_force must be finite";
   if (!std::isfinite(c->force_amp)) return "force_amp must be finite";
+  if (c->strip_ny_total < 0) return "strip_ny_total must be >= 0 (0: the context is the whole lattice)";
+  if (is_strip(*c)) {
+    if (c->strip_ny_total > (1 << 30)) return "strip_ny_total must not exceed 2^30";
+    if (c->strip_y0 < 0 || (long long)c->strip_y0 + c->ny > c->strip_ny_total)
+      return "a strip needs 0 <= strip_y0 and strip_y0 + ny <= strip_ny_total";
+    if (c->open_x) return "a strip cannot be an open channel";
+  }
   if (stirring_on(*c)) {
     if (c->kmin < 0 || c->kmax < c->kmin) return "the stirring shell needs 0 <= kmin <= kmax";
-    if (2 * c->kmax >= std::min(c->nx, c->ny)) return "kmax must be below min(nx, ny) / 2";
+    if (2 * c->kmax >= std::min(c->nx, total_rows(*c))) return "kmax must be below min(nx, ny) / 2 (ny of the whole lattice)";
     if (shell_modes(c->kmin, c->kmax).kx.empty()) return "the stirring shell holds no wave vector";
   }
   if (c->vset == 2 && (stirring_on(*c) || c->body_force[0] != 0.0 || c->body_force[1] != 0.0))
@@ -186,6 +207,8 @@ struct rlbm_ctx {
   int stages = 2;              // shared-memory pipeline depth of the step kernel (1 or 2)
   int stir_rows = 1;           // stirring rows: 1 = staged with each tile, 2 = read from global memory
   unsigned launch_seq = 0;     // step-kernel launches so far (selects the tile counter)
+  int halo_faces = 0;          // a strip: faces whose ghost rows come from neighbours (bit 0 below, 1 above)
+  int halo_pending = 0;        // faces not unpacked since the last step, set_state or init
   CUtensorMap tmap_in[2], tmap_G[2], tmap_EY;
   std::vector<uint8_t> host_stage;
 
@@ -496,6 +519,8 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   if (!c) { g_thread_error = "host allocation failed"; return RLBM_E_NOMEM; }
   c->cfg = *cfg;
   c->cfg.solid = nullptr; c->cfg.init_eps = c->cfg.init_ux = c->cfg.init_uy = nullptr;
+  c->cfg.strip_solid_halo = nullptr;
+  c->halo_faces = c->halo_pending = halo_faces(*cfg);
   c->L = L;
   c->ws = static_cast<char *>(dev_workspace);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -513,7 +538,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   std::memset(c->geom.beta, 0, sizeof(c->geom.beta));
   if (cfg->vset == 3) fill_beta<3>(C, c->geom.beta); else fill_beta<2>(C, c->geom.beta);
   c->geom.nx = cfg->nx; c->geom.ny = cfg->ny; c->geom.pitch = L.pitch; c->geom.plane = L.plane;
-  c->geom.walls = (cfg->walls_y ? WALLS_Y : 0) | (cfg->open_x ? OPEN_X : 0);
+  c->geom.walls = is_strip(*cfg) ? STRIP_Y : (cfg->walls_y ? WALLS_Y : 0) | (cfg->open_x ? OPEN_X : 0);
   c->geom.nbmask = nullptr;
   {
     const std::string tm = make_tensor_maps(c);
@@ -531,6 +556,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   c->phys.has_force = (stirring_on(*cfg) || cfg->body_force[0] != 0.0 || cfg->body_force[1] != 0.0) ? 1 : 0;
   c->phys.stochastic = cfg->rounding == 0 ? 1 : 0;
   c->phys.round_key = (unsigned)(cfg->seed ^ (cfg->seed >> 32)) ^ 0x5bd1e995u;
+  c->phys.y_off = is_strip(*cfg) ? cfg->strip_y0 : 0;
 
   // Host staging buffers; copies from pageable memory have consumed their source when
   // cudaMemcpyAsync returns, and init synchronises the stream before it returns.
@@ -542,12 +568,20 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
     if (cfg->solid[i] != 0) --c->nfluid;
 
   // solid-neighbour masks: bit 4 = the cell, bit (dy+1)*3+(dx+1) = neighbour (x+dx, y+dy);
-  // rows y = -1 and y = ny are solid when walls_y is set.
-  if (cfg->solid || cfg->walls_y) {
+  // rows y = -1 and y = ny are solid when walls_y is set.  For a strip, a ghost row is solid
+  // at a wall face, and elsewhere as strip_solid_halo says.
+  if (needs_mask(*cfg)) {
     keep.emplace_back(2 * ncell);
     uint16_t *nb = reinterpret_cast<uint16_t *>(keep.back().data());
     const int nx = cfg->nx, ny = cfg->ny;
+    const int faces = halo_faces(*cfg);
     auto solid_at = [&](int x, int y) -> bool {
+      if (is_strip(*cfg) && (y < 0 || y >= ny)) {
+        const int face = y < 0 ? 0 : 1;
+        if (!(faces & (1 << face))) return true;  // a wall
+        x = (x + nx) % nx;
+        return cfg->strip_solid_halo && cfg->strip_solid_halo[(size_t)face * nx + x] != 0;
+      }
       if (y < 0 || y >= ny) {
         if (cfg->walls_y) return true;
         y = (y + ny) % ny;
@@ -573,13 +607,15 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
     const Modes m = shell_modes(cfg->kmin, cfg->kmax);
     // phase rows in the layout of ey_index: per row 2 eyp reals, blocks of 8 lattice rows,
     // entry k of a block = (Re y, Re y+4, Im y, Im y+4) for y = 8 b + k
+    // (the phase of lattice row y0 + y for a strip starting at row y0 of ny_t rows)
     std::vector<double> ey((size_t)L.nrows * 2 * L.eyp, 0.0);
+    const long long y0 = is_strip(*cfg) ? cfg->strip_y0 : 0, nyt = total_rows(*cfg);
     for (int r = 0; r < L.nrows; ++r)
       for (int y = 0; y < cfg->ny; ++y) {
-        const long long j = ((long long)m.row_ky[r] * y) % cfg->ny;
+        const long long j = ((long long)m.row_ky[r] * (y0 + y)) % nyt;
         const size_t i = (size_t)r * 2 * L.eyp + ey_index(y);
-        ey[i] = std::cos(2.0 * M_PI * j / cfg->ny);
-        ey[i + 2] = std::sin(2.0 * M_PI * j / cfg->ny);
+        ey[i] = std::cos(2.0 * M_PI * (double)j / (double)nyt);
+        ey[i + 2] = std::sin(2.0 * M_PI * (double)j / (double)nyt);
       }
     keep.emplace_back();
     if (cfg->precision == RLBM_F64) {
@@ -642,6 +678,11 @@ rlbm_status rlbm_step(rlbm_ctx *c, int64_t nsteps) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
   if (rlbm_status s = usable(c)) return s;
   if (nsteps < 0) return c->fail(RLBM_E_INVAL, "nsteps must be >= 0");
+  if (c->halo_faces && nsteps > 0) {
+    if (nsteps > 1) return c->fail(RLBM_E_INVAL, "a strip steps one step at a time, between halo exchanges");
+    if (c->halo_pending) return c->fail(RLBM_E_STATE, "the strip's ghost rows are not unpacked since its last step");
+    c->halo_pending = c->halo_faces;
+  }
   Scoped dev(c->device);
   for (int64_t i = 0; i < nsteps; ++i) {
     const HostStir s = stir_for_step(c, c->step);
@@ -657,6 +698,7 @@ rlbm_status rlbm_step(rlbm_ctx *c, int64_t nsteps) {
 rlbm_status rlbm_moments(rlbm_ctx *c, double *eps, double *ux, double *uy, double *totals) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
   if (rlbm_status s = usable(c)) return s;
+  if (c->halo_pending) return c->fail(RLBM_E_STATE, "the strip's ghost rows are not unpacked since its last step");
   Scoped dev(c->device);
   const size_t n = (size_t)c->cfg.nx * c->cfg.ny * sizeof(double);
   cudaError_t e = dispatch_moments(c);
@@ -671,6 +713,7 @@ rlbm_status rlbm_moments(rlbm_ctx *c, double *eps, double *ux, double *uy, doubl
 rlbm_status rlbm_spectrum(rlbm_ctx *c, int32_t nbins, double *E) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
   if (rlbm_status s = usable(c)) return s;
+  if (is_strip(c->cfg)) return c->fail(RLBM_E_INVAL, "a strip has no spectrum of its own: it needs the whole lattice");
   if (nbins < 1 || !E) return c->fail(RLBM_E_INVAL, "nbins must be >= 1 and E non-NULL");
   Scoped dev(c->device);
   cudaError_t e = dispatch_moments(c);
@@ -724,6 +767,7 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
   cudaError_t e = cudaMemcpyAsync(c->ws + c->L.pop[c->cur], c->host_stage.data(), bytes, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return c->cuda_fail(e, "copy of the state");
   c->step = step;
+  c->halo_pending = c->halo_faces;
   if ((e = dispatch_ghosts(c, c->cur)) != cudaSuccess) return c->cuda_fail(e, "ghost fill kernel");
   if ((e = dispatch_open_ghosts(c, c->cur)) != cudaSuccess) return c->cuda_fail(e, "open-channel ghost kernel");
   if ((e = stir_prime(c, step)) != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
@@ -733,6 +777,7 @@ rlbm_status rlbm_set_state(rlbm_ctx *c, const double *host, int64_t step) {
 rlbm_status rlbm_band_energy(rlbm_ctx *c, int64_t k2lo, int64_t k2hi, double *E) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
   if (rlbm_status s = usable(c)) return s;
+  if (is_strip(c->cfg)) return c->fail(RLBM_E_INVAL, "a strip has no band energy of its own: it needs the whole lattice");
   if (!E || k2lo < 0) return c->fail(RLBM_E_INVAL, "E must be non-NULL and k2lo >= 0");
   Scoped dev(c->device);
   cudaError_t e = dispatch_moments(c);
@@ -752,6 +797,7 @@ rlbm_status rlbm_band_energy(rlbm_ctx *c, int64_t k2lo, int64_t k2hi, double *E)
 rlbm_status rlbm_column_means(rlbm_ctx *c, double *jx, double *jy) {
   if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
   if (rlbm_status s = usable(c)) return s;
+  if (is_strip(c->cfg)) return c->fail(RLBM_E_INVAL, "a strip has no column means of its own: it needs the whole lattice");
   Scoped dev(c->device);
   cudaError_t e = dispatch_moments(c);
   if (e != cudaSuccess) return c->cuda_fail(e, "moments kernel launch");
@@ -762,6 +808,60 @@ rlbm_status rlbm_column_means(rlbm_ctx *c, double *jx, double *jy) {
   if (jx && (e = cudaMemcpyAsync(jx, d, 8 * (size_t)nx, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of j_x");
   if (jy && (e = cudaMemcpyAsync(jy, d + nx, 8 * (size_t)nx, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return c->cuda_fail(e, "copy of j_y");
   return check_device(c);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The planes that cross a face and the byte offsets of their boundary or ghost rows in the
+// current population buffer.  Moving down (v_y < 0) crosses face 0 from above: the strip
+// below needs row 0's such planes in its ghost row above (unpack face 1), and this strip's
+// ghost row below (unpack face 0) receives the planes moving up.
+HaloRows halo_rows(const rlbm_ctx *c, int face, bool pack) {
+  HaloRows h{};
+  const int Q = c->L.Q;
+  const int want = (face == 0) == pack ? -1 : 1;  // sign of v_y of the planes carried
+  const long long row = pack ? (face == 0 ? 1 : c->cfg.ny) : (face == 0 ? 0 : c->cfg.ny + 1);
+  const long long sb = (long long)store_bytes(c->cfg.precision);
+  for (int q = 0; q < Q; ++q) {
+    const double vy = c->cfg.vset == 3 ? VSet<3>::vy(q) : VSet<2>::vy(q);
+    if ((vy > 1e-12 ? 1 : vy < -1e-12 ? -1 : 0) != want) continue;
+    h.off[h.nplanes++] = sb * ((long long)q * c->L.plane + row * c->L.pitch);
+  }
+  return h;
+}
+
+rlbm_status halo_copy(rlbm_ctx *c, int32_t face, void *dev, bool pack) {
+  if (!c) { g_thread_error = "ctx is NULL"; return RLBM_E_INVAL; }
+  if (rlbm_status s = usable(c)) return s;
+  if (!is_strip(c->cfg)) return c->fail(RLBM_E_INVAL, "the context is a whole lattice, not a strip");
+  if (face != 0 && face != 1) return c->fail(RLBM_E_INVAL, "face must be 0 (below row 0) or 1 (above row ny - 1)");
+  if (!(c->halo_faces & (1 << face))) return c->fail(RLBM_E_INVAL, "that face of the strip is a wall");
+  if (!dev || reinterpret_cast<uintptr_t>(dev) % 16) return c->fail(RLBM_E_INVAL, "the halo buffer must be a 16-byte aligned device pointer");
+  Scoped d(c->device);
+  const HaloRows h = halo_rows(c, face, pack);
+  const long long row_bytes = (long long)store_bytes(c->cfg.precision) * c->L.pitch;
+  cudaError_t e = launch_halo_copy(c->ws + c->L.pop[c->cur], h, row_bytes, static_cast<char *>(dev), pack, c->stream);
+  if (e != cudaSuccess) return c->cuda_fail(e, pack ? "halo pack kernel" : "halo unpack kernel");
+  if (!pack) c->halo_pending &= ~(1 << face);
+  return RLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlbm_status rlbm_halo_bytes(const rlbm_ctx *c, size_t *bytes) {
+  if (!c || !bytes) { g_thread_error = "ctx and bytes must be non-NULL"; return RLBM_E_INVAL; }
+  *bytes = is_strip(c->cfg) ? (size_t)halo_rows(c, 0, true).nplanes * store_bytes(c->cfg.precision) * c->L.pitch : 0;
+  return RLBM_OK;
+}
+
+rlbm_status rlbm_halo_pack(rlbm_ctx *c, int32_t face, void *dev_out) { return halo_copy(c, face, dev_out, true); }
+
+rlbm_status rlbm_halo_unpack(rlbm_ctx *c, int32_t face, const void *dev_in) {
+  return halo_copy(c, face, const_cast<void *>(dev_in), false);
 }
 
 int32_t rlbm_num_planes(const rlbm_ctx *c) { return c ? c->L.Q : -1; }
@@ -972,6 +1072,7 @@ rlbm_status rlbm_batch_init(rlbm_ctx *const *members, int32_t nmembers, void *de
       { g_thread_error = "member " + std::to_string(i) + " differs from member 0 in velocity set, storage type, a, dt, eta/s, eps0, force or rounding"; return RLBM_E_INVAL; }
     if (members[i]->device != members[0]->device) { g_thread_error = "members live on different devices"; return RLBM_E_INVAL; }
     if (members[i]->cfg.open_x) { g_thread_error = "member " + std::to_string(i) + " is an open channel (batches take periodic-x lattices)"; return RLBM_E_INVAL; }
+    if (is_strip(members[i]->cfg)) { g_thread_error = "member " + std::to_string(i) + " is a strip (batches take whole lattices)"; return RLBM_E_INVAL; }
   }
   rlbm_batch *b = new (std::nothrow) rlbm_batch();
   if (!b) { g_thread_error = "host allocation failed"; return RLBM_E_NOMEM; }
@@ -1205,6 +1306,7 @@ std::string grad_check(const rlbm_ctx *c, int64_t nsteps, int32_t segment) {
   if (c->cfg.precision != RLBM_F64 && c->cfg.precision != RLBM_F32)
     return "the adjoint runs on FP64 and FP32 storage (the 16-bit forms round stochastically)";
   if (c->cfg.open_x) return "the adjoint is built for periodic-x lattices (no open-channel boundaries)";
+  if (is_strip(c->cfg)) return "the adjoint runs on a whole lattice, not on a strip";
   if (nsteps < 1) return "nsteps must be >= 1";
   if (segment < 0) return "segment must be >= 0 (0 = ceil(sqrt(nsteps)))";
   return "";

@@ -144,6 +144,7 @@ template <typename R> struct Physics {
   int stochastic;  // 16-bit storage: stochastic rounding
   unsigned round_key;
   unsigned step;   // low 32 bits of the step index (rounding bits)
+  int y_off;       // lattice row of row 0 (a strip of a larger lattice; else 0): rounding bits
 };
 
 // ---------------------------------------------------------------------------

@@ -22,7 +22,7 @@ __device__ __forceinline__ int ghost_col(int x, int nx, int walls) {
   return x == 0 ? nx : (x == nx - 1 ? -1 : INT_MIN);
 }
 __device__ __forceinline__ int ghost_row(int y, int ny, int walls) {
-  return (walls & WALLS_Y) ? INT_MIN : (y == 0 ? ny : (y == ny - 1 ? -1 : INT_MIN));
+  return (walls & (WALLS_Y | STRIP_Y)) ? INT_MIN : (y == 0 ? ny : (y == ny - 1 ? -1 : INT_MIN));
 }
 constexpr long long WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: bounded TMA waits
 
@@ -275,8 +275,8 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
   S sA[Q], sB[Q];
   {
     const bool sr = sizeof(S) == 2 && p.stochastic;
-    uint32_t rA = sr ? cell_hash(x, yA, p.step, p.round_key) : 0u;
-    uint32_t rB = sr ? cell_hash(x, yB, p.step, p.round_key) : 0u;
+    uint32_t rA = sr ? cell_hash(x, yA + p.y_off, p.step, p.round_key) : 0u;
+    uint32_t rB = sr ? cell_hash(x, yB + p.y_off, p.step, p.round_key) : 0u;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       rA = lcg_next(rA);
@@ -848,6 +848,7 @@ __global__ void fill_ghosts_kernel(S *__restrict__ f, const Geometry<typename Re
   S *pl = f + q * g.plane;
   const long long dst = (long long)(gy + 1) * g.pitch + gx + PadLayout<S>::XOFF;
   const bool yghost = gy < 0 || gy >= g.ny;
+  if (yghost && (g.walls & STRIP_Y)) return;  // a strip's ghost rows come from the halo exchange
   if (yghost && (g.walls & WALLS_Y)) { pl[dst] = store_h<S, typename RealOf<S>::type>(0); return; }
   const int sx = (gx + g.nx) % g.nx, sy = (gy + g.ny) % g.ny;
   pl[dst] = pl[(long long)(sy + 1) * g.pitch + sx + PadLayout<S>::XOFF];
@@ -1029,6 +1030,7 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, cons
   p.stochastic = hp.stochastic;
   p.round_key = hp.round_key;
   p.step = (unsigned)(hp.step & 0xffffffffll);
+  p.y_off = hp.y_off;
   const Stir<R> s = to_stir<R>(hs);
   const CUtensorMap &mi = *(const CUtensorMap *)tin, &mg = *(const CUtensorMap *)tg, &me = *(const CUtensorMap *)tey;
   const bool mask = hg.nbmask != nullptr, force = hp.has_force != 0;
@@ -1096,6 +1098,7 @@ static cudaError_t launch_batch_t(int vset, const BatchTables &bt, const HostGeo
   p.stochastic = hp.stochastic;
   p.round_key = 0;
   p.step = 0;
+  p.y_off = 0;
   const bool force = hp.has_force != 0;
   if (stages == 1)
     return launch_batch_n<S, 1>(vset, bt, w, p, srows, amp, bstep, mask, force, grid_limit, ntiles, stream);

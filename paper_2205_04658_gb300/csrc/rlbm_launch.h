@@ -10,8 +10,10 @@ namespace rlbm {
 
 // Boundary flags of a lattice (Geometry::walls): bit 0 = bounce-back walls in y (the ghost
 // rows stay zero), bit 1 = open channel in x (inflow column left of x = 0, written once;
-// zero-gradient outflow right of x = nx - 1).
-constexpr int WALLS_Y = 1, OPEN_X = 2;
+// zero-gradient outflow right of x = nx - 1), bit 2 = a strip of a larger lattice (the
+// ghost rows are written by the halo exchange, never by the kernels; which ghost-row cells
+// are solid is in the neighbour mask).
+constexpr int WALLS_Y = 1, OPEN_X = 2, STRIP_Y = 4;
 
 struct HostGeom {
   int nx, ny, pitch;
@@ -27,6 +29,7 @@ struct HostPhys {
   int stochastic;          // 16-bit storage: stochastic rounding
   unsigned round_key;      // key of the rounding bits
   long long step;          // index n of the step being launched
+  int y_off;               // lattice row of the context's row 0 (a strip of a larger lattice; else 0)
 };
 
 struct HostStir {
@@ -134,6 +137,15 @@ cudaError_t launch_mode_grads_f64(const ModeGradArgs &a, cudaStream_t st);
 cudaError_t launch_mode_grads_f32(const ModeGradArgs &a, cudaStream_t st);
 cudaError_t launch_mode_sum(const double *gstep, long long nsteps, int nmodes, double *gsig, cudaStream_t st);
 cudaError_t launch_adj_twiddles(double2 *tw, float2 *twf, int n, cudaStream_t st);
+
+// Halo rows of a strip (rlbm_aux.cu): nplanes rows of row_bytes each, the plane p's row at
+// byte offset off[p] of the population buffer, to (pack) or from (unpack) buf[p * row_bytes].
+struct HaloRows {
+  int nplanes;
+  long long off[8];
+};
+cudaError_t launch_halo_copy(char *pop, const HaloRows &rows, long long row_bytes, char *buf, bool pack,
+                             cudaStream_t st);
 
 // Reductions and spectrum (rlbm_aux.cu)
 cudaError_t launch_counter_inc(long long *counter, int *tile_ctr, cudaStream_t st);

@@ -36,6 +36,8 @@ class rlbm_config(ctypes.Structure):
         ("init_eps", ctypes.POINTER(ctypes.c_double)), ("init_ux", ctypes.POINTER(ctypes.c_double)),
         ("init_uy", ctypes.POINTER(ctypes.c_double)), ("fp64_landau_vmax", ctypes.c_double),
         ("open_x", ctypes.c_int32), ("inflow_ux", ctypes.c_double),
+        ("strip_y0", ctypes.c_int32), ("strip_ny_total", ctypes.c_int32),
+        ("strip_solid_halo", ctypes.POINTER(ctypes.c_uint8)),
     ]
 
 
@@ -73,6 +75,9 @@ def lib():
             "rlbm_batch_last_error": (ctypes.c_char_p, [P]),
             "rlbm_batch_free": (None, [P]),
             "rlbm_spectrum_noalloc": (c_i32, [P, P, c_i32, c_i32, c_i32, P, P]),
+            "rlbm_halo_bytes": (c_i32, [P, ctypes.POINTER(c_sz)]),
+            "rlbm_halo_pack": (c_i32, [P, c_i32, P]),
+            "rlbm_halo_unpack": (c_i32, [P, c_i32, P]),
             "rlbm_num_modes": (c_i32, [P]),
             "rlbm_set_mode_scale": (c_i32, [P, dp, c_i32]),
             "rlbm_gradient_query_workspace": (c_i32, [P, c_i64, c_i32, ctypes.POINTER(c_sz)]),
@@ -103,15 +108,15 @@ def _dptr(a):
 def make_config(nx, ny, precision="f32", walls_y=0, vset=3, a=0.1, dt=0.05, eta_over_s=0.1, eps0=1.0,
                 body_force=(0.0, 0.0), kmin=0, kmax=0, force_amp=0.0, seed=0, solid=None,
                 init_eps=None, init_ux=None, init_uy=None, fp64_landau_vmax=0.0, rounding="stochastic",
-                open_x=0, inflow_ux=0.0):
+                open_x=0, inflow_ux=0.0, strip_y0=0, strip_ny_total=0, strip_solid_halo=None):
     """An rlbm_config and the host arrays it points to (keep both alive until rlbm_init
     returns)."""
     keep = {}
 
-    def arr(x, dtype, name):
+    def arr(x, dtype, name, rows=ny):
         if x is None:
             return None
-        a_ = np.ascontiguousarray(np.asarray(x, dtype=dtype).reshape(ny, nx))
+        a_ = np.ascontiguousarray(np.asarray(x, dtype=dtype).reshape(rows, nx))
         keep[name] = a_
         return a_.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8 if dtype == np.uint8 else ctypes.c_double))
 
@@ -128,6 +133,8 @@ def make_config(nx, ny, precision="f32", walls_y=0, vset=3, a=0.1, dt=0.05, eta_
     c.init_uy = arr(init_uy, np.float64, "uy")
     c.fp64_landau_vmax = fp64_landau_vmax
     c.open_x, c.inflow_ux = int(open_x), float(inflow_ux)
+    c.strip_y0, c.strip_ny_total = int(strip_y0), int(strip_ny_total)
+    c.strip_solid_halo = arr(strip_solid_halo, np.uint8, "solid_halo", rows=2)
     return c, keep
 
 
@@ -195,6 +202,20 @@ def rlbm_spectrum_noalloc(d_ux, d_uy, nx, ny, nbins, d_E, cuda_stream):
     """Spectrum of device velocity fields (device pointers as integers), allocating nothing."""
     _check(lib().rlbm_spectrum_noalloc(ctypes.c_void_p(d_ux), ctypes.c_void_p(d_uy), int(nx), int(ny), int(nbins),
                                        ctypes.c_void_p(d_E), ctypes.c_void_p(cuda_stream)))
+
+
+def rlbm_halo_bytes(ctx):
+    n = ctypes.c_size_t(0)
+    _check(lib().rlbm_halo_bytes(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def rlbm_halo_pack(ctx, face, dev_out):
+    _check(lib().rlbm_halo_pack(ctx, int(face), ctypes.c_void_p(dev_out)), ctx)
+
+
+def rlbm_halo_unpack(ctx, face, dev_in):
+    _check(lib().rlbm_halo_unpack(ctx, int(face), ctypes.c_void_p(dev_in)), ctx)
 
 
 def rlbm_velocity_classes(vset=3):
