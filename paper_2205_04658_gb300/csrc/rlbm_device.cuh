@@ -593,9 +593,10 @@ __device__ __forceinline__ Macro<R> cell_macro(const R h[VSet<VS>::Q], const Mom
   }
 }
 
-// Landau matching of two cells at once (the Newton steps of `landau` on both lanes, until
-// both have converged); a lane that has not converged, or whose |v|^2 exceeds vmax2, is
-// re-solved in FP64 from the same populations.
+// Landau matching of two cells at once: the Newton steps of `landau` on both lanes, each
+// lane keeping its value from the step at which it converged (so a cell's result does not
+// depend on the cell it is paired with); a lane that has not converged, or whose |v|^2
+// exceeds vmax2, is re-solved in FP64 from the same populations.
 template <int VS>
 __device__ __forceinline__ Macro<F2> cell_macro_pair(const F2 h[VSet<VS>::Q], const Mom<F2> &M, float vmax2) {
   constexpr float dinv = 1.0f / VSet<VS>::DP;
@@ -619,11 +620,11 @@ __device__ __forceinline__ Macro<F2> cell_macro_pair(const F2 h[VSet<VS>::Q], co
     const F2 idet = FM<F2>::rcp(jxx * jyy - jxy * jyx);
     const F2 dx = (jxy * ry - jyy * rx) * idet;
     const F2 dy = (jyx * rx - jxx * ry) * idet;
-    vx += dx;
-    vy += dy;
+    vx += F2(convA ? 0.0f : dx.v.x, convB ? 0.0f : dx.v.y);
+    vy += F2(convA ? 0.0f : dy.v.x, convB ? 0.0f : dy.v.y);
     const F2 d2 = fma(dx, dx, dy * dy), lim = F2(tol * tol) * (F2(1e-6f) + fma(vx, vx, vy * vy));
-    convA = d2.v.x <= lim.v.x;
-    convB = d2.v.y <= lim.v.y;
+    convA = convA || d2.v.x <= lim.v.x;
+    convB = convB || d2.v.y <= lim.v.y;
     if (convA && convB) break;
   }
   const F2 v2 = fma(vx, vx, vy * vy);

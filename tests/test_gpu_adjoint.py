@@ -48,7 +48,10 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 2e-4)])
+# FP32: the forward recomputation and the reverse sweep round every operation to FP32
+# (2^-24); over these 20-24 steps the gradients land 0.5e-6 to 3e-6 from the FP64 oracle's
+# (measured on a GB300), so 1e-5 bounds them with a margin of about three.
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 1e-5)])
 def test_stirred_gradient_matches_oracle_adjoint(R, precision, tol):
     """40 x 36 (ragged against the 32 x 8 tile), shell 2..4, body force, 24 steps, with
     non-unit multipliers."""
@@ -59,12 +62,14 @@ def test_stirred_gradient_matches_oracle_adjoint(R, precision, tol):
     J, gs, ge, gb = _gpu_grad(R, cfg, 24, precision, sigma=sigma)
     assert abs(J - ref["J"]) <= (1e-12 if precision == "f64" else 1e-5) * ref["J"]
     assert gs.shape == (nm,)
+    print("%s: relative error against the oracle adjoint: sigma %.2e, eta/s %.2e, body force %.2e"
+          % (precision, _rel(gs, ref["sigma"]), _rel(ge, ref["eta_over_s"]), _rel(gb, ref["body_force"])))
     assert _rel(gs, ref["sigma"]) <= tol, (gs, ref["sigma"])
     assert _rel(ge, ref["eta_over_s"]) <= tol, (ge, ref["eta_over_s"])
     assert _rel(gb, ref["body_force"]) <= tol, (gb, ref["body_force"])
 
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 1e-5)])
 def test_walls_discs_gradient_matches_oracle_adjoint(R, precision, tol):
     nx, ny = 48, 24
     mask, _ = inputs.disc_mask(nx, ny, radius=2, fraction=0.06, seed=17, walls_y=True)
@@ -74,6 +79,8 @@ def test_walls_discs_gradient_matches_oracle_adjoint(R, precision, tol):
     ref = A.gradient(cfg, 20)
     J, gs, ge, gb = _gpu_grad(R, cfg, 20, precision)
     assert abs(J - ref["J"]) <= (1e-12 if precision == "f64" else 1e-5) * ref["J"]
+    print("%s walls+discs: relative error against the oracle adjoint: eta/s %.2e, body force %.2e"
+          % (precision, _rel(ge, ref["eta_over_s"]), _rel(gb, ref["body_force"])))
     assert _rel(ge, ref["eta_over_s"]) <= tol
     assert _rel(gb, ref["body_force"]) <= tol
 
@@ -167,41 +174,61 @@ def test_autograd_function_gradcheck(R):
     assert sigma.grad.shape == (nm,) and eta.grad.ndim == 0 and body.grad.shape == (2,)
 
 
-def _objective_fp64(R, nx, ny, nsteps, kw, sigma=None):
-    """J of a forward FP64 run through the plain step / totals path (no adjoint code)."""
-    lat = R.Lattice(nx, ny, precision="f64", **kw)
-    if sigma is not None:
-        lat.set_mode_scale(sigma)
-    acc = 0.0
+def _objectives_fp64(R, nx, ny, nsteps, runs):
+    """J of several forward FP64 runs [(kw, sigma), ...] through the plain step / totals path
+    (no adjoint code), stepped in lockstep, each on its own stream so that their kernels
+    overlap on the GPU."""
+    import torch
+    lats = []
+    for kw, sigma in runs:
+        lat = R.Lattice(nx, ny, stream=torch.cuda.Stream(), precision="f64", **kw)
+        if sigma is not None:
+            lat.set_mode_scale(sigma)
+        lats.append(lat)
+    acc = np.zeros(len(lats))
     for _ in range(nsteps):
-        lat.step(1)
-        acc += lat.totals()[3]
-    lat.close()
+        for lat in lats:
+            lat.step(1)
+        for i, lat in enumerate(lats):
+            acc[i] += lat.totals()[3]
+    for lat in lats:
+        lat.close()
     return acc / (nsteps * nx * ny)
 
 
 def test_adjoint_512_matches_central_differences(R):
     """The stirred 512 x 512 workload (shell 4 <= |k| <= 6, 34 modes, amplitude 1e-4,
     seed 5, eta/s 0.05), 2000 steps, sqrt(N) checkpoints: the FP32 adjoint against
-    central differences of the FP64 forward objective (h = 1e-4 relative)."""
+    central differences of the FP64 forward objective (h = 1e-4 relative) for every one of
+    the 34 mode multipliers, eta/s and the body force.  Bars: each mode within 1e-4 of the
+    largest mode gradient (a mode whose gradient is far below the others cannot be resolved
+    to 1e-4 of itself by differences of J), the three largest within 1e-4 of themselves,
+    and eta/s and the body force within 1e-4 of themselves."""
     nx = ny = 512
     N = 2000
     kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
     J, gs, ge, gb = _gpu_grad(R, dict(nx=nx, ny=ny, **kw), N, "f32")
     nm = gs.size
     assert nm == 34
-    top = np.argsort(-np.abs(gs))[:3]
-    for m in top:
-        sp, sm = np.ones(nm), np.ones(nm)
-        sp[m] += 1e-4
-        sm[m] -= 1e-4
-        fd = (_objective_fp64(R, nx, ny, N, kw, sp) - _objective_fp64(R, nx, ny, N, kw, sm)) / 2e-4
-        assert abs(gs[m] - fd) <= 1e-4 * abs(fd), (m, gs[m], fd)
-    h = 1e-4 * 0.05
-    fd = (_objective_fp64(R, nx, ny, N, dict(kw, eta_over_s=0.05 + h))
-          - _objective_fp64(R, nx, ny, N, dict(kw, eta_over_s=0.05 - h))) / (2 * h)
-    assert abs(ge - fd) <= 1e-4 * abs(fd), (ge, fd)
-    hb = 1e-6
-    fd = (_objective_fp64(R, nx, ny, N, dict(kw, body_force=(hb, 0.0)))
-          - _objective_fp64(R, nx, ny, N, dict(kw, body_force=(-hb, 0.0)))) / (2 * hb)
-    assert abs(gb[0] - fd) <= 1e-4 * abs(fd), (gb[0], fd)
+    runs = []
+    for m in range(nm):
+        for sgn in (1.0, -1.0):
+            sig = np.ones(nm)
+            sig[m] += sgn * 1e-4
+            runs.append((kw, sig))
+    h, hb = 1e-4 * 0.05, 1e-6
+    runs += [(dict(kw, eta_over_s=0.05 + h), None), (dict(kw, eta_over_s=0.05 - h), None),
+             (dict(kw, body_force=(hb, 0.0)), None), (dict(kw, body_force=(-hb, 0.0)), None)]
+    Js = _objectives_fp64(R, nx, ny, N, runs)
+    fd = (Js[0:2 * nm:2] - Js[1:2 * nm:2]) / 2e-4
+    err = np.abs(gs - fd)
+    print("mode gradients: max |adjoint - FD| / max |FD| = %.2e (max |FD| %.3e, min |FD| %.3e)"
+          % (err.max() / np.abs(fd).max(), np.abs(fd).max(), np.abs(fd).min()))
+    assert err.max() <= 1e-4 * np.abs(fd).max()
+    for m in np.argsort(-np.abs(fd))[:3]:
+        assert err[m] <= 1e-4 * abs(fd[m]), (m, gs[m], fd[m])
+    fde = (Js[2 * nm] - Js[2 * nm + 1]) / (2 * h)
+    fdb = (Js[2 * nm + 2] - Js[2 * nm + 3]) / (2 * hb)
+    print("eta/s: %.6e vs FD %.6e; body force: %.6e vs FD %.6e" % (ge, fde, gb[0], fdb))
+    assert abs(ge - fde) <= 1e-4 * abs(fde), (ge, fde)
+    assert abs(gb[0] - fdb) <= 1e-4 * abs(fdb), (gb[0], fdb)
