@@ -60,8 +60,10 @@ def parse():
                    help="ensemble64: number of members (64; fewer only for profiling runs)")
     p.add_argument("--adjoint-steps", type=int, default=2000,
                    help="adjoint512: steps of the differentiated run (2000; fewer only for profiling runs)")
-    p.add_argument("--workload", default="stirred", choices=["stirred", "ensemble64", "adjoint512", "graphene", "channel"],
-                   help="stirred: one lattice (default); ensemble64: 64 stirred members of uneven sizes "
+    p.add_argument("--workload", default="stirred",
+                   choices=["stirred", "chained", "ensemble64", "adjoint512", "graphene", "channel"],
+                   help="stirred: one lattice (default); chained: the same in 500-step chained blocks, as the "
+                        "workload runs; ensemble64: 64 stirred members of uneven sizes "
                         "advanced by one persistent launch per step; adjoint512: gradient of the kinetic "
                         "energy of a 512^2 stirred run (2000 steps) by the checkpointed adjoint")
     a = p.parse_args()
@@ -848,6 +850,14 @@ def run_ensemble(args):
     print(json.dumps(standalone_line(f, args)), flush=True)
 
 
+def run_chained(args):
+    import torch
+    from paper_2205_04658_gb300 import rlbm
+    torch.cuda.set_device(0)
+    rlbm.lib()
+    print(json.dumps(standalone_line(form_stirred_chained(args, torch, rlbm), args)), flush=True)
+
+
 def run_adjoint(args):
     import torch
     from paper_2205_04658_gb300 import rlbm
@@ -906,6 +916,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "chained":
+        run_chained(args)
     elif args.workload == "ensemble64":
         run_ensemble(args)
     elif args.workload == "adjoint512":

@@ -184,8 +184,8 @@ RLBM_API int32_t rlbm_num_planes(const rlbm_ctx *ctx);
 RLBM_API rlbm_status rlbm_set_launch(rlbm_ctx *ctx, int32_t ctas, int32_t stages, int32_t stir_rows);
 
 /* Autotuner: times every launch shape it knows (pipeline depth x CTA count x stirring
- * rows staged or read from global memory), `reps`
- * launches each, on the current state, and keeps the fastest.  The state and the step
+ * rows staged or read from global memory), `reps` launches each, chained as rlbm_step
+ * chains consecutive steps, on the current state, and keeps the fastest.  The state and the step
  * counter are left as they were (the launches rewrite the next buffer only).  *ms_out
  * (may be NULL) receives the chosen shape's time per step in milliseconds.  Syncs.
  * The paper has no counterpart. */

@@ -916,10 +916,12 @@ rlbm_status rlbm_autotune(rlbm_ctx *c, int32_t reps, double *ms_out) {
         c->stages = stage_opts[si];
         c->grid_limit = grid_opts[gi];
         // the step kernel reads the current buffer and writes the other one; repeating it
-        // leaves the state (and the step counter) as it was
+        // leaves the state (and the step counter) as it was.  The repetitions are chained as
+        // rlbm_step chains consecutive steps (programmatic dependent launch), so the shape is
+        // chosen for the way the steps run.
         if ((e = dispatch_step(c, c->cur, st)) != cudaSuccess) break;  // warm-up
         cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch_step(c, c->cur, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch_step(c, c->cur, st, r > 0);
         cudaEventRecord(e1, c->stream);
         if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
         float ms = 0.0f;
