@@ -482,7 +482,10 @@ def form_stirred_chained(args, torch, rlbm):
     committed ncu summary of chained steps gives the DRAM bytes per step beside it."""
     nx = ny = 1024
     lat = rlbm.Lattice(nx, ny, precision="f32", **workload(args, 0))
-    lat.autotune(20)
+    if args.shape:  # a fixed launch shape (profiling runs, where timing the candidates means nothing)
+        lat.set_launch(*(int(v) for v in args.shape.split(",")))
+    else:
+        lat.autotune(20)
     lat.step(50)
     blocks = []
     for _ in range(4):

@@ -227,26 +227,51 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     if (FORCE) {
       if (staged) {
         const R4<float> *Gs = reinterpret_cast<const R4<float> *>(stg + TL::IN_STRIDE) + lx;
-        // (Re yA, Re yB, Im yA, Im yB) of each staged phase row: the pairs load as they are used
+        // (Re yA, Re yB, Im yA, Im yB) of each staged phase row: the pairs load as they are used.
+        // Two rows per iteration into two partial sums, so that both rows' loads and FMA chains
+        // are in flight at once (the synthesis is latency-bound when it runs one row at a time).
         const R4<float> *Es = reinterpret_cast<const R4<float> *>(stg + ey_off) + ly;
+        T Fx2(0.0f), Fy2(0.0f);
+        int r = 0;
 #pragma unroll 1
-        for (int r = 0; r < st.nrows; ++r) {
+        for (; r + 1 < st.nrows; r += 2) {
+          const R4<float> G = Gs[r * TILE_X], G1 = Gs[(r + 1) * TILE_X];
+          const R4<float> E = Es[r * 4], E1 = Es[(r + 1) * 4];
+          const T Ere(E.x, E.y), Eim(E.z, E.w), Ere1(E1.x, E1.y), Eim1(E1.z, E1.w);
+          Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
+          Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
+          Fx2 = fma(T(G1.x), Ere1, fma(T(-G1.y), Eim1, Fx2));
+          Fy2 = fma(T(G1.z), Ere1, fma(T(-G1.w), Eim1, Fy2));
+        }
+        if (r < st.nrows) {
           const R4<float> G = Gs[r * TILE_X];
           const R4<float> E = Es[r * 4];
           const T Ere(E.x, E.y), Eim(E.z, E.w);
           Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
           Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
         }
+        Fx += Fx2;
+        Fy += Fy2;
       } else {
+        // the same sums in the same order as the staged path (even rows into Fx, Fy, odd rows
+        // into Fx2, Fy2), so the two give the same bits
+        T Fx2(0.0f), Fy2(0.0f);
         for (int r = 0; r < st.nrows; ++r) {
           const R4<float> G = st.G_cur[(long long)r * g.nx + x];
           // yA = y0 + ly with ly < 4: yA and yB = yA + 4 share one entry of the phase table
           const R4<float> E = *reinterpret_cast<const R4<float> *>(reinterpret_cast<const float *>(st.EY) +
                                                                    (long long)r * 2 * st.eyp + ey_index(yA));
           const T Ere(E.x, E.y), Eim(E.z, E.w);
-          Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
-          Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
+          if (r & 1) {
+            Fx2 = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx2));
+            Fy2 = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy2));
+          } else {
+            Fx = fma(T(G.x), Ere, fma(T(-G.y), Eim, Fx));
+            Fy = fma(T(G.z), Ere, fma(T(-G.w), Eim, Fy));
+          }
         }
+        Fx += Fx2;
+        Fy += Fy2;
       }
     }
     if (macro_out) {  // the cells' Landau solutions and forces, kept for the reverse sweep
