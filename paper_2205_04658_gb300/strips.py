@@ -15,6 +15,9 @@ lattice's own rows, and rlbm_halo_pack / rlbm_halo_unpack move one face's crossi
   * exchange(): one halo exchange between processes that each hold one strip, over
     torch.distributed point-to-point messages (gloo between host processes; the same calls
     carry device tensors between GPUs).
+  * DistributedStrip: this process's strip of a lattice spread over the ranks of a process
+    group, exchanged with exchange() after every step (messages staged through pinned host
+    memory when the backend moves host tensors only, as gloo does).
 
 Conserved totals of the whole lattice are the sums of the strips' totals (FP64)."""
 import numpy as np
@@ -65,6 +68,92 @@ def exchange(dist, send_lo, send_hi, recv_lo, recv_hi, rank, world, periodic, gr
             w.wait()
 
 
+def _strip_kwargs(nx, ny, y0, y1, kw):
+    """Keyword arguments of rlbm.Lattice for the strip of rows [y0, y1) of the lattice that the
+    lattice-wide keyword arguments kw describe (their arrays cut to the strip's rows)."""
+    skw = {k: v for k, v in kw.items() if k not in ("solid", "init_eps", "init_ux", "init_uy")}
+    skw.update(strip_y0=y0, strip_ny_total=ny)
+    for k in ("init_eps", "init_ux", "init_uy"):
+        if kw.get(k) is not None:
+            skw[k] = np.asarray(kw[k], np.float64).reshape(ny, nx)[y0:y1]
+    if kw.get("solid") is not None:
+        m = np.asarray(kw["solid"], np.uint8).reshape(ny, nx)
+        skw["solid"] = m[y0:y1]
+        skw["strip_solid_halo"] = np.stack([m[(y0 - 1) % ny], m[y1 % ny]])
+    return skw
+
+
+class DistributedStrip:
+    """The strip of an nx x ny lattice that this rank of a torch.distributed process group
+    holds (strips in rank order, bottom first), on the current device.  Takes the keyword
+    arguments of rlbm.Lattice for the whole lattice.  step(n) advances it and exchanges the
+    halos with the neighbouring ranks after each step; every rank calls it together.
+    device_messages: send device tensors (NCCL); False stages the messages through pinned
+    host memory (gloo); None picks by the group's backend."""
+
+    def __init__(self, dist, nx, ny, stream=None, group=None, device_messages=None, **kw):
+        import torch
+        self.dist, self.group = dist, group
+        self.rank, self.world = dist.get_rank(group), dist.get_world_size(group)
+        self.nx, self.ny = nx, ny
+        self.periodic = not kw.get("walls_y", 0)
+        self.y0, self.y1 = strip_rows(ny, self.world)[self.rank]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.lat = rlbm.Lattice(nx, self.y1 - self.y0, stream=self.stream, **_strip_kwargs(nx, ny, self.y0, self.y1, kw))
+        if device_messages is None:
+            device_messages = dist.get_backend(group) == "nccl"
+        self.device_messages = device_messages
+        n = rlbm.rlbm_halo_bytes(self.lat.ctx)
+        self.dev = [torch.empty(n, dtype=torch.uint8, device="cuda") for _ in range(4)]  # send lo, hi; recv lo, hi
+        self.host = None if device_messages else [torch.empty(n, dtype=torch.uint8).pin_memory() for _ in range(4)]
+        self.exchange()
+
+    def exchange(self):
+        import torch
+        below, above = neighbours(self.rank, self.world, self.periodic)
+        ctx = self.lat.ctx
+        if below is not None:
+            rlbm.rlbm_halo_pack(ctx, 0, self.dev[0].data_ptr())
+        if above is not None:
+            rlbm.rlbm_halo_pack(ctx, 1, self.dev[1].data_ptr())
+        self.stream.synchronize()  # the messages are complete before another stream or the host reads them
+        if self.device_messages:
+            msg = self.dev
+        else:
+            for i in (0, 1):
+                self.host[i].copy_(self.dev[i])
+            msg = self.host
+        exchange(self.dist, msg[0], msg[1], msg[2], msg[3], self.rank, self.world, self.periodic, self.group)
+        if self.device_messages:  # the received messages are complete on torch's current stream
+            self.stream.wait_stream(torch.cuda.current_stream())
+        else:
+            for i in (2, 3):
+                self.dev[i].copy_(self.host[i])
+            torch.cuda.synchronize()
+        if below is not None:
+            rlbm.rlbm_halo_unpack(ctx, 0, self.dev[2].data_ptr())
+        if above is not None:
+            rlbm.rlbm_halo_unpack(ctx, 1, self.dev[3].data_ptr())
+
+    def step(self, n=1):
+        for _ in range(n):
+            self.lat.step(1)
+            self.exchange()
+
+    def moments(self):
+        """This strip's eps, u^x, u^y and the lattice's totals (an FP64 sum over the ranks)."""
+        import torch
+        E, UX, UY, tot = self.lat.moments()
+        t = torch.from_numpy(np.array(tot, dtype=np.float64))
+        if self.device_messages:
+            t = t.cuda()
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
+        return E, UX, UY, t.cpu().numpy()
+
+    def close(self):
+        self.lat.close()
+
+
 class StripSet:
     """A lattice of nx x ny cells held as `nstrips` strip contexts on the current device.
     Takes the keyword arguments of rlbm.Lattice; the lattice-wide arrays (solid, init_*)
@@ -77,19 +166,8 @@ class StripSet:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.periodic = not kw.get("walls_y", 0)
         self.rows = strip_rows(ny, nstrips)
-        solid = kw.pop("solid", None)
-        fields = {k: kw.pop(k, None) for k in ("init_eps", "init_ux", "init_uy")}
-        self.strips = []
-        for (y0, y1) in self.rows:
-            skw = dict(kw, strip_y0=y0, strip_ny_total=ny)
-            for k, v in fields.items():
-                if v is not None:
-                    skw[k] = np.asarray(v, np.float64).reshape(ny, nx)[y0:y1]
-            if solid is not None:
-                m = np.asarray(solid, np.uint8).reshape(ny, nx)
-                skw["solid"] = m[y0:y1]
-                skw["strip_solid_halo"] = np.stack([m[(y0 - 1) % ny], m[y1 % ny]])
-            self.strips.append(rlbm.Lattice(nx, y1 - y0, stream=self.stream, **skw))
+        self.strips = [rlbm.Lattice(nx, y1 - y0, stream=self.stream, **_strip_kwargs(nx, ny, y0, y1, kw))
+                       for (y0, y1) in self.rows]
         nbytes = rlbm.rlbm_halo_bytes(self.strips[0].ctx)
         # message buffers: [strip][face] (torch device allocations are 256-byte aligned)
         self.msg = [[torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
