@@ -614,24 +614,31 @@ def ensemble_errors(rlbm, precisions):
 def form_adjoint(args, torch, rlbm, nsteps=2000, reps=3):
     """Time per gradient of J = time-averaged mean |v|^2 / 2 of the 512^2 stirred run (shell
     4 <= |k| <= 6, 34 modes, amplitude 1e-4, seed 5, eta/s 0.05) with respect to the 34
-    mode multipliers, eta/s and the body force: forward with sqrt(N) checkpoints, segment
-    recomputation and the reverse sweep, all inside the timed call; compared with the
-    forward alone."""
+    mode multipliers, eta/s and the body force: the forward (keeping every state and each
+    step's Landau solution and force when they fit in a third of the free memory, else
+    sqrt(N) checkpoints and a recomputation per segment) and the reverse sweep, all inside
+    the timed call; compared with the forward alone."""
     nx = ny = 512
     kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
     stream = torch.cuda.Stream()
     lat = rlbm.Lattice(nx, ny, stream=stream, precision="f32", **kw)
     tuned_ms = lat.autotune(20)
-    nbytes = rlbm.rlbm_gradient_query_workspace(lat.ctx, nsteps, 0)
+    # every state kept when it fits in a third of the free memory (the forward runs once),
+    # else checkpoints every ceil(sqrt(N)) steps and each segment recomputed
+    segment = nsteps
+    nbytes = rlbm.rlbm_gradient_query_workspace(lat.ctx, nsteps, segment)
+    if nbytes > torch.cuda.mem_get_info()[0] // 3:
+        segment = 0
+        nbytes = rlbm.rlbm_gradient_query_workspace(lat.ctx, nsteps, segment)
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
     ptr = (ws.data_ptr() + 255) // 256 * 256
     with torch.cuda.stream(stream):
-        rlbm.rlbm_gradient(lat.ctx, nsteps, 0, ptr, nbytes)  # warm-up
+        rlbm.rlbm_gradient(lat.ctx, nsteps, segment, ptr, nbytes)  # warm-up
         times = []
         for _ in range(reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            J, gs, ge, gb = rlbm.rlbm_gradient(lat.ctx, nsteps, 0, ptr, nbytes)  # returns after a stream sync
+            J, gs, ge, gb = rlbm.rlbm_gradient(lat.ctx, nsteps, segment, ptr, nbytes)  # returns after a stream sync
             times.append(time.perf_counter() - t0)
     fwd = [time_chained(lat, torch, nsteps) * nsteps / 1e3 for _ in range(reps)]
     lat.close()
@@ -640,7 +647,8 @@ def form_adjoint(args, torch, rlbm, nsteps=2000, reps=3):
     return {"value": t, "unit": "s per gradient", "higher_is_better": False, "dtype": "f32",
             "workload": "gradient of the 512x512 stirred run (shell 4<=|k|<=6, 34 modes, amp 1e-4, seed 5, "
                         "eta/s 0.05), %d steps, wrt 34 mode multipliers, eta/s, body force" % nsteps,
-            "checkpoint_segment": int(round(nsteps ** 0.5 + 0.4999)), "workspace_bytes": nbytes,
+            "checkpoint_segment": segment if segment else int(round(nsteps ** 0.5 + 0.4999)),
+            "workspace_bytes": nbytes,
             "forward_only_s": tf, "gradient_over_forward": t / tf, "gradient_mlups": nx * ny * nsteps / t / 1e6,
             "J": J, "grad_eta_over_s": ge, "step_launch_tuned_ms": tuned_ms,
             "error": {"vs": "central finite differences of the FP64 forward, h = 1e-4 (tests/test_gpu_adjoint.py)",

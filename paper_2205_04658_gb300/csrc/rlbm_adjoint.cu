@@ -231,6 +231,7 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
   __shared__ R2<R> sF[8][32];
+  __shared__ R2<R> sE[32][8];  // the tile's phase rows EY_r(y0 + j) of the force adjoint's projections
   __shared__ double red[8][4];
   const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5, lane = tid & 31, warp = tid >> 5;
   const int wid = blockIdx.x, nworkers = gridDim.x;
@@ -287,6 +288,13 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
     R gom = R(0), gFx = R(0), gFy = R(0), jv = R(0);
 #pragma unroll
     for (int q = 0; q < Q; ++q) kap[q] = R(0);
+    // phase rows of the projections below, loaded now (one entry per thread: k_y row tid / 8,
+    // tile row tid % 8) so that the loads complete while the cell's reverse runs
+    R2<R> eyv{R(0), R(0)};
+    const bool ey_shared = st.nrows <= 32;  // wider shells read the phase rows from global memory below
+    const bool ey_loader = FORCE && ey_shared && tid < st.nrows * 8;
+    if (ey_loader && ty * TILE_Y + (tid & 7) < g.ny)
+      eyv = ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)(tid >> 3) * 2 * st.eyp, ty * TILE_Y + (tid & 7));
     if (fluid) {
       R h[Q], lam[Q];
       // the forward's Landau solution and force of this cell, loaded first so that the
@@ -368,15 +376,17 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
     // projections of the force adjoint on the k_y rows of the stirring tables
     if (FORCE && st.nrows > 0) {
       sF[ly][lx] = R2<R>{gFx, gFy};
+      if (ey_loader) sE[tid >> 3][tid & 7] = eyv;
       __syncthreads();
       const int jmax = g.ny - ty * TILE_Y;  // rows of this tile inside the lattice (>= 1)
       for (int r = ly; r < st.nrows; r += 8) {
-        const R *ey = reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp;
         R4<R> z{R(0), R(0), R(0), R(0)};
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           if (j < jmax) {
-            const R2<R> E = ey_at<R>(ey, ty * TILE_Y + j);
+            const R2<R> E = ey_shared ? sE[r][j]
+                                      : ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)r * 2 * st.eyp,
+                                                 ty * TILE_Y + j);
             const R2<R> F = sF[j][lx];
             z.x += F.x * E.x;
             z.y += F.x * E.y;

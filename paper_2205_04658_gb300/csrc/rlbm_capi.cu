@@ -1402,12 +1402,15 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   // ghost rows of wall-bounded lattices are never written: start from zeroed buffers
   if ((e = cudaMemsetAsync(w, 0, G.total, c->stream)) != cudaSuccess) return c->cuda_fail(e, "cudaMemsetAsync");
 
-  // forward: B_{-1} (the context's buffer) to checkpoint 0; B_{k seg - 1} into checkpoint k
+  // forward: B_{-1} (the context's buffer) to checkpoint 0; B_{k seg - 1} into checkpoint k.
+  // With one segment the recomputation of that segment (below) is the forward itself: it
+  // starts from checkpoint 0 and keeps every state, so no separate forward pass runs.
   const int64_t s0 = c->step;
+  const bool one_pass = G.K == 1;
   if ((e = cudaMemcpyAsync(ckpt(0), c->ws + c->L.pop[c->cur], G.state_bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
     return c->cuda_fail(e, "copy of the start state");
   int where = -1;  // B_{n-1}: -1 - k = checkpoint k, 0 / 1 = context buffer
-  for (int64_t n = 0; n < nsteps; ++n) {
+  for (int64_t n = 0; !one_pass && n < nsteps; ++n) {
     const CUtensorMap *ti = where < 0 ? &mck[-1 - where] : &c->tmap_in[where];
     void *fout;
     int next;
@@ -1423,8 +1426,10 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
       return c->cuda_fail(e, "step kernel launch");
     where = next;
   }
-  c->cur = where;  // the last step writes a context buffer
-  c->step = s0 + nsteps;
+  if (!one_pass) {
+    c->cur = where;  // the last step writes a context buffer
+    c->step = s0 + nsteps;
+  }
 
   // reverse sweep
   if ((e = launch_adj_twiddles(reinterpret_cast<double2 *>(w + G.tw), reinterpret_cast<float2 *>(w + G.twf), c->cfg.nx,
@@ -1451,6 +1456,43 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   mg.amp = c->cfg.force_amp;
   double *gstep = reinterpret_cast<double *>(w + G.gstep), *gsig = reinterpret_cast<double *>(w + G.gsig);
   const double cj = 1.0 / ((double)nsteps * (double)c->nfluid);
+  // stirring rows of steps lo .. hi-1 of segment k into the segment's table store, and the
+  // states B_lo .. B_{hi-2} from checkpoint k into the slots (B_{hi-1} into the scratch state)
+  auto recompute = [&](int k, int64_t lo, int64_t hi) -> cudaError_t {
+    cudaError_t e2;
+    if (c->L.nmodes) {
+      HostStir sp = stir_for_step(c, s0 + lo);
+      void *cn = c->ws + c->L.coef[(s0 + lo) & 1], *cn1 = c->ws + c->L.coef[(s0 + lo + 1) & 1];
+      e2 = c->cfg.precision == RLBM_F64 ? launch_stir_prime_f64(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream)
+                                        : launch_stir_prime_f32(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream);
+      if (e2 != cudaSuccess) return e2;
+    }
+    // steps lo .. hi-1 again, each keeping its cells' Landau solution and force for the
+    // reverse step of the same index (the last one's state and next rows are not needed)
+    for (int64_t n = lo; n <= hi - 1; ++n) {
+      const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
+      HostStir st = stir_for_step(c, s0 + n);
+      if (c->L.nmodes) {
+        st.G_cur = gtab((int)(n - lo));
+        st.G_next = n == hi - 1 ? w + G.gscratch : gtab((int)(n - lo + 1));
+      }
+      c->phys.step = s0 + n;
+      void *fout = n == hi - 1 ? w + G.scratch : slot((int)(n - lo));
+      if ((e2 = dispatch_step_raw(c, ti, fout, s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr, n > lo,
+                                  w + G.macro + G.macro_bytes * (size_t)(n - lo))) != cudaSuccess)
+        return e2;
+    }
+    return cudaSuccess;
+  };
+  if (one_pass) {
+    if ((e = recompute(0, 0, nsteps)) != cudaSuccess) return c->cuda_fail(e, "step kernel launch (forward)");
+    // the state after the run, B_{N-1}, into a context buffer, as rlbm_step(N) would leave it
+    const int dst = c->cur ^ 1;
+    if ((e = cudaMemcpyAsync(c->ws + c->L.pop[dst], w + G.scratch, G.state_bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+      return c->cuda_fail(e, "copy of the final state");
+    c->cur = dst;
+    c->step = s0 + nsteps;
+  }
   int kc = 0;  // kap[kc] holds kappa_{n+1}
   // the last state: objective only (its force terms are multiplied by a zero adjoint)
   a.B = c->ws + c->L.pop[c->cur];
@@ -1465,30 +1507,7 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
   for (int k = G.K - 1; k >= 0; --k) {
     const int64_t lo = (int64_t)k * G.seg, hi = std::min<int64_t>(lo + G.seg, nsteps);
-    // stirring rows of steps lo .. hi-1 into the segment's table store, and the states
-    // B_lo .. B_{hi-2} from checkpoint k into the slots
-    if (c->L.nmodes) {
-      HostStir sp = stir_for_step(c, s0 + lo);
-      void *cn = c->ws + c->L.coef[(s0 + lo) & 1], *cn1 = c->ws + c->L.coef[(s0 + lo + 1) & 1];
-      e = c->cfg.precision == RLBM_F64 ? launch_stir_prime_f64(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream)
-                                       : launch_stir_prime_f32(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream);
-      if (e != cudaSuccess) return c->cuda_fail(e, "stirring set-up kernels");
-    }
-    // steps lo .. hi-1 again, each keeping its cells' Landau solution and force for the
-    // reverse step of the same index (the last one's state and next rows are not needed)
-    for (int64_t n = lo; n <= hi - 1; ++n) {
-      const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
-      HostStir st = stir_for_step(c, s0 + n);
-      if (c->L.nmodes) {
-        st.G_cur = gtab((int)(n - lo));
-        st.G_next = n == hi - 1 ? w + G.gscratch : gtab((int)(n - lo + 1));
-      }
-      c->phys.step = s0 + n;
-      void *fout = n == hi - 1 ? w + G.scratch : slot((int)(n - lo));
-      if ((e = dispatch_step_raw(c, ti, fout, s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr, n > lo,
-                                 w + G.macro + G.macro_bytes * (size_t)(n - lo))) != cudaSuccess)
-        return c->cuda_fail(e, "step kernel launch (recompute)");
-    }
+    if (!one_pass && (e = recompute(k, lo, hi)) != cudaSuccess) return c->cuda_fail(e, "step kernel launch (recompute)");
     for (int64_t n = hi - 1; n >= lo; --n) {
       a.B = n == lo ? ckpt(k) : slot((int)(n - lo - 1));
       a.tB = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
