@@ -55,6 +55,41 @@ __device__ __forceinline__ void pull_staged(const T *tile, int plane, int txb, i
   }
 }
 
+// The same two pulls for the two cells (x, y) and (x, y + 4) of a thread (db = the staged offset
+// of the second cell), as packed FP32 pairs: the FP32 reverse step.
+template <int VS, bool MASK, int SIGN>
+__device__ __forceinline__ void pull_staged_pair(const float *tile, int plane, int txb, int b0, int db,
+                                                 const Geometry<float> &g, unsigned nbA, unsigned nbB,
+                                                 F2 out[VSet<VS>::Q]) {
+  constexpr int Q = VSet<VS>::Q;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float *pl = tile + q * plane + b0;
+    const float *own = tile + VSet<VS>::opp(q) * plane + b0;
+    const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
+    F2 acc = F2(g.beta2[q][0]) * F2(pl[0], pl[db]);
+    if (sx != 0) {
+      float vA = pl[SIGN * sx], vB = pl[db + SIGN * sx];
+      if (MASK && ((nbA >> (4 + SIGN * sx)) & 1u)) vA = own[0];
+      if (MASK && ((nbB >> (4 + SIGN * sx)) & 1u)) vB = own[db];
+      acc = fma(F2(g.beta2[q][1]), F2(vA, vB), acc);
+    }
+    if (sy != 0) {
+      float vA = pl[SIGN * sy * txb], vB = pl[db + SIGN * sy * txb];
+      if (MASK && ((nbA >> (4 + 3 * SIGN * sy)) & 1u)) vA = own[0];
+      if (MASK && ((nbB >> (4 + 3 * SIGN * sy)) & 1u)) vB = own[db];
+      acc = fma(F2(g.beta2[q][2]), F2(vA, vB), acc);
+    }
+    if (sx != 0 && sy != 0) {
+      float vA = pl[SIGN * (sy * txb + sx)], vB = pl[db + SIGN * (sy * txb + sx)];
+      if (MASK && ((nbA >> (4 + SIGN * (3 * sy + sx))) & 1u)) vA = own[0];
+      if (MASK && ((nbB >> (4 + SIGN * (3 * sy + sx))) & 1u)) vB = own[db];
+      acc = fma(F2(g.beta2[q][3]), F2(vA, vB), acc);
+    }
+    out[q] = acc;
+  }
+}
+
 // Reverse of one cell's collision and force (coll_coeffs / collide_all) and of its
 // objective term cj |v|^2 / 2, given the cell's post-streaming deviations h, their
 // moments M and Landau solution m, and the adjoint lam of the cell's output.  Returns
@@ -114,7 +149,7 @@ __device__ __forceinline__ void cell_adjoint(const R h[VSet<VS>::Q], const R lam
   ux_b -= cc_b * R(2 * V::CC) * epsh * ux;
   uy_b -= cc_b * R(2 * V::CC) * epsh * uy;
   // om = omega0 eps^(1/4) (D_p = 3) or omega0 eps^(1/3) (D_p = 2)
-  epsh_b += om_b * om / (R(VS == 3 ? 4 : 3) * epsh);
+  epsh_b += divide(om_b * om, R(VS == 3 ? 4 : 3) * epsh);
   gom = om_b * om;
 
   R e_b = R(0), mx_b = R(0), my_b = R(0), txx_b = R(0), txy_b = R(0), tyy_b = R(0);
@@ -169,11 +204,11 @@ __device__ __forceinline__ void cell_adjoint(const R h[VSet<VS>::Q], const R lam
   vy_b -= epsh_b * M.my;
 
   // Landau: J = dR/dv = -T + v m^T - eps^ I;  J^T w = vbar;  pbar -= (dR/dp)^T w
-  constexpr R dinv = R(1.0 / V::DP);
+  const R dinv = R(1.0 / V::DP);
   const R Txx = dinv + M.txx, Txy = M.txy, Tyy = dinv + M.tyy;
   const R jxx = -Txx + vx * M.mx - epsh, jxy = -Txy + vx * M.my;
   const R jyx = -Txy + vy * M.mx, jyy = -Tyy + vy * M.my - epsh;
-  const R idet = R(1) / (jxx * jyy - jxy * jyx);
+  const R idet = divide(R(1), jxx * jyy - jxy * jyx);
   const R wx = (jyy * vx_b - jyx * vy_b) * idet;
   const R wy = (jxx * vy_b - jxy * vx_b) * idet;
   const R wv = wx * vx + wy * vy;
@@ -432,6 +467,230 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
   }
 }
 
+// The FP32 reverse step with two cells per thread (128 threads): cells (x, y) and (x, y + 4) of
+// the 32 x 8 tile, the pulls, moments, the cell's reverse and the objective on packed FP32
+// pairs, as the forward step kernel computes its FP32 paths.  Tile walk, staging, chaining,
+// stores, row projections and tile sums as in adjoint_kernel.
+template <int VS, bool MASK, bool FORCE, bool LAM, int NST>
+__global__ void __launch_bounds__(128)
+adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tK,
+                    float *__restrict__ kout, const Geometry<float> g, const Physics<float> p,
+                    const AdjStir<float> st, const float cj, double *__restrict__ acc,
+                    R4<float> *__restrict__ zpart, unsigned *__restrict__ err, const float *__restrict__ macro) {
+  using TL = Tile<float, VS>;
+  using T = F2;
+  constexpr int Q = VSet<VS>::Q;
+  constexpr int PL = TL::TYB * TL::TXB;  // elements of a staged plane
+  constexpr int STAGE = TL::IN_STRIDE * (LAM ? 2 : 1);
+  constexpr int DB = (TILE_Y / 2) * TL::TXB;  // staged offset of a thread's second cell
+  constexpr int NT = 128;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
+  __shared__ R2<float> sF[8][32];
+  __shared__ R2<float> sE[32][8];  // the tile's phase rows EY_r(y0 + j) of the projections
+  __shared__ double red[4][4];
+  const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5, lane = tid & 31, warp = tid >> 5;
+  const int wid = blockIdx.x, nworkers = gridDim.x;
+  const int ntx = (g.nx + 31) / 32, ntiles = ntx * ((g.ny + 7) / 8);
+  const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
+  const uint32_t stage_bytes = TL::IN_BYTES * (LAM ? 2 : 1);
+  if (tid == 0) {
+    for (int s2 = 0; s2 < NST; ++s2) mbar_init(&bar[s2], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue_B = [&](int k) {
+    const int t = wid + k * nworkers;
+    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    uint64_t *b = &bar[k % NST];
+    mbar_expect_tx(b, stage_bytes);
+    tma_load_3d(smem + (k % NST) * STAGE, &tB, b, x0 + TL::XOFF - TL::V, y0, 0);
+  };
+  auto issue_K = [&](int k) {
+    if (!LAM) return;
+    const int t = wid + k * nworkers;
+    const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
+    tma_load_3d(smem + (k % NST) * STAGE + TL::IN_STRIDE, &tK, &bar[k % NST], x0 + TL::XOFF - TL::V, y0, 0);
+  };
+  auto issue = [&](int k) { issue_B(k); issue_K(k); };
+  if (tid == 0)
+    for (int k = 0; k < NST && k < my_tiles; ++k) issue_B(k);
+  griddep_wait();
+  if (tid == 0)
+    for (int k = 0; k < NST && k < my_tiles; ++k) issue_K(k);
+  bool alive = true;
+  {
+    const bool ok = my_tiles == 0 || mbar_wait_bounded(&bar[0], 0, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) alive = false;
+  }
+  const bool ey_shared = st.nrows <= 32;  // wider shells read the phase rows from global memory below
+  const int ney = (FORCE && ey_shared) ? st.nrows * 8 : 0;
+  for (int k = 0; alive && k < my_tiles; ++k) {
+    if (tid == 0 && k == my_tiles - 1) griddep_launch_dependents();
+    const int t = wid + k * nworkers;
+    const int tx = t % ntx, ty = t / ntx;
+    const int x = tx * TILE_X + lx, yA = ty * TILE_Y + ly, yB = yA + TILE_Y / 2;
+    const float *tileB = reinterpret_cast<const float *>(smem + (k % NST) * STAGE);
+    const float *tileK = reinterpret_cast<const float *>(smem + (k % NST) * STAGE + TL::IN_STRIDE);
+    const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
+    const bool inA = x < g.nx && yA < g.ny, inB = x < g.nx && yB < g.ny;
+    unsigned nbA = 0, nbB = 0;
+    if (MASK) {
+      if (inA) nbA = g.nbmask[(long long)yA * g.nx + x];
+      if (inB) nbB = g.nbmask[(long long)yB * g.nx + x];
+    }
+    const bool flA = inA && !(MASK && (nbA & 16u)), flB = inB && !(MASK && (nbB & 16u));
+    // phase rows of the projections below, loaded now (entries tid and tid + 128: k_y row e / 8,
+    // tile row e % 8) so that the loads complete while the cells' reverse runs
+    R2<float> ey0{0.0f, 0.0f}, ey1{0.0f, 0.0f};
+    const int yj = ty * TILE_Y + (tid & 7);
+    if (tid < ney && yj < g.ny)
+      ey0 = ey_at<float>(reinterpret_cast<const float *>(st.EY) + (long long)(tid >> 3) * 2 * st.eyp, yj);
+    if (tid + NT < ney && yj < g.ny)
+      ey1 = ey_at<float>(reinterpret_cast<const float *>(st.EY) + (long long)((tid + NT) >> 3) * 2 * st.eyp, yj);
+    T kap[Q];
+    T gom(0.0f), gFx(0.0f), gFy(0.0f), jv(0.0f);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) kap[q] = T(0.0f);
+    if (flA || flB) {
+      T h[Q], lam[Q];
+      // the forward's Landau solution and force of the two cells, loaded first so that the
+      // loads overlap the pulls
+      float mA[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, mB[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      if (macro) {
+        const long long nc = (long long)g.nx * g.ny;
+        if (flA) {
+#pragma unroll
+          for (int j = 0; j < 5; ++j) mA[j] = macro[j * nc + (long long)yA * g.nx + x];
+        }
+        if (flB) {
+#pragma unroll
+          for (int j = 0; j < 5; ++j) mB[j] = macro[j * nc + (long long)yB * g.nx + x];
+        }
+      }
+      pull_staged_pair<VS, MASK, -1>(tileB, PL, TL::TXB, b0, DB, g, nbA, nbB, h);
+      if (LAM) {
+        pull_staged_pair<VS, MASK, 1>(tileK, PL, TL::TXB, b0, DB, g, nbA, nbB, lam);
+      } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) lam[q] = T(0.0f);
+      }
+      if (!(flA && flB)) {  // a lane without fluid (outside the lattice or solid) works on the rest state
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          h[q] = T(flA ? h[q].v.x : 0.0f, flB ? h[q].v.y : 0.0f);
+          lam[q] = T(flA ? lam[q].v.x : 0.0f, flB ? lam[q].v.y : 0.0f);
+        }
+      }
+      const Mom<T> M = moments_of<T, T, VS, FORCE>(h);
+      Macro<T> m;
+      T Fx(p.body_x), Fy(p.body_y);
+      if (macro) {
+        // u^mu = gamma (1, v) as the step kernel forms it from v
+        const T vx(mA[1], mB[1]), vy(mA[2], mB[2]);
+        const T gam = FM<T>::rsqrt(T(1.0f) - fma(vx, vx, vy * vy));
+        m.eps_m1 = T(mA[0], mB[0]);
+        m.vx = vx;
+        m.vy = vy;
+        m.u0 = gam;
+        m.ux = gam * vx;
+        m.uy = gam * vy;
+        m.ok = true;
+        Fx = T(mA[3], mB[3]);
+        Fy = T(mA[4], mB[4]);
+      } else {
+        m = cell_macro_pair<VS>(h, M, p.vmax2);
+        if (!m.ok) atomicOr(err, (isfinite(m.eps_m1.v.x) && isfinite(m.eps_m1.v.y)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
+        // (without kappa_{n+1}, the state's force meets a zero adjoint: the body force stands in)
+      }
+      cell_adjoint<T, VS, FORCE>(h, lam, M, m, T(p.omega0), T(p.fpref), Fx, Fy, T(cj), kap, gom, gFx, gFy);
+      jv = T(cj) * T(0.5f) * fma(m.vx, m.vx, m.vy * m.vy);
+      if (!(flA && flB)) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) kap[q] = T(flA ? kap[q].v.x : 0.0f, flB ? kap[q].v.y : 0.0f);
+        gom = T(flA ? gom.v.x : 0.0f, flB ? gom.v.y : 0.0f);
+        gFx = T(flA ? gFx.v.x : 0.0f, flB ? gFx.v.y : 0.0f);
+        gFy = T(flA ? gFy.v.x : 0.0f, flB ? gFy.v.y : 0.0f);
+        jv = T(flA ? jv.v.x : 0.0f, flB ? jv.v.y : 0.0f);
+      }
+    }
+#pragma unroll
+    for (int ln = 0; ln < 2; ++ln) {
+      const int y = ln ? yB : yA;
+      if (!(ln ? inB : inA)) continue;
+      float *o = kout + (long long)(y + 1) * g.pitch + x + PadLayout<float>::XOFF;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) o[q * g.plane] = ln ? kap[q].v.y : kap[q].v.x;
+      const int gxv = ghost_col(x, g.nx, g.walls);
+      const int gyv = ghost_row(y, g.ny, g.walls);
+      if (gxv != INT_MIN || gyv != INT_MIN) {
+        const int px[3] = {gxv, x, gxv}, py[3] = {y, gyv, gyv};
+        for (int a = 0; a < 3; ++a) {
+          if (px[a] == INT_MIN || py[a] == INT_MIN) continue;
+          float *d = kout + (long long)(py[a] + 1) * g.pitch + px[a] + PadLayout<float>::XOFF;
+#pragma unroll
+          for (int q = 0; q < Q; ++q) d[q * g.plane] = ln ? kap[q].v.y : kap[q].v.x;
+        }
+      }
+    }
+    // projections of the force adjoint on the k_y rows of the stirring tables
+    if (FORCE && st.nrows > 0) {
+      sF[ly][lx] = R2<float>{gFx.v.x, gFy.v.x};
+      sF[ly + TILE_Y / 2][lx] = R2<float>{gFx.v.y, gFy.v.y};
+      if (tid < ney) sE[tid >> 3][tid & 7] = ey0;
+      if (tid + NT < ney) sE[(tid + NT) >> 3][tid & 7] = ey1;
+      __syncthreads();
+      const int jmax = g.ny - ty * TILE_Y;  // rows of this tile inside the lattice (>= 1)
+      for (int r = warp; r < st.nrows; r += NT / 32) {
+        R4<float> z{0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < jmax) {
+            const R2<float> E = ey_shared ? sE[r][j]
+                                          : ey_at<float>(reinterpret_cast<const float *>(st.EY) +
+                                                             (long long)r * 2 * st.eyp, ty * TILE_Y + j);
+            const R2<float> F = sF[j][lx];
+            z.x += F.x * E.x;
+            z.y += F.x * E.y;
+            z.z += F.y * E.x;
+            z.w += F.y * E.y;
+          }
+        }
+        if (x < g.nx) zpart[((long long)ty * st.nrows + r) * g.nx + x] = z;
+      }
+    }
+    // tile sums (fixed order): the two cells of a thread, warp sums in FP32, the four warp
+    // sums in FP64
+    float v[4] = {gom.v.x + gom.v.y, gFx.v.x + gFx.v.y, gFy.v.x + gFy.v.y, jv.v.x + jv.v.y};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], off);
+      if (lane == 0) red[warp][c] = (double)v[c];
+    }
+    __syncthreads();
+    if (tid < 4) {
+      double sum = 0.0;
+      for (int w4 = 0; w4 < NT / 32; ++w4) sum += red[w4][tid];
+      atomicAdd(&acc[(long long)t * 4 + tid], sum);
+    }
+    if (NST == 1) {  // the only stage is free once every thread is done with it
+      __syncthreads();
+      if (tid == 0 && k + 1 < my_tiles) issue(k + 1);
+    }
+    const bool ok = k + 1 >= my_tiles || mbar_wait_bounded(&bar[(k + 1) % NST], ((k + 1) / NST) & 1, WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {  // (NST = 2: also the barrier after which this stage is free)
+      alive = false;
+      break;
+    }
+    if (NST >= 2 && tid == 0 && k + NST < my_tiles) issue(k + NST);
+  }
+  if (!alive && tid == 0) {
+    atomicOr(err, ERR_TIMEOUT);
+    for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&bar[s2], 0, WAIT_CYCLES);
+  }
+}
+
 // zsum_j[r][x] = sum over block rows of zpart_j: the k_y-row transform of the force
 // adjoint of step j of a segment at column x (blockIdx.z = j), in the compute type.
 template <typename R>
@@ -521,6 +780,13 @@ __global__ void adj_twiddle_kernel(double2 *tw, float2 *twf, int n) {
   twf[t] = make_float2((float)c, (float)s);
 }
 
+// The reverse-step kernel of a storage type (same parameters for both forms).
+template <typename S, int VS, bool MASK, bool FORCE, bool LAM, int NST>
+static auto pick_adjoint_kernel() {
+  if constexpr (sizeof(S) == 4) return adjoint_pair_kernel<VS, MASK, FORCE, LAM, NST>;
+  else return adjoint_kernel<S, VS, MASK, FORCE, LAM, NST>;
+}
+
 template <typename S, int VS, bool MASK, bool FORCE, bool LAM>
 static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typename RealOf<S>::type> &g,
                                     const Physics<typename RealOf<S>::type> &p,
@@ -529,7 +795,10 @@ static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typenam
   using R = typename RealOf<S>::type;
   using TL = Tile<S, VS>;
   constexpr int NST = 2;
-  auto kern = adjoint_kernel<S, VS, MASK, FORCE, LAM, NST>;
+  // FP32: two cells per thread on packed pairs (128 threads); FP64: one cell per thread
+  constexpr bool PAIR = sizeof(S) == 4;
+  constexpr int NT = PAIR ? 128 : 256;
+  auto kern = pick_adjoint_kernel<S, VS, MASK, FORCE, LAM, NST>();
   const int smem = NST * TL::IN_STRIDE * (LAM ? 2 : 1) + 64 + 128;
   static int configured_dev = -1, max_blocks = 0, sms = 0;
   int dev = 0;
@@ -537,7 +806,7 @@ static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typenam
   if (configured_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, kern, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks, kern, NT, smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -552,7 +821,7 @@ static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typenam
   if (LAM && a.chained) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(workers);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -563,8 +832,8 @@ static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typenam
     return cudaLaunchKernelEx(&cfg, kern, mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err,
                               (const R *)a.macro);
   }
-  kern<<<workers, 256, smem, st>>>(mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err,
-                                   (const R *)a.macro);
+  kern<<<workers, NT, smem, st>>>(mB, mK, (R *)a.kout, g, p, s, (R)a.cj, a.acc, (R4<R> *)a.zpart, a.err,
+                                  (const R *)a.macro);
   return cudaGetLastError();
 }
 

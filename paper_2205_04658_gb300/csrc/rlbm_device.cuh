@@ -418,6 +418,7 @@ struct F2 {
   __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
   __device__ __forceinline__ explicit F2(float2 w) : v(w) {}
   __device__ __forceinline__ F2 &operator+=(F2 o) { v = __fadd2_rn(v, o.v); return *this; }
+  __device__ __forceinline__ F2 &operator-=(F2 o) { v = __ffma2_rn(o.v, make_float2(-1.0f, -1.0f), v); return *this; }
 };
 __device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
 __device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
@@ -425,6 +426,10 @@ __device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a
 __device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v)); }
 __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
 __device__ __forceinline__ F2 fmax(F2 a, F2 b) { return F2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+// a / b, correctly rounded per lane
+template <typename T> __device__ __forceinline__ T divide(T a, T b) { return a / b; }
+__device__ __forceinline__ F2 divide(F2 a, F2 b) { return F2(a.v.x / b.v.x, a.v.y / b.v.y); }
+
 template <> struct FM<F2> {
   static __device__ __forceinline__ F2 rcp(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
   static __device__ __forceinline__ F2 rsqrt(F2 x) { return F2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
