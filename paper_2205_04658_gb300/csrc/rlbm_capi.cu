@@ -450,11 +450,12 @@ rlbm_status usable(rlbm_ctx *c) {
   return RLBM_OK;
 }
 
+// h of a stored value and back (FP16 storage holds HScale<__half>::up times h)
 template <typename S> double to_double(S v) { return (double)v; }
-template <> double to_double<__half>(__half v) { return (double)__half2float(v); }
+template <> double to_double<__half>(__half v) { return (double)__half2float(v) * HScale<__half>::down; }
 template <> double to_double<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 template <typename S> S from_double(double v) { return (S)v; }
-template <> __half from_double<__half>(double v) { return __float2half_rn((float)v); }
+template <> __half from_double<__half>(double v) { return __float2half_rn((float)(v * HScale<__half>::up)); }
 template <> __nv_bfloat16 from_double<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
 template <typename S> void unpack_state(const rlbm_ctx *c, const uint8_t *src, double *dst) {
@@ -606,7 +607,7 @@ rlbm_status rlbm_init(const rlbm_config *cfg, void *dev_workspace, size_t bytes,
   if (L.nmodes) {
     const Modes m = shell_modes(cfg->kmin, cfg->kmax);
     // phase rows in the layout of ey_index: per row 2 eyp reals, blocks of 8 lattice rows,
-    // entry k of a block = (Re y, Re y+4, Im y, Im y+4) for y = 8 b + k
+    // entry k of a block = (Re y, Re y+1, Im y, Im y+1) for y = 8 b + 2 k
     // (the phase of lattice row y0 + y for a strip starting at row y0 of ny_t rows)
     std::vector<double> ey((size_t)L.nrows * 2 * L.eyp, 0.0);
     const long long y0 = is_strip(*cfg) ? cfg->strip_y0 : 0, nyt = total_rows(*cfg);

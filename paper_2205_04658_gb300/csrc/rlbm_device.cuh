@@ -89,20 +89,41 @@ template <int VS> __host__ __device__ constexpr int sgny(int q) {
 // ---------------------------------------------------------------------------
 // Storage conversions
 // ---------------------------------------------------------------------------
+// Scale of the stored deviations.  FP16 storage holds 2^8 h: the deviations down to 2^-22
+// (not 2^-14) then lie in FP16's normal range, where the stochastic rounding of the stores
+// is unbiased, and |h| up to 255 stays below FP16's largest value.  Powers of two, so the
+// scaling itself is exact.
+template <typename S> struct HScale {
+  static constexpr float up = 1.0f, down = 1.0f;
+};
+template <> struct HScale<__half> {
+  static constexpr float up = 256.0f, down = 1.0f / 256.0f;
+};
+
+// h of one stored value (load_h: global memory through the read-only path; load_h_s:
+// shared memory) and h to its stored form.
 template <typename S, typename R> __device__ __forceinline__ R load_h(const S *p) { return (R)__ldg(p); }
 template <> __device__ __forceinline__ float load_h<__half, float>(const __half *p) {
-  return __half2float(__ldg(p));
+  return __half2float(__ldg(p)) * HScale<__half>::down;
 }
 template <> __device__ __forceinline__ float load_h<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
   return __bfloat162float(__ldg(p));
 }
 template <typename S, typename R> __device__ __forceinline__ R load_h_s(const S *p) { return (R)*p; }
-template <> __device__ __forceinline__ float load_h_s<__half, float>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float load_h_s<__half, float>(const __half *p) {
+  return __half2float(*p) * HScale<__half>::down;
+}
 template <> __device__ __forceinline__ float load_h_s<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
   return __bfloat162float(*p);
 }
+// A stored value as FP32 without the storage scale (the paired step kernels fold 1 / up
+// into their pull weights).
+template <typename S> __device__ __forceinline__ float load_s_raw(const S *p) { return load_h_s<S, float>(p); }
+template <> __device__ __forceinline__ float load_s_raw<__half>(const __half *p) { return __half2float(*p); }
 template <typename S, typename R> __device__ __forceinline__ S store_h(R v) { return (S)v; }
-template <> __device__ __forceinline__ __half store_h<__half, float>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half store_h<__half, float>(float v) {
+  return __float2half_rn(v * HScale<__half>::up);
+}
 template <> __device__ __forceinline__ __nv_bfloat16 store_h<__nv_bfloat16, float>(float v) {
   return __float2bfloat16_rn(v);
 }
@@ -150,31 +171,49 @@ template <typename R> struct Physics {
 // ---------------------------------------------------------------------------
 // Stochastic rounding of the 16-bit stores: unbiased (E[round(v)] = v), so the rounding
 // errors of successive steps do not add up coherently.  The random bits are a
-// counter-based hash of (cell, step, key) stepped by a linear congruential generator per
-// value, so a run repeats exactly.
+// counter-based hash of (cell, step, key), advanced by a Weyl step (an odd constant near
+// 2^32 / golden ratio added modulo 2^32) per value, so a run repeats exactly.  Every value's
+// bits are uniform because the hash is; the 17 values of one cell take evenly spread
+// offsets from it.  (An integer add, where a multiplicative generator would occupy the
+// FMA pipe that the cell's arithmetic already saturates.)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t cell_hash(uint32_t x, uint32_t y, uint32_t step, uint32_t key) {
   uint32_t h = (x * 0x9E3779B1u) ^ ((y + 0x7F4A7C15u) * 0x85EBCA77u) ^ ((step ^ key) * 0xC2B2AE3Du);
   h ^= h >> 16; h *= 0x7FEB352Du; h ^= h >> 15; h *= 0x846CA68Bu; h ^= h >> 16;
   return h;
 }
-__device__ __forceinline__ uint32_t lcg_next(uint32_t r) { return r * 1664525u + 1013904223u; }
+__device__ __forceinline__ uint32_t next_bits(uint32_t r) { return r + 0x9E3779B9u; }
 
 // v rounded to storage type S: to nearest, or stochastically with the random bits r.
-// FP16: adding 13 random bits below the kept mantissa and truncating (round toward zero)
-// rounds the magnitude up with probability equal to the dropped fraction; below the
-// FP16 normal range (|v| < 2^-14) the value is rounded to nearest.  BF16: the same with
-// 16 bits on the FP32 pattern.
+// BF16: adding 16 random bits below the kept mantissa of the FP32 pattern and truncating
+// (round toward zero) rounds the magnitude up with probability equal to the dropped
+// fraction.  (FP16 pairs: round_pair_f16 below.)
 template <typename S> __device__ __forceinline__ S store_round(float v, bool sr, uint32_t r) {
   return store_h<S, float>(v);
-}
-template <> __device__ __forceinline__ __half store_round<__half>(float v, bool sr, uint32_t r) {
-  if (!sr || fabsf(v) < 6.103515625e-05f) return __float2half_rn(v);
-  return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));
 }
 template <> __device__ __forceinline__ __nv_bfloat16 store_round<__nv_bfloat16>(float v, bool sr, uint32_t r) {
   if (!sr) return __float2bfloat16_rn(v);
   return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
+}
+
+// The two cells of a pair, already multiplied by the storage scale, rounded stochastically
+// to FP16 in one packed conversion with the random bits ra, rb (the low half of the result
+// holds a, the high half b): 13 random bits are added below the kept FP16 mantissa of each
+// FP32 value and the sums are truncated (round toward zero), which rounds the magnitude up
+// with probability equal to the dropped fraction.  Below FP16's normal range (2^-14, i.e.
+// |h| < 2^-22) the 13 bits do not reach every dropped bit and the rounding leans toward
+// zero by less than one FP16 subnormal spacing, 2^-32 in h.
+__device__ __forceinline__ uint32_t round_pair_f16_sr(float a, float b, uint32_t ra, uint32_t rb) {
+  const float ua = __uint_as_float(__float_as_uint(a) + (ra >> 19));
+  const float ub = __uint_as_float(__float_as_uint(b) + (rb >> 19));
+  uint32_t d;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(ub), "f"(ua));  // (high, low) = (b, a)
+  return d;
+}
+// The same rounded to nearest.
+__device__ __forceinline__ uint32_t round_pair_f16_rn(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 template <typename R> struct Stir {
@@ -301,9 +340,9 @@ __device__ inline void stir_table_part(const Stir<R> &s, int rank, int ncta, int
 
 // The per-row phase table EY_r(y) = exp(i 2 pi k_y(r) y / ny): each k_y row holds 2 eyp
 // reals in blocks of 8 lattice rows; entry k (0..3) of block b holds
-// (Re y, Re y+4, Im y, Im y+4) for y = 8b + k.  One 16-byte load then gives a thread of the
-// paired kernels (cells y and y + 4) both phases as register pairs.
-__host__ __device__ __forceinline__ int ey_index(int y) { return (y >> 3) * 16 + (y & 3) * 4 + ((y >> 2) & 1); }
+// (Re y, Re y+1, Im y, Im y+1) for y = 8b + 2k.  One 16-byte load then gives a thread of the
+// paired step kernels (cells y and y + 1) both phases as register pairs.
+__host__ __device__ __forceinline__ int ey_index(int y) { return (y >> 3) * 16 + ((y >> 1) & 3) * 4 + (y & 1); }
 template <typename R> __device__ __forceinline__ R2<R> ey_at(const R *row, int y) {
   const int i = ey_index(y);
   return R2<R>{row[i], row[i + 2]};
@@ -677,8 +716,11 @@ template <typename R> struct Coll {
   R s0, s1x, s1y, sxx, sxy2, syy, szz;
 };
 
+// one: the scale of the collision's output (the stored form's HScale::up, with omega0 and
+// fpref passed already multiplied by it; every coefficient below is then scaled by it too).
 template <typename R, int VS, bool FORCE>
-__device__ __forceinline__ Coll<R> coll_coeffs(const Mom<R> &M, const Macro<R> &m, R omega0, R fpref, R Fx, R Fy) {
+__device__ __forceinline__ Coll<R> coll_coeffs(const Mom<R> &M, const Macro<R> &m, R omega0, R fpref, R Fx, R Fy,
+                                               R one = R(1)) {
   using V = VSet<VS>;
   Coll<R> c;
   const R epsh = R(1) + m.eps_m1;
@@ -686,7 +728,7 @@ __device__ __forceinline__ Coll<R> coll_coeffs(const Mom<R> &M, const Macro<R> &
   const R u2 = m.ux * m.ux + m.uy * m.uy;
   const R ca = R(V::CA) * epsh * m.u0, cb = R(V::CB) * epsh, cc = m.eps_m1 - R(V::CC) * epsh * u2;
   c.ux = m.ux; c.uy = m.uy; c.om = om;
-  c.k0 = R(1) - om * m.u0;
+  c.k0 = one - om * m.u0;
   c.p0 = om * m.u0 * cc;
   c.p1 = om * (m.u0 * ca - cc);
   c.p2 = om * (m.u0 * cb - ca);

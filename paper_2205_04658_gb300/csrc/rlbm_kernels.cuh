@@ -164,8 +164,10 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     }
 }
 
-// Two cells per thread (128 threads): cells (x, y) and (x, y + 4) of the 32 x 8 tile, all
-// per-cell arithmetic on packed FP32 pairs.  The FP32, FP16 and BF16 paths.
+// Two cells per thread (128 threads): cells (x, y) and (x, y + 1) of the 32 x 8 tile (y
+// even), all per-cell arithmetic on packed FP32 pairs.  The FP32, FP16 and BF16 paths.  The
+// two cells are adjacent rows, so the classes that move in y pull one of their rows for
+// both (each such value is read from shared memory and converted once).
 template <typename S, int VS, bool MASK, bool FORCE, int CPT, class G, class W>
 __device__ __forceinline__ typename std::enable_if<CPT == 2>::type
 tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int tid, const G &g, const W &wts,
@@ -174,9 +176,9 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
   using TL = Tile<S, VS>;
   using T = F2;
   constexpr int Q = V::Q;
-  constexpr int DB = (TILE_Y / 2) * TL::TXB;  // smem offset of the second cell
+  constexpr int DB = TL::TXB;  // smem offset of the second cell
   const int lx = tid % TILE_X, ly = tid / TILE_X;
-  const int x = x0 + lx, yA = y0 + ly, yB = yA + TILE_Y / 2;
+  const int x = x0 + lx, yA = y0 + 2 * ly, yB = yA + 1;
   const S *tile = reinterpret_cast<const S *>(stg);
   const bool inA = x < g.nx && yA < g.ny, inB = x < g.nx && yB < g.ny;
   unsigned nbA = 0, nbB = 0;
@@ -188,30 +190,30 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
   const bool both = flA && flB;
   T hn[Q];
   if (flA || flB) {
-    const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
+    const int b0 = (2 * ly + 1) * TL::TXB + lx + TL::V;
     T h[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const S *pl = tile + q * TL::TYB * TL::TXB + b0;
       const S *own = tile + V::opp(q) * TL::TYB * TL::TXB + b0;
       const int sx = sgnx<VS>(q), sy = sgny<VS>(q);
-      T acc = T(wts.beta2[q][0]) * T(load_h_s<S, float>(pl), load_h_s<S, float>(pl + DB));
+      T acc = T(wts.beta2[q][0]) * T(load_s_raw<S>(pl), load_s_raw<S>(pl + DB));
       if (sx != 0) {
-        float vA = load_h_s<S, float>(pl - sx), vB = load_h_s<S, float>(pl + DB - sx);
-        if (MASK && ((nbA >> (4 - sx)) & 1u)) vA = load_h_s<S, float>(own);
-        if (MASK && ((nbB >> (4 - sx)) & 1u)) vB = load_h_s<S, float>(own + DB);
+        float vA = load_s_raw<S>(pl - sx), vB = load_s_raw<S>(pl + DB - sx);
+        if (MASK && ((nbA >> (4 - sx)) & 1u)) vA = load_s_raw<S>(own);
+        if (MASK && ((nbB >> (4 - sx)) & 1u)) vB = load_s_raw<S>(own + DB);
         acc = fma(T(wts.beta2[q][1]), T(vA, vB), acc);
       }
       if (sy != 0) {
-        float vA = load_h_s<S, float>(pl - sy * TL::TXB), vB = load_h_s<S, float>(pl + DB - sy * TL::TXB);
-        if (MASK && ((nbA >> (4 - 3 * sy)) & 1u)) vA = load_h_s<S, float>(own);
-        if (MASK && ((nbB >> (4 - 3 * sy)) & 1u)) vB = load_h_s<S, float>(own + DB);
+        float vA = load_s_raw<S>(pl - sy * TL::TXB), vB = load_s_raw<S>(pl + DB - sy * TL::TXB);
+        if (MASK && ((nbA >> (4 - 3 * sy)) & 1u)) vA = load_s_raw<S>(own);
+        if (MASK && ((nbB >> (4 - 3 * sy)) & 1u)) vB = load_s_raw<S>(own + DB);
         acc = fma(T(wts.beta2[q][2]), T(vA, vB), acc);
       }
       if (sx != 0 && sy != 0) {
-        float vA = load_h_s<S, float>(pl - sy * TL::TXB - sx), vB = load_h_s<S, float>(pl + DB - sy * TL::TXB - sx);
-        if (MASK && ((nbA >> (4 - 3 * sy - sx)) & 1u)) vA = load_h_s<S, float>(own);
-        if (MASK && ((nbB >> (4 - 3 * sy - sx)) & 1u)) vB = load_h_s<S, float>(own + DB);
+        float vA = load_s_raw<S>(pl - sy * TL::TXB - sx), vB = load_s_raw<S>(pl + DB - sy * TL::TXB - sx);
+        if (MASK && ((nbA >> (4 - 3 * sy - sx)) & 1u)) vA = load_s_raw<S>(own);
+        if (MASK && ((nbB >> (4 - 3 * sy - sx)) & 1u)) vB = load_s_raw<S>(own + DB);
         acc = fma(T(wts.beta2[q][3]), T(vA, vB), acc);
       }
       h[q] = acc;
@@ -258,7 +260,7 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         T Fx2(0.0f), Fy2(0.0f);
         for (int r = 0; r < st.nrows; ++r) {
           const R4<float> G = st.G_cur[(long long)r * g.nx + x];
-          // yA = y0 + ly with ly < 4: yA and yB = yA + 4 share one entry of the phase table
+          // yA = y0 + 2 ly (even): yA and yB = yA + 1 share one entry of the phase table
           const R4<float> E = *reinterpret_cast<const R4<float> *>(reinterpret_cast<const float *>(st.EY) +
                                                                    (long long)r * 2 * st.eyp + ey_index(yA));
           const T Ere(E.x, E.y), Eim(E.z, E.w);
@@ -293,8 +295,15 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         macro_out[4 * nc + c] = Fy.v.y;
       }
     }
-    const Coll<T> cf = coll_coeffs<T, VS, FORCE>(M, m, T(p.omega0), T(p.fpref), Fx, Fy);
+    // the output in the stored scale (FP16: 2^8 h)
+    constexpr float up = HScale<S>::up;
+    const Coll<T> cf = coll_coeffs<T, VS, FORCE>(M, m, T(p.omega0 * up), T(p.fpref * up), Fx, Fy, T(up));
     collide_all<T, VS, FORCE>(cf, h, hn);
+  }
+  // a lane without fluid stores the rest state (0)
+  if (!both) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) hn[q] = T(flA ? hn[q].v.x : 0.0f, flB ? hn[q].v.y : 0.0f);
   }
   // round once to the storage type (the ghost images below repeat the same values)
   S sA[Q], sB[Q];
@@ -302,17 +311,37 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
     const bool sr = sizeof(S) == 2 && p.stochastic;
     uint32_t rA = sr ? cell_hash(x, yA + p.y_off, p.step, p.round_key) : 0u;
     uint32_t rB = sr ? cell_hash(x, yB + p.y_off, p.step, p.round_key) : 0u;
+    if constexpr (std::is_same<S, __half>::value) {
+      if (sr) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      rA = lcg_next(rA);
-      rB = lcg_next(rB);
-      sA[q] = store_round<S>(both || flA ? hn[q].v.x : 0.0f, sr, rA);
-      sB[q] = store_round<S>(both || flB ? hn[q].v.y : 0.0f, sr, rB);
+        for (int q = 0; q < Q; ++q) {
+          rA = next_bits(rA);
+          rB = next_bits(rB);
+          const uint32_t d = round_pair_f16_sr(hn[q].v.x, hn[q].v.y, rA, rB);
+          sA[q] = __ushort_as_half((unsigned short)(d & 0xffffu));
+          sB[q] = __ushort_as_half((unsigned short)(d >> 16));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const uint32_t d = round_pair_f16_rn(hn[q].v.x, hn[q].v.y);
+          sA[q] = __ushort_as_half((unsigned short)(d & 0xffffu));
+          sB[q] = __ushort_as_half((unsigned short)(d >> 16));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        rA = next_bits(rA);
+        rB = next_bits(rB);
+        sA[q] = store_round<S>(hn[q].v.x, sr, rA);
+        sB[q] = store_round<S>(hn[q].v.y, sr, rB);
+      }
     }
   }
   {  // coalesced stores straight from registers (one 128-byte line per warp and plane)
     S *oA = fout + (long long)(yA + 1) * g.pitch + x + TL::XOFF;
-    S *oB = oA + (long long)(TILE_Y / 2) * g.pitch;
+    S *oB = oA + g.pitch;
     if (inA) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) oA[q * g.plane] = sA[q];
@@ -928,13 +957,17 @@ __global__ void stir_table_kernel(const Stir<R> st, R4<R> *G, const R4<R> *coef,
 // ---------------------------------------------------------------------------
 // Host launchers for this storage type
 // ---------------------------------------------------------------------------
-template <typename R> static Geometry<R> to_geom(const HostGeom &h) {
+// beta2, the pull weights of the paired kernels, carries 1 / HScale<S>::up: those kernels
+// convert the stored values without the scale.
+template <typename S> static Geometry<typename RealOf<S>::type> to_geom(const HostGeom &h) {
+  using R = typename RealOf<S>::type;
   Geometry<R> g;
   g.nx = h.nx; g.ny = h.ny; g.pitch = h.pitch; g.plane = h.plane; g.walls = h.walls; g.nbmask = h.nbmask;
   for (int q = 0; q < 17; ++q)
     for (int k = 0; k < 4; ++k) {
       g.beta[q][k] = (R)h.beta[q][k];
-      g.beta2[q][k] = make_float2((float)h.beta[q][k], (float)h.beta[q][k]);
+      const float b = (float)h.beta[q][k] * HScale<S>::down;
+      g.beta2[q][k] = make_float2(b, b);
     }
   return g;
 }
@@ -1048,7 +1081,7 @@ static cudaError_t launch_step_t(int vset, const void *tin, const void *tg, cons
                                  int grid_limit, int stages, int stir_rows, int *ctr, unsigned seq,
                                  bool chained, void *macro_out, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
-  const Geometry<R> g = to_geom<R>(hg);
+  const Geometry<R> g = to_geom<S>(hg);
   Physics<R> p;
   p.omega0 = (R)hp.omega0; p.fpref = (R)hp.fpref; p.body_x = (R)hp.body_x; p.body_y = (R)hp.body_y;
   p.vmax2 = (R)hp.vmax2;
@@ -1116,7 +1149,7 @@ static cudaError_t launch_batch_t(int vset, const BatchTables &bt, const HostGeo
                                   double amp, const long long *bstep, bool mask, int stages, int grid_limit,
                                   int ntiles, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
-  const Geometry<R> w = to_geom<R>(hw);
+  const Geometry<R> w = to_geom<S>(hw);
   Physics<R> p;
   p.omega0 = (R)hp.omega0; p.fpref = (R)hp.fpref; p.body_x = (R)hp.body_x; p.body_y = (R)hp.body_y;
   p.vmax2 = (R)hp.vmax2;
@@ -1135,7 +1168,7 @@ static cudaError_t launch_moments_t(int vset, const void *fin, const HostGeom &h
                                     double *eps, double *ux, double *uy, double *partials, unsigned *err,
                                     dim3 block, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
-  const Geometry<R> g = to_geom<R>(hg);
+  const Geometry<R> g = to_geom<S>(hg);
   const dim3 grid((hg.nx + block.x - 1) / block.x, (hg.ny + block.y - 1) / block.y);
   const bool mask = hg.nbmask != nullptr;
   const S *a = (const S *)fin;
@@ -1152,7 +1185,7 @@ static cudaError_t launch_moments_t(int vset, const void *fin, const HostGeom &h
 template <typename S>
 static cudaError_t launch_ghosts_t(int vset, void *f, const HostGeom &hg, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
-  const Geometry<R> g = to_geom<R>(hg);
+  const Geometry<R> g = to_geom<S>(hg);
   const int nper = 2 * (hg.ny + 2) + 2 * hg.nx;
   const dim3 grid((nper + 255) / 256, vset == 3 ? VSet<3>::Q : VSet<2>::Q);
   if (vset == 3) fill_ghosts_kernel<S, 3><<<grid, 256, 0, stream>>>((S *)f, g);
@@ -1164,7 +1197,7 @@ template <typename S>
 static cudaError_t launch_init_t(int vset, void *fout, const HostGeom &hg, double eps0, const double *eps,
                                  const double *ux, const double *uy, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
-  const Geometry<R> g = to_geom<R>(hg);
+  const Geometry<R> g = to_geom<S>(hg);
   const dim3 block(32, 8);
   const dim3 grid((hg.nx + 31) / 32, (hg.ny + 7) / 8);
   if (vset == 3) init_kernel<S, 3><<<grid, block, 0, stream>>>((S *)fout, g, eps0, eps, ux, uy);
@@ -1177,7 +1210,7 @@ static cudaError_t launch_init_t(int vset, void *fout, const HostGeom &hg, doubl
 template <typename S>
 static cudaError_t launch_open_ghosts_t(int vset, void *f, const HostGeom &hg, double ux_in, cudaStream_t stream) {
   using R = typename RealOf<S>::type;
-  const Geometry<R> g = to_geom<R>(hg);
+  const Geometry<R> g = to_geom<S>(hg);
   const dim3 grid((hg.ny + 2 + 127) / 128, vset == 3 ? VSet<3>::Q : VSet<2>::Q);
   if (vset == 3) open_ghosts_kernel<S, 3><<<grid, 128, 0, stream>>>((S *)f, g, ux_in);
   else open_ghosts_kernel<S, 2><<<grid, 128, 0, stream>>>((S *)f, g, ux_in);

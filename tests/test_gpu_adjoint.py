@@ -197,20 +197,32 @@ def _objectives_fp64(R, nx, ny, nsteps, runs):
     return acc / (nsteps * nx * ny)
 
 
+# The FP32 body-force gradient is a sum over all cells and steps of the force adjoint whose
+# terms cancel: at 512^2 x 2000 the sum of their magnitudes is 6.4e3 times the sum itself
+# (measured on a GB300).  A relative rounding of 2^-24 shared by the terms (an FP32 constant, a
+# step of the same arithmetic in every cell) therefore moves the sum by 3.8e-4 of itself, and
+# the FP32 adjoint lands 1e-4 to 5e-4 from the FP64 one depending on the order of its
+# arithmetic.  Bar: 2e-3, five times that unit.  The FP64 adjoint meets 1e-4 on every gradient.
+F32_BODY_FORCE_TOL = 2e-3
+
+
 def test_adjoint_512_matches_central_differences(R):
     """The stirred 512 x 512 workload (shell 4 <= |k| <= 6, 34 modes, amplitude 1e-4,
-    seed 5, eta/s 0.05), 2000 steps, sqrt(N) checkpoints: the FP32 adjoint against
-    central differences of the FP64 forward objective (h = 1e-4 relative) for every one of
-    the 34 mode multipliers, eta/s and the body force.  Bars: each mode within 1e-4 of the
-    largest mode gradient (a mode whose gradient is far below the others cannot be resolved
-    to 1e-4 of itself by differences of J), the three largest within 1e-4 of themselves,
-    and eta/s and the body force within 1e-4 of themselves."""
+    seed 5, eta/s 0.05), 2000 steps, sqrt(N) checkpoints, against central differences of
+    the FP64 forward objective (h = 1e-4 relative) for every one of the 34 mode multipliers,
+    eta/s and the body force.
+    FP64 adjoint: every gradient within 1e-4 of its own difference quotient.
+    FP32 adjoint: each mode within 1e-4 of the largest mode gradient (a mode whose gradient
+    is far below the others cannot be resolved to 1e-4 of itself by FP32 arithmetic), the
+    three largest and eta/s within 1e-4 of themselves, the body force within
+    F32_BODY_FORCE_TOL of itself."""
     nx = ny = 512
     N = 2000
     kw = dict(eta_over_s=0.05, kmin=4, kmax=6, force_amp=1e-4, seed=5)
-    J, gs, ge, gb = _gpu_grad(R, dict(nx=nx, ny=ny, **kw), N, "f32")
-    nm = gs.size
-    assert nm == 34
+    J32, gs32, ge32, gb32 = _gpu_grad(R, dict(nx=nx, ny=ny, **kw), N, "f32")
+    J64, gs64, ge64, gb64 = _gpu_grad(R, dict(nx=nx, ny=ny, **kw), N, "f64")
+    nm = gs32.size
+    assert nm == 34 and gs64.size == 34
     runs = []
     for m in range(nm):
         for sgn in (1.0, -1.0):
@@ -222,14 +234,20 @@ def test_adjoint_512_matches_central_differences(R):
              (dict(kw, body_force=(hb, 0.0)), None), (dict(kw, body_force=(-hb, 0.0)), None)]
     Js = _objectives_fp64(R, nx, ny, N, runs)
     fd = (Js[0:2 * nm:2] - Js[1:2 * nm:2]) / 2e-4
-    err = np.abs(gs - fd)
-    print("mode gradients: max |adjoint - FD| / max |FD| = %.2e (max |FD| %.3e, min |FD| %.3e)"
-          % (err.max() / np.abs(fd).max(), np.abs(fd).max(), np.abs(fd).min()))
-    assert err.max() <= 1e-4 * np.abs(fd).max()
-    for m in np.argsort(-np.abs(fd))[:3]:
-        assert err[m] <= 1e-4 * abs(fd[m]), (m, gs[m], fd[m])
     fde = (Js[2 * nm] - Js[2 * nm + 1]) / (2 * h)
     fdb = (Js[2 * nm + 2] - Js[2 * nm + 3]) / (2 * hb)
-    print("eta/s: %.6e vs FD %.6e; body force: %.6e vs FD %.6e" % (ge, fde, gb[0], fdb))
-    assert abs(ge - fde) <= 1e-4 * abs(fde), (ge, fde)
-    assert abs(gb[0] - fdb) <= 1e-4 * abs(fdb), (gb[0], fdb)
+    err64 = np.abs(gs64 - fd) / np.abs(fd)
+    err32 = np.abs(gs32 - fd)
+    print("FP64: modes max |adjoint - FD| / |FD| = %.2e; eta/s %.2e; body force %.2e"
+          % (err64.max(), abs(ge64 - fde) / abs(fde), abs(gb64[0] - fdb) / abs(fdb)))
+    print("FP32: modes max |adjoint - FD| / max |FD| = %.2e (max |FD| %.3e, min |FD| %.3e); eta/s %.2e; "
+          "body force %.2e" % (err32.max() / np.abs(fd).max(), np.abs(fd).max(), np.abs(fd).min(),
+                               abs(ge32 - fde) / abs(fde), abs(gb32[0] - fdb) / abs(fdb)))
+    assert err64.max() <= 1e-4
+    assert abs(ge64 - fde) <= 1e-4 * abs(fde), (ge64, fde)
+    assert abs(gb64[0] - fdb) <= 1e-4 * abs(fdb), (gb64[0], fdb)
+    assert err32.max() <= 1e-4 * np.abs(fd).max()
+    for m in np.argsort(-np.abs(fd))[:3]:
+        assert err32[m] <= 1e-4 * abs(fd[m]), (m, gs32[m], fd[m])
+    assert abs(ge32 - fde) <= 1e-4 * abs(fde), (ge32, fde)
+    assert abs(gb32[0] - fdb) <= F32_BODY_FORCE_TOL * abs(fdb), (gb32[0], fdb)
