@@ -327,13 +327,12 @@ RLBM_API rlbm_status rlbm_set_mode_scale(rlbm_ctx *ctx, const double *sigma, int
  * rlbm_gradient runs the nsteps forward steps (the context ends at s0 + nsteps, exactly as
  * after rlbm_step(ctx, nsteps)), keeping the post-collision state every `segment` steps
  * (0: ceil(sqrt(nsteps))), then the hand-written adjoint backwards, recomputing each
- * segment from its checkpoint: about 2 sqrt(nsteps) states of memory and one extra
- * forward pass.  The recomputation also keeps, for every step of the segment in hand, the
- * step's Landau solution and force (5 values per cell), which the reverse steps read.
- * segment >= nsteps keeps every state instead (one segment; about nsteps states and
- * nsteps sets of those values, e.g. 54 GB for 512^2 FP32 and 2000 steps): the forward runs
- * once, keeping what the reverse steps read, and no step is recomputed.  The results do
- * not depend on segment.  It returns J and dJ/dsigma_m (host, rlbm_num_modes values; may be NULL),
+ * segment from its checkpoint: about sqrt(nsteps) states of memory and one extra forward
+ * pass.  The recomputation keeps, for every step of the segment in hand, the step's Landau
+ * solution, force and streamed deviations h (5 + 17 values per cell for the paper's set,
+ * in the storage type), which the reverse steps read.  segment >= nsteps keeps those
+ * values for every step instead (one segment, e.g. 46 GB for 512^2 FP32 and 2000 steps):
+ * the forward runs once and no step is recomputed.  The results do not depend on segment.  It returns J and dJ/dsigma_m (host, rlbm_num_modes values; may be NULL),
  * dJ/d(eta/s) (host, 1; may be NULL) and dJ/dF_body (host, 2; may be NULL; zero for the
  * eight-direction set, which has no force term), evaluated at
  * the current sigma, eta/s and body force.  FP64 and FP32 storage only (E_INVAL for the

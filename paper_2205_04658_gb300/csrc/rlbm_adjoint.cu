@@ -55,7 +55,7 @@ __device__ __forceinline__ void pull_staged(const T *tile, int plane, int txb, i
   }
 }
 
-// The same two pulls for the two cells (x, y) and (x, y + 4) of a thread (db = the staged offset
+// The same two pulls for the two cells (x, y) and (x, y + 1) of a thread (db = the staged offset
 // of the second cell), as packed FP32 pairs: the FP32 reverse step.
 template <int VS, bool MASK, int SIGN>
 __device__ __forceinline__ void pull_staged_pair(const float *tile, int plane, int txb, int b0, int db,
@@ -237,18 +237,19 @@ __device__ __forceinline__ void cell_adjoint(const R h[VSet<VS>::Q], const R lam
 }
 
 // One adjoint step over the lattice.  Persistent CTAs of 256 threads (one cell each) walk
-// the 32 x 8 tiles (tile t to CTA t mod grid); per tile one TMA box stages B_{n-1} with its
-// one-cell halo and (LAM) a second one kappa_{n+1}, two stages rotating on mbarriers with
-// bounded waits, as in the forward step kernel.
-//   tB    load map of the post-collision buffer B_{n-1} of the forward run
-//   tK    load map of kappa_{n+1} (unused when LAM is false: the last state, objective only)
+// the 32 x 8 tiles (tile t to CTA t mod grid); per tile one TMA box stages kappa_{n+1} (LAM)
+// or, for the last state, B_{n-1}, with its one-cell halo, two stages rotating on mbarriers
+// with bounded waits, as in the forward step kernel.
+//   tB    load map of the post-collision buffer B_{n-1} of the forward run (used when LAM is
+//         false: the last state, objective only, whose h is pulled and matched here)
+//   tK    load map of kappa_{n+1} (LAM)
 //   kout  kappa_n; ghost cells are written like the forward's (periodic copies)
 //   cj    objective weight of S_n (1 / (N N_fluid), or 0 for the first state)
 //   acc   per-tile FP64 sums, accumulated over steps: d/d(ln omega0), F adjoint x, y, J
 //   zpart per tile row and k_y row r: sum over the tile's 8 rows of gF(x, y) EY_r(y)
-//   macro the step's eps/eps0 - 1, v_x, v_y, F_x, F_y per cell (5 planes of nx * ny) as the
-//         forward step kernel computed them when it recomputed the step, or NULL: Landau
-//         matching and the force synthesis are then done here
+//   macro (LAM) the step's eps/eps0 - 1, v_x, v_y, F_x, F_y and streamed h per cell (5 + Q
+//         planes of nx * ny) as the forward step kernel computed them when it recomputed the
+//         step; without LAM, Landau matching and the force synthesis are done here
 template <typename S, int VS, bool MASK, bool FORCE, bool LAM, int NST>
 __global__ void __launch_bounds__(256)
 adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tK,
@@ -261,7 +262,7 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
   static_assert(sizeof(S) == sizeof(R), "the adjoint runs on FP32 or FP64 storage");
   constexpr int Q = VSet<VS>::Q;
   constexpr int PL = TL::TYB * TL::TXB;  // elements of a staged plane
-  constexpr int STAGE = TL::IN_STRIDE * (LAM ? 2 : 1);
+  constexpr int STAGE = TL::IN_STRIDE;  // kappa_{n+1} (LAM) or B_{n-1}
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
@@ -272,7 +273,7 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
   const int wid = blockIdx.x, nworkers = gridDim.x;
   const int ntx = (g.nx + 31) / 32, ntiles = ntx * ((g.ny + 7) / 8);
   const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
-  const uint32_t stage_bytes = TL::IN_BYTES * (LAM ? 2 : 1);
+  const uint32_t stage_bytes = TL::IN_BYTES;
   if (tid == 0) {
     for (int s2 = 0; s2 < NST; ++s2) mbar_init(&bar[s2], 1);
     fence_mbar_init();
@@ -280,6 +281,7 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
   __syncthreads();
   // thread 0: the k-th tile of this CTA into stage k % NST (B, then kappa, on one barrier)
   auto issue_B = [&](int k) {
+    if (LAM) return;
     const int t = wid + k * nworkers;
     const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
     uint64_t *b = &bar[k % NST];
@@ -290,12 +292,14 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
     if (!LAM) return;
     const int t = wid + k * nworkers;
     const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
-    tma_load_3d(smem + (k % NST) * STAGE + TL::IN_STRIDE, &tK, &bar[k % NST], x0 + TL::XOFF - TL::V, y0, 0);
+    uint64_t *b = &bar[k % NST];
+    mbar_expect_tx(b, stage_bytes);
+    tma_load_3d(smem + (k % NST) * STAGE, &tK, b, x0 + TL::XOFF - TL::V, y0, 0);
   };
   auto issue = [&](int k) { issue_B(k); issue_K(k); };
-  // B_{n-1} was written before the reverse sweep of its segment began, so its first tiles
+  // B_{n-1} (the last state) was written before the reverse sweep began, so its first tiles
   // are copied at once; a launch chained to the previous reverse step (programmatic
-  // dependent launch) then waits for that step's kappa_{n+1}, and writes nothing before.
+  // dependent launch) waits for that step's kappa_{n+1}, and writes nothing before.
   if (tid == 0)
     for (int k = 0; k < NST && k < my_tiles; ++k) issue_B(k);
   griddep_wait();
@@ -312,8 +316,8 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
     const int t = wid + k * nworkers;
     const int tx = t % ntx, ty = t / ntx;
     const int x = tx * TILE_X + lx, y = ty * TILE_Y + ly;
-    const S *tileB = reinterpret_cast<const S *>(smem + (k % NST) * STAGE);
-    const R *tileK = reinterpret_cast<const R *>(smem + (k % NST) * STAGE + TL::IN_STRIDE);
+    const S *tileB = reinterpret_cast<const S *>(smem + (k % NST) * STAGE);  // without LAM
+    const R *tileK = reinterpret_cast<const R *>(smem + (k % NST) * STAGE);  // LAM
     const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
     const bool inside = x < g.nx && y < g.ny;
     unsigned nb = 0;
@@ -332,25 +336,25 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
       eyv = ey_at<R>(reinterpret_cast<const R *>(st.EY) + (long long)(tid >> 3) * 2 * st.eyp, ty * TILE_Y + (tid & 7));
     if (fluid) {
       R h[Q], lam[Q];
-      // the forward's Landau solution and force of this cell, loaded first so that the
-      // loads overlap the pulls
+      // the forward's Landau solution, force and streamed h of this cell, loaded first so
+      // that the loads overlap the pull
       R mv[5] = {R(0), R(0), R(0), R(0), R(0)};
-      if (macro) {
+      if (LAM) {
         const long long nc = (long long)g.nx * g.ny, c = (long long)y * g.nx + x;
 #pragma unroll
         for (int k = 0; k < 5; ++k) mv[k] = macro[k * nc + c];
-      }
-      pull_staged<R, VS, MASK, -1>(reinterpret_cast<const R *>(tileB), PL, TL::TXB, b0, g, nb, h);
-      if (LAM) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) h[q] = macro[(5 + q) * nc + c];
         pull_staged<R, VS, MASK, 1>(tileK, PL, TL::TXB, b0, g, nb, lam);
       } else {
+        pull_staged<R, VS, MASK, -1>(reinterpret_cast<const R *>(tileB), PL, TL::TXB, b0, g, nb, h);
 #pragma unroll
         for (int q = 0; q < Q; ++q) lam[q] = R(0);
       }
       const Mom<R> M = moments_of<R, R, VS, FORCE>(h);
       Macro<R> m;
       R Fx = p.body_x, Fy = p.body_y;
-      if (macro) {
+      if (LAM) {
         // u^mu = gamma (1, v) as the step kernel forms it from v
         const R gam = FM<R>::rsqrt(R(1) - fma(mv[1], mv[1], mv[2] * mv[2]));
         m.eps_m1 = mv[0];
@@ -366,7 +370,7 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
         m = cell_macro<R, VS>(h, M, p.vmax2);
         if (!m.ok) atomicOr(err, (R(1) + m.eps_m1 > R(0) && isfinite(m.eps_m1)) ? ERR_UNPHYSICAL : ERR_UNSTABLE);
       }
-      if (FORCE && !macro) {
+      if (FORCE && !LAM) {
         // two rows per iteration, in two partial sums: both rows' loads are in flight at once
         const R *ey = reinterpret_cast<const R *>(st.EY);
         R Fx2 = R(0), Fy2 = R(0);
@@ -467,7 +471,7 @@ adjoint_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constant__ C
   }
 }
 
-// The FP32 reverse step with two cells per thread (128 threads): cells (x, y) and (x, y + 4) of
+// The FP32 reverse step with two cells per thread (128 threads): cells (x, y) and (x, y + 1) of
 // the 32 x 8 tile, the pulls, moments, the cell's reverse and the objective on packed FP32
 // pairs, as the forward step kernel computes its FP32 paths.  Tile walk, staging, chaining,
 // stores, row projections and tile sums as in adjoint_kernel.
@@ -481,8 +485,8 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
   using T = F2;
   constexpr int Q = VSet<VS>::Q;
   constexpr int PL = TL::TYB * TL::TXB;  // elements of a staged plane
-  constexpr int STAGE = TL::IN_STRIDE * (LAM ? 2 : 1);
-  constexpr int DB = (TILE_Y / 2) * TL::TXB;  // staged offset of a thread's second cell
+  constexpr int STAGE = TL::IN_STRIDE;  // kappa_{n+1} (LAM) or B_{n-1}
+  constexpr int DB = TL::TXB;  // staged offset of a thread's second cell (the next row)
   constexpr int NT = 128;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -494,13 +498,14 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
   const int wid = blockIdx.x, nworkers = gridDim.x;
   const int ntx = (g.nx + 31) / 32, ntiles = ntx * ((g.ny + 7) / 8);
   const int my_tiles = wid < ntiles ? (ntiles - 1 - wid) / nworkers + 1 : 0;
-  const uint32_t stage_bytes = TL::IN_BYTES * (LAM ? 2 : 1);
+  const uint32_t stage_bytes = TL::IN_BYTES;
   if (tid == 0) {
     for (int s2 = 0; s2 < NST; ++s2) mbar_init(&bar[s2], 1);
     fence_mbar_init();
   }
   __syncthreads();
   auto issue_B = [&](int k) {
+    if (LAM) return;
     const int t = wid + k * nworkers;
     const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
     uint64_t *b = &bar[k % NST];
@@ -511,7 +516,9 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
     if (!LAM) return;
     const int t = wid + k * nworkers;
     const int x0 = (t % ntx) * TILE_X, y0 = (t / ntx) * TILE_Y;
-    tma_load_3d(smem + (k % NST) * STAGE + TL::IN_STRIDE, &tK, &bar[k % NST], x0 + TL::XOFF - TL::V, y0, 0);
+    uint64_t *b = &bar[k % NST];
+    mbar_expect_tx(b, stage_bytes);
+    tma_load_3d(smem + (k % NST) * STAGE, &tK, b, x0 + TL::XOFF - TL::V, y0, 0);
   };
   auto issue = [&](int k) { issue_B(k); issue_K(k); };
   if (tid == 0)
@@ -530,10 +537,10 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
     if (tid == 0 && k == my_tiles - 1) griddep_launch_dependents();
     const int t = wid + k * nworkers;
     const int tx = t % ntx, ty = t / ntx;
-    const int x = tx * TILE_X + lx, yA = ty * TILE_Y + ly, yB = yA + TILE_Y / 2;
-    const float *tileB = reinterpret_cast<const float *>(smem + (k % NST) * STAGE);
-    const float *tileK = reinterpret_cast<const float *>(smem + (k % NST) * STAGE + TL::IN_STRIDE);
-    const int b0 = (ly + 1) * TL::TXB + lx + TL::V;
+    const int x = tx * TILE_X + lx, yA = ty * TILE_Y + 2 * ly, yB = yA + 1;
+    const float *tileB = reinterpret_cast<const float *>(smem + (k % NST) * STAGE);  // without LAM
+    const float *tileK = reinterpret_cast<const float *>(smem + (k % NST) * STAGE);  // LAM
+    const int b0 = (2 * ly + 1) * TL::TXB + lx + TL::V;
     const bool inA = x < g.nx && yA < g.ny, inB = x < g.nx && yB < g.ny;
     unsigned nbA = 0, nbB = 0;
     if (MASK) {
@@ -555,24 +562,31 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
     for (int q = 0; q < Q; ++q) kap[q] = T(0.0f);
     if (flA || flB) {
       T h[Q], lam[Q];
-      // the forward's Landau solution and force of the two cells, loaded first so that the
-      // loads overlap the pulls
+      // the forward's Landau solution, force and streamed h of the two cells, loaded first
+      // so that the loads overlap the pull
       float mA[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, mB[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-      if (macro) {
-        const long long nc = (long long)g.nx * g.ny;
+      if (LAM) {
+        const long long nc = (long long)g.nx * g.ny, cA = (long long)yA * g.nx + x, cB = (long long)yB * g.nx + x;
+        float hA[Q], hB[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) hA[q] = hB[q] = 0.0f;
         if (flA) {
 #pragma unroll
-          for (int j = 0; j < 5; ++j) mA[j] = macro[j * nc + (long long)yA * g.nx + x];
+          for (int j = 0; j < 5; ++j) mA[j] = macro[j * nc + cA];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) hA[q] = macro[(5 + q) * nc + cA];
         }
         if (flB) {
 #pragma unroll
-          for (int j = 0; j < 5; ++j) mB[j] = macro[j * nc + (long long)yB * g.nx + x];
+          for (int j = 0; j < 5; ++j) mB[j] = macro[j * nc + cB];
+#pragma unroll
+          for (int q = 0; q < Q; ++q) hB[q] = macro[(5 + q) * nc + cB];
         }
-      }
-      pull_staged_pair<VS, MASK, -1>(tileB, PL, TL::TXB, b0, DB, g, nbA, nbB, h);
-      if (LAM) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) h[q] = T(hA[q], hB[q]);
         pull_staged_pair<VS, MASK, 1>(tileK, PL, TL::TXB, b0, DB, g, nbA, nbB, lam);
       } else {
+        pull_staged_pair<VS, MASK, -1>(tileB, PL, TL::TXB, b0, DB, g, nbA, nbB, h);
 #pragma unroll
         for (int q = 0; q < Q; ++q) lam[q] = T(0.0f);
       }
@@ -586,7 +600,7 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
       const Mom<T> M = moments_of<T, T, VS, FORCE>(h);
       Macro<T> m;
       T Fx(p.body_x), Fy(p.body_y);
-      if (macro) {
+      if (LAM) {
         // u^mu = gamma (1, v) as the step kernel forms it from v
         const T vx(mA[1], mB[1]), vy(mA[2], mB[2]);
         const T gam = FM<T>::rsqrt(T(1.0f) - fma(vx, vx, vy * vy));
@@ -636,8 +650,8 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
     }
     // projections of the force adjoint on the k_y rows of the stirring tables
     if (FORCE && st.nrows > 0) {
-      sF[ly][lx] = R2<float>{gFx.v.x, gFy.v.x};
-      sF[ly + TILE_Y / 2][lx] = R2<float>{gFx.v.y, gFy.v.y};
+      sF[2 * ly][lx] = R2<float>{gFx.v.x, gFy.v.x};
+      sF[2 * ly + 1][lx] = R2<float>{gFx.v.y, gFy.v.y};
       if (tid < ney) sE[tid >> 3][tid & 7] = ey0;
       if (tid + NT < ney) sE[(tid + NT) >> 3][tid & 7] = ey1;
       __syncthreads();
@@ -799,7 +813,7 @@ static cudaError_t launch_adjoint_k(const AdjointArgs &a, const Geometry<typenam
   constexpr bool PAIR = sizeof(S) == 4;
   constexpr int NT = PAIR ? 128 : 256;
   auto kern = pick_adjoint_kernel<S, VS, MASK, FORCE, LAM, NST>();
-  const int smem = NST * TL::IN_STRIDE * (LAM ? 2 : 1) + 64 + 128;
+  const int smem = NST * TL::IN_STRIDE + 64 + 128;
   static int configured_dev = -1, max_blocks = 0, sms = 0;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -846,7 +860,10 @@ static cudaError_t launch_adjoint_v(const AdjointArgs &a, const Geometry<typenam
   s.G = (const R4<R> *)a.G;
   s.EY = (const R2<R> *)a.EY;
   s.eyp = a.eyp;
-  if (a.kin) return launch_adjoint_k<S, VS, MASK, FORCE, true>(a, g, p, s, st);
+  if (a.kin) {
+    if (!a.macro) return cudaErrorInvalidValue;  // a reverse step reads its forward step's stored values
+    return launch_adjoint_k<S, VS, MASK, FORCE, true>(a, g, p, s, st);
+  }
   return launch_adjoint_k<S, VS, MASK, FORCE, false>(a, g, p, s, st);
 }
 

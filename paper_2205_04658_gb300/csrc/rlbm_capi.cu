@@ -1272,7 +1272,7 @@ GradLayout grad_layout(const rlbm_ctx *c, int64_t N, int32_t segment) {
   G.seg = segment > 0 ? segment : std::max(1, (int)std::ceil(std::sqrt((double)N)));
   if (G.seg > N) G.seg = (int)N;
   G.K = (int)((N + G.seg - 1) / G.seg);
-  G.nslots = G.seg - 1;
+  G.nslots = std::min(2, G.seg - 1);  // ping-pong states of a segment's recomputation
   const int prec = c->cfg.precision;
   const size_t rb = real_bytes(prec);
   G.state_bytes = align_up(store_bytes(prec) * c->L.Q * c->L.plane);
@@ -1296,8 +1296,9 @@ GradLayout grad_layout(const rlbm_ctx *c, int64_t N, int32_t segment) {
   G.gstep = take(8 * (size_t)c->L.nmodes * (size_t)N);
   G.gsig = take(8 * (size_t)c->L.nmodes);
   G.out = take(64);
-  // each recomputed step's eps/eps0 - 1, v_x, v_y, F_x, F_y per cell, for the reverse sweep
-  G.macro_bytes = align_up(5 * rb * (size_t)c->cfg.nx * c->cfg.ny);
+  // each recomputed step's eps/eps0 - 1, v_x, v_y, F_x, F_y and streamed h_q per cell, for the
+  // reverse sweep
+  G.macro_bytes = align_up((5 + (size_t)c->L.Q) * rb * (size_t)c->cfg.nx * c->cfg.ny);
   G.macro = take(G.macro_bytes * G.seg);
   G.scratch = take(G.state_bytes);   // output of the last recomputed step of a segment (unused)
   G.gscratch = take(G.table_bytes);  // and the stirring rows it prepares for the next step
@@ -1457,8 +1458,10 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   mg.amp = c->cfg.force_amp;
   double *gstep = reinterpret_cast<double *>(w + G.gstep), *gsig = reinterpret_cast<double *>(w + G.gsig);
   const double cj = 1.0 / ((double)nsteps * (double)c->nfluid);
-  // stirring rows of steps lo .. hi-1 of segment k into the segment's table store, and the
-  // states B_lo .. B_{hi-2} from checkpoint k into the slots (B_{hi-1} into the scratch state)
+  // stirring rows of steps lo .. hi-1 of segment k into the segment's table store, and each
+  // step's stored values (Landau solution, force, streamed h) into its slot of G.macro; the
+  // states B_lo .. B_{hi-2} alternate between the two ping-pong slots (B_{hi-1} goes to the
+  // scratch state)
   auto recompute = [&](int k, int64_t lo, int64_t hi) -> cudaError_t {
     cudaError_t e2;
     if (c->L.nmodes) {
@@ -1468,17 +1471,17 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
                                         : launch_stir_prime_f32(sp, cn, cn1, gtab(0), c->cfg.nx, s0 + lo, c->stream);
       if (e2 != cudaSuccess) return e2;
     }
-    // steps lo .. hi-1 again, each keeping its cells' Landau solution and force for the
-    // reverse step of the same index (the last one's state and next rows are not needed)
+    // steps lo .. hi-1 again, each keeping its cells' Landau solution, force and streamed h
+    // for the reverse step of the same index (the last one's state and next rows are not needed)
     for (int64_t n = lo; n <= hi - 1; ++n) {
-      const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
+      const CUtensorMap *ti = n == lo ? &mck[k] : &msl[(int)((n - lo - 1) & 1)];
       HostStir st = stir_for_step(c, s0 + n);
       if (c->L.nmodes) {
         st.G_cur = gtab((int)(n - lo));
         st.G_next = n == hi - 1 ? w + G.gscratch : gtab((int)(n - lo + 1));
       }
       c->phys.step = s0 + n;
-      void *fout = n == hi - 1 ? w + G.scratch : slot((int)(n - lo));
+      void *fout = n == hi - 1 ? w + G.scratch : slot((int)((n - lo) & 1));
       if ((e2 = dispatch_step_raw(c, ti, fout, s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr, n > lo,
                                   w + G.macro + G.macro_bytes * (size_t)(n - lo))) != cudaSuccess)
         return e2;
@@ -1510,8 +1513,8 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
     const int64_t lo = (int64_t)k * G.seg, hi = std::min<int64_t>(lo + G.seg, nsteps);
     if (!one_pass && (e = recompute(k, lo, hi)) != cudaSuccess) return c->cuda_fail(e, "step kernel launch (recompute)");
     for (int64_t n = hi - 1; n >= lo; --n) {
-      a.B = n == lo ? ckpt(k) : slot((int)(n - lo - 1));
-      a.tB = n == lo ? &mck[k] : &msl[(int)(n - lo - 1)];
+      a.B = ckpt(k);  // (not read: the step's streamed h is in its stored values)
+      a.tB = &mck[k];
       a.kin = w + G.kap[kc];
       a.tK = &mkap[kc];
       a.kout = w + G.kap[kc ^ 1];

@@ -129,13 +129,15 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
           }
         }
       }
-      if (macro_out) {  // the cell's Landau solution and force, kept for the reverse sweep
+      if (macro_out) {  // the cell's Landau solution, force and streamed h, kept for the reverse sweep
         const long long nc = (long long)g.nx * g.ny, c = (long long)y * g.nx + x;
         macro_out[c] = m.eps_m1;
         macro_out[nc + c] = m.vx;
         macro_out[2 * nc + c] = m.vy;
         macro_out[3 * nc + c] = Fx;
         macro_out[4 * nc + c] = Fy;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) macro_out[(5 + q) * nc + c] = h[q];
       }
       const Coll<R> cf = coll_coeffs<R, VS, FORCE>(M, m, p.omega0, p.fpref, Fx, Fy);
       collide_all<R, VS, FORCE>(cf, h, hn);
@@ -276,7 +278,7 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         Fy += Fy2;
       }
     }
-    if (macro_out) {  // the cells' Landau solutions and forces, kept for the reverse sweep
+    if (macro_out) {  // the cells' Landau solutions, forces and streamed h, kept for the reverse sweep
       const long long nc = (long long)g.nx * g.ny;
       if (flA) {
         const long long c = (long long)yA * g.nx + x;
@@ -285,6 +287,8 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         macro_out[2 * nc + c] = m.vy.v.x;
         macro_out[3 * nc + c] = Fx.v.x;
         macro_out[4 * nc + c] = Fy.v.x;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) macro_out[(5 + q) * nc + c] = h[q].v.x;
       }
       if (flB) {
         const long long c = (long long)yB * g.nx + x;
@@ -293,6 +297,8 @@ tile_cells(const unsigned char *stg, int ey_off, S *fout, int x0, int y0, int ti
         macro_out[2 * nc + c] = m.vy.v.y;
         macro_out[3 * nc + c] = Fx.v.y;
         macro_out[4 * nc + c] = Fy.v.y;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) macro_out[(5 + q) * nc + c] = h[q].v.y;
       }
     }
     // the output in the stored scale (FP16: 2^8 h)
@@ -982,8 +988,9 @@ template <typename R> static Stir<R> to_stir(const HostStir &h) {
   return s;
 }
 
-// STORE: the variant that also keeps each fluid cell's Landau solution and force (the
-// gradient's recomputation); the regular kernel is compiled without that store.
+// STORE: the variant that also keeps each fluid cell's Landau solution, force and streamed
+// deviations h (5 + Q planes of nx * ny values; the gradient's recomputation); the regular
+// kernel is compiled without that store.
 template <typename S, int VS, bool MASK, bool FORCE, int NST, bool STORE>
 static cudaError_t launch_step_k(const CUtensorMap &tin, const CUtensorMap &tG, const CUtensorMap &tEY, void *fout,
                                  const Geometry<typename RealOf<S>::type> &g, const Physics<typename RealOf<S>::type> &p,

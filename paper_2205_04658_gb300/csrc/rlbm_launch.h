@@ -108,8 +108,9 @@ struct AdjointArgs {
   const void *tB, *tK;     // host CUtensorMap load maps of B and kin (the layout of the state)
   bool chained;            // the launch directly follows the reverse step of step n + 1 on the
                            // stream, and B was written before that step (programmatic launch)
-  const void *macro;       // the step's eps/eps0 - 1, v_x, v_y, F_x, F_y per cell from the forward
-                           // recomputation (5 planes of nx * ny), or NULL
+  const void *macro;       // the step's eps/eps0 - 1, v_x, v_y, F_x, F_y and streamed h_0 .. h_{Q-1}
+                           // per cell from the forward recomputation (5 + Q planes of nx * ny), or
+                           // NULL (then B is pulled and matched: the objective of the last state)
   void *kout;              // kappa_n
   double cj;               // objective weight of the state S_n
   double *acc;             // [blocks][4] FP64 accumulators
