@@ -331,7 +331,7 @@ RLBM_API rlbm_status rlbm_set_mode_scale(rlbm_ctx *ctx, const double *sigma, int
  * pass.  The recomputation keeps, for every step of the segment in hand, the step's Landau
  * solution, force and streamed deviations h (5 + 17 values per cell for the paper's set,
  * in the storage type), which the reverse steps read.  segment >= nsteps keeps those
- * values for every step instead (one segment, e.g. 46 GB for 512^2 FP32 and 2000 steps):
+ * values for every step instead (one segment, e.g. 54 GB for 512^2 FP32 and 2000 steps):
  * the forward runs once and no step is recomputed.  The results do not depend on segment.  It returns J and dJ/dsigma_m (host, rlbm_num_modes values; may be NULL),
  * dJ/d(eta/s) (host, 1; may be NULL) and dJ/dF_body (host, 2; may be NULL; zero for the
  * eight-direction set, which has no force term), evaluated at
