@@ -68,8 +68,10 @@ typedef enum {
  * h_i = f_i / (w_i eps0) - 1 in that type and compute in it (F32 falls back to FP64
  * for the Landau solve of a cell whose |v| exceeds fp64_landau_vmax or whose FP32
  * Newton solve does not converge).  F16 and BF16 store h_i in 16 bits and compute
- * in FP32: BF16 holds h_i, F16 holds 256 h_i (so |h_i| < 255; the scale keeps the
- * deviations down to 2^-22 in FP16's normal range).  rlbm_get_state / rlbm_set_state
+ * in FP32: BF16 holds h_i, F16 holds 256 h_i (the scale keeps the deviations down to
+ * 2^-22 in FP16's normal range; |h_i| is held up to 255.9, and a larger value is stored
+ * as that limit by the stochastic rounding, or as infinity by round to nearest, which the
+ * next step reports as E_UNSTABLE).  rlbm_get_state / rlbm_set_state
  * exchange h_i itself; the scale is internal. */
 typedef enum { RLBM_F64 = 0, RLBM_F32 = 1, RLBM_F16 = 2, RLBM_BF16 = 3 } rlbm_precision;
 
