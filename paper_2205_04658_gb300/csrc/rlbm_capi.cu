@@ -1376,7 +1376,7 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   char *w = static_cast<char *>(dev_workspace);
   auto ckpt = [&](int k) { return w + G.ckpt + G.state_bytes * (size_t)k; };
   auto slot = [&](int j) { return w + G.slots + G.state_bytes * (size_t)j; };
-  std::vector<CUtensorMap> mck(G.K), msl(G.nslots), mgt;
+  std::vector<CUtensorMap> mck(G.K), msl(G.nslots);
   for (int k = 0; k < G.K; ++k) {
     const std::string m = encode_state_map(c, ckpt(k), &mck[k]);
     if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
@@ -1392,17 +1392,19 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
     if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
   }
   auto gtab = [&](int j) { return w + G.gst + G.table_bytes * (size_t)j; };
+  // the load maps of the per-step stirring rows are encoded as the steps are queued (not
+  // all before the first launch), so that the host work overlaps the GPU's
   const bool staged_rows = c->L.nrows > 0 && c->L.nrows <= 16;
-  if (staged_rows) {
-    mgt.resize(G.seg);
-    for (int j = 0; j < G.seg; ++j) {
-      const std::string m = encode_table_map(c, gtab(j), &mgt[j]);
-      if (!m.empty()) return c->fail(RLBM_E_CUDA, m);
-    }
-  }
+  std::string map_error;
   cudaError_t e;
-  // ghost rows of wall-bounded lattices are never written: start from zeroed buffers
-  if ((e = cudaMemsetAsync(w, 0, G.total, c->stream)) != cudaSuccess) return c->cuda_fail(e, "cudaMemsetAsync");
+  // Zeroed before use: the state and adjoint buffers (ghost rows of wall-bounded lattices
+  // are never written) and the tile accumulators (added to), which lie together from ckpt up
+  // to the stirring-row store, and the scratch state.  Everything else in the workspace is
+  // written before it is read (the stored per-step values of a cell only where it is fluid,
+  // and only those are read), so the tens of GB of one-segment runs are not cleared.
+  if ((e = cudaMemsetAsync(w + G.ckpt, 0, G.gst - G.ckpt, c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(w + G.scratch, 0, G.state_bytes, c->stream)) != cudaSuccess)
+    return c->cuda_fail(e, "cudaMemsetAsync");
 
   // forward: B_{-1} (the context's buffer) to checkpoint 0; B_{k seg - 1} into checkpoint k.
   // With one segment the recomputation of that segment (below) is the forward itself: it
@@ -1482,14 +1484,22 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
       }
       c->phys.step = s0 + n;
       void *fout = n == hi - 1 ? w + G.scratch : slot((int)((n - lo) & 1));
-      if ((e2 = dispatch_step_raw(c, ti, fout, s0 + n, st, staged_rows ? &mgt[(int)(n - lo)] : nullptr, n > lo,
+      CUtensorMap mg_n;  // copied into the launch's parameters
+      if (staged_rows) {
+        map_error = encode_table_map(c, gtab((int)(n - lo)), &mg_n);
+        if (!map_error.empty()) return cudaErrorInvalidValue;
+      }
+      if ((e2 = dispatch_step_raw(c, ti, fout, s0 + n, st, staged_rows ? &mg_n : nullptr, n > lo,
                                   w + G.macro + G.macro_bytes * (size_t)(n - lo))) != cudaSuccess)
         return e2;
     }
     return cudaSuccess;
   };
   if (one_pass) {
-    if ((e = recompute(0, 0, nsteps)) != cudaSuccess) return c->cuda_fail(e, "step kernel launch (forward)");
+    if ((e = recompute(0, 0, nsteps)) != cudaSuccess) {
+      if (!map_error.empty()) return c->fail(RLBM_E_CUDA, map_error);
+      return c->cuda_fail(e, "step kernel launch (forward)");
+    }
     // the state after the run, B_{N-1}, into a context buffer, as rlbm_step(N) would leave it
     const int dst = c->cur ^ 1;
     if ((e = cudaMemcpyAsync(c->ws + c->L.pop[dst], w + G.scratch, G.state_bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
@@ -1511,7 +1521,10 @@ rlbm_status rlbm_gradient(rlbm_ctx *c, int64_t nsteps, int32_t segment, void *de
   if ((e = dispatch_adjoint(c, a)) != cudaSuccess) return c->cuda_fail(e, "adjoint kernel launch");
   for (int k = G.K - 1; k >= 0; --k) {
     const int64_t lo = (int64_t)k * G.seg, hi = std::min<int64_t>(lo + G.seg, nsteps);
-    if (!one_pass && (e = recompute(k, lo, hi)) != cudaSuccess) return c->cuda_fail(e, "step kernel launch (recompute)");
+    if (!one_pass && (e = recompute(k, lo, hi)) != cudaSuccess) {
+      if (!map_error.empty()) return c->fail(RLBM_E_CUDA, map_error);
+      return c->cuda_fail(e, "step kernel launch (recompute)");
+    }
     for (int64_t n = hi - 1; n >= lo; --n) {
       a.B = ckpt(k);  // (not read: the step's streamed h is in its stored values)
       a.tB = &mck[k];
