@@ -648,45 +648,53 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
         }
       }
     }
-    // projections of the force adjoint on the k_y rows of the stirring tables
-    if (FORCE && st.nrows > 0) {
-      sF[2 * ly][lx] = R2<float>{gFx.v.x, gFy.v.x};
-      sF[2 * ly + 1][lx] = R2<float>{gFx.v.y, gFy.v.y};
-      if (tid < ney) sE[tid >> 3][tid & 7] = ey0;
-      if (tid + NT < ney) sE[(tid + NT) >> 3][tid & 7] = ey1;
-      __syncthreads();
-      const int jmax = g.ny - ty * TILE_Y;  // rows of this tile inside the lattice (>= 1)
-      for (int r = warp; r < st.nrows; r += NT / 32) {
-        R4<float> z{0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          if (j < jmax) {
-            const R2<float> E = ey_shared ? sE[r][j]
-                                          : ey_at<float>(reinterpret_cast<const float *>(st.EY) +
-                                                             (long long)r * 2 * st.eyp, ty * TILE_Y + j);
-            const R2<float> F = sF[j][lx];
-            z.x += F.x * E.x;
-            z.y += F.x * E.y;
-            z.z += F.y * E.x;
-            z.w += F.y * E.y;
-          }
-        }
-        if (x < g.nx) zpart[((long long)ty * st.nrows + r) * g.nx + x] = z;
-      }
-    }
     // tile sums (fixed order): the two cells of a thread, warp sums in FP32, the four warp
-    // sums in FP64
+    // sums in FP64; the warp sums go to shared memory with the projections' inputs, so that
+    // one barrier serves both
     float v[4] = {gom.v.x + gom.v.y, gFx.v.x + gFx.v.y, gFy.v.x + gFy.v.y, jv.v.x + jv.v.y};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], off);
       if (lane == 0) red[warp][c] = (double)v[c];
     }
+    const bool proj = FORCE && st.nrows > 0;
+    if (proj) {
+      sF[2 * ly][lx] = R2<float>{gFx.v.x, gFy.v.x};
+      sF[2 * ly + 1][lx] = R2<float>{gFx.v.y, gFy.v.y};
+      if (tid < ney) sE[tid >> 3][tid & 7] = ey0;
+      if (tid + NT < ney) sE[(tid + NT) >> 3][tid & 7] = ey1;
+    }
     __syncthreads();
     if (tid < 4) {
       double sum = 0.0;
       for (int w4 = 0; w4 < NT / 32; ++w4) sum += red[w4][tid];
       atomicAdd(&acc[(long long)t * 4 + tid], sum);
+    }
+    // projections of the force adjoint on the k_y rows of the stirring tables: the column's
+    // 8 values of gF loaded once, (x, y) and (z, w) of each row's sum on packed pairs
+    if (proj) {
+      const int jmax = g.ny - ty * TILE_Y;  // rows of this tile inside the lattice (>= 1)
+      F2 Fx8[8], Fy8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const R2<float> F = sF[j][lx];
+        Fx8[j] = F2(j < jmax ? F.x : 0.0f);
+        Fy8[j] = F2(j < jmax ? F.y : 0.0f);
+      }
+      for (int r = warp; r < st.nrows; r += NT / 32) {
+        F2 zxy(0.0f), zzw(0.0f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const R2<float> E = ey_shared ? sE[r][j]
+                                        : (j < jmax ? ey_at<float>(reinterpret_cast<const float *>(st.EY) +
+                                                                       (long long)r * 2 * st.eyp, ty * TILE_Y + j)
+                                                    : R2<float>{0.0f, 0.0f});
+          const F2 e(E.x, E.y);
+          zxy = fma(Fx8[j], e, zxy);
+          zzw = fma(Fy8[j], e, zzw);
+        }
+        if (x < g.nx) zpart[((long long)ty * st.nrows + r) * g.nx + x] = R4<float>{zxy.v.x, zxy.v.y, zzw.v.x, zzw.v.y};
+      }
     }
     if (NST == 1) {  // the only stage is free once every thread is done with it
       __syncthreads();
@@ -723,55 +731,67 @@ __global__ void zsum_kernel(const R4<R> *__restrict__ zpart, int nby, int nrows,
   zsum[(j * nrows + r) * nx + x] = s;
 }
 
+constexpr int MG_THREADS = 128;        // threads of a mode-gradient block
+constexpr int MG_MAX_ROW_MODES = 64;   // modes of one k_y row reduced per pass
+static_assert(MG_MAX_ROW_MODES <= MG_THREADS, "one thread per mode finishes a pass");
+
 // gstep[j][m] = d/d sigma_m of sum_x gF(x) . F(x) for the draws of step n0 + j
-// (blockIdx.x = m, blockIdx.y = j):
+// (blockIdx.x = k_y row, blockIdx.y = j):
 //   F(x, y) = sum_m sigma_m Re[(cx_m, cy_m) exp(i 2 pi (k_x x / nx + k_y y / ny))],
 // so the derivative is Re[cx_m W_x] + Re[cy_m W_y] with W = sum_x exp(i 2 pi k_x x / nx) zsum_r(x).
 // The per-step values are summed over all steps, in step order, at the end of the run,
 // so the checkpoint segmentation does not change a bit.
 template <typename R>
-__global__ void mode_grad_kernel(const R4<R> *__restrict__ zsum, int nrows, const R2<R> *__restrict__ tw,
-                                 const int *__restrict__ mode_kx, const int *__restrict__ row_start, int nx,
-                                 unsigned long long seed, long long n0, double amp, int nmodes,
-                                 double *__restrict__ gstep) {
-  const int mo = blockIdx.x, j = blockIdx.y;
-  int r = 0;
-  while (row_start[r + 1] <= mo) ++r;
-  const int kx = mode_kx[mo];
+__global__ void __launch_bounds__(MG_THREADS)
+mode_grad_kernel(const R4<R> *__restrict__ zsum, int nrows, const R2<R> *__restrict__ tw,
+                 const int *__restrict__ mode_kx, const int *__restrict__ row_start, int nx,
+                 unsigned long long seed, long long n0, double amp, int nmodes, double *__restrict__ gstep) {
+  // one block per (k_y row r, step j): the row's transform is read from L2 for all its modes,
+  // MG_MAX_ROW_MODES modes at a time
+  const int r = blockIdx.x, j = blockIdx.y;
   const R4<R> *zs = zsum + ((long long)j * nrows + r) * nx;
-  R a[4] = {R(0), R(0), R(0), R(0)};
-  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-    int t = (kx * x) % nx;
-    if (t < 0) t += nx;
-    const R2<R> e = tw[t];
-    const R4<R> z = zs[x];
-    a[0] += e.x * z.x - e.y * z.y;
-    a[1] += e.x * z.y + e.y * z.x;
-    a[2] += e.x * z.z - e.y * z.w;
-    a[3] += e.x * z.w + e.y * z.z;
-  }
-  __shared__ double red[8][4];
+  __shared__ double red[MG_MAX_ROW_MODES][MG_THREADS / 32][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = row_start[r], m1 = row_start[r + 1]; c0 < m1; c0 += MG_MAX_ROW_MODES) {
+    const int c1 = min(m1, c0 + MG_MAX_ROW_MODES);
+    for (int mo = c0; mo < c1; ++mo) {
+      const int kx = mode_kx[mo];
+      R a[4] = {R(0), R(0), R(0), R(0)};
+      for (int x = threadIdx.x; x < nx; x += MG_THREADS) {
+        int t = (kx * x) % nx;
+        if (t < 0) t += nx;
+        const R2<R> e = tw[t];
+        const R4<R> z = zs[x];
+        a[0] += e.x * z.x - e.y * z.y;
+        a[1] += e.x * z.y + e.y * z.x;
+        a[2] += e.x * z.z - e.y * z.w;
+        a[3] += e.x * z.w + e.y * z.z;
+      }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    double v = (double)a[k];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) red[warp][k] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double W[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8)
-      for (int k = 0; k < 4; ++k) W[k] += red[w8][k];
-    double c[4];
-    if constexpr (sizeof(R) == 8) {
-      stir_draw(seed, n0 + j, mo, amp, c);
-    } else {
-      float cf[4];
-      stir_draw_f32(seed, n0 + j, mo, (float)amp, cf);
-      for (int k = 0; k < 4; ++k) c[k] = (double)cf[k];
+      for (int k = 0; k < 4; ++k) {
+        double v = (double)a[k];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[mo - c0][warp][k] = v;
+      }
     }
-    gstep[(long long)j * nmodes + mo] = c[0] * W[0] - c[1] * W[1] + c[2] * W[2] - c[3] * W[3];
+    __syncthreads();
+    // the draws of the step and the derivative: one thread per mode
+    const int mo = c0 + (int)threadIdx.x;
+    if (mo < c1) {
+      double W[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int w = 0; w < MG_THREADS / 32; ++w)
+        for (int k = 0; k < 4; ++k) W[k] += red[mo - c0][w][k];
+      double c[4];
+      if constexpr (sizeof(R) == 8) {
+        stir_draw(seed, n0 + j, mo, amp, c);
+      } else {
+        float cf[4];
+        stir_draw_f32(seed, n0 + j, mo, (float)amp, cf);
+        for (int k = 0; k < 4; ++k) c[k] = (double)cf[k];
+      }
+      gstep[(long long)j * nmodes + mo] = c[0] * W[0] - c[1] * W[1] + c[2] * W[2] - c[3] * W[3];
+    }
+    __syncthreads();  // red is refilled by the next chunk
   }
 }
 
@@ -875,8 +895,9 @@ static cudaError_t launch_mode_grads_t(const ModeGradArgs &a, cudaStream_t st) {
   zsum_kernel<R><<<dim3((a.nx + 127) / 128, a.nrows, a.nj), 128, 0, st>>>((const R4<R> *)a.zpart, a.nby, a.nrows, a.nx,
                                                                          (R4<R> *)a.zsum);
   const void *tw = sizeof(R) == 8 ? a.tw : a.twf;
-  mode_grad_kernel<R><<<dim3(a.nmodes, a.nj), 256, 0, st>>>((const R4<R> *)a.zsum, a.nrows, (const R2<R> *)tw, a.mode_kx,
-                                                           a.row_start, a.nx, a.seed, a.n0, a.amp, a.nmodes, a.gstep);
+  mode_grad_kernel<R><<<dim3(a.nrows, a.nj), MG_THREADS, 0, st>>>((const R4<R> *)a.zsum, a.nrows, (const R2<R> *)tw,
+                                                                  a.mode_kx, a.row_start, a.nx, a.seed, a.n0, a.amp,
+                                                                  a.nmodes, a.gstep);
   return cudaGetLastError();
 }
 
