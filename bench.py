@@ -680,6 +680,12 @@ def run_forms(args, torch, rlbm, flush):
     errs = graphene_errors(rlbm, ["f32", "f16", "bf16"])
     for p in ("f16", "f32", "bf16"):
         forms["c3_graphene2048x512_%s" % p] = dict(form_graphene(args, torch, rlbm, flush, p), error=errs[p])
+    # the config's other impurity fractions (geometry seeds 31, 35), timed in FP16 and FP32
+    # (their errors are those of the same storage forms on the 15 % sample above)
+    for frac, gseed in ((0.01, 31), (0.05, 35)):
+        for p in ("f16", "f32"):
+            forms["c3_graphene2048x512_%dpct_%s" % (round(100 * frac), p)] = form_graphene(
+                args, torch, rlbm, flush, p, frac=frac, gseed=gseed)
     errs = ensemble_errors(rlbm, ["f32", "f16", "bf16"])
     plain = form_plain_members(args, torch, rlbm, form_sides())
     plain["error"] = errs["f32"]
