@@ -492,7 +492,7 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
   unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * STAGE);
   __shared__ R2<float> sF[8][32];
-  __shared__ R2<float> sE[32][8];  // the tile's phase rows EY_r(y0 + j) of the projections
+  __shared__ __align__(16) R2<float> sE[32][8];  // the tile's phase rows EY_r(y0 + j) of the projections
   __shared__ double red[4][4];
   const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5, lane = tid & 31, warp = tid >> 5;
   const int wid = blockIdx.x, nworkers = gridDim.x;
@@ -681,19 +681,50 @@ adjoint_pair_kernel(const __grid_constant__ CUtensorMap tB, const __grid_constan
         Fx8[j] = F2(j < jmax ? F.x : 0.0f);
         Fy8[j] = F2(j < jmax ? F.y : 0.0f);
       }
-      for (int r = warp; r < st.nrows; r += NT / 32) {
-        F2 zxy(0.0f), zzw(0.0f);
+      if (ey_shared) {
+        // two rows per warp at a time, each row's sums in two halves (even and odd j), so that
+        // four independent FMA chains of four run at once; the phase rows in 16-byte loads
+        for (int r = warp; r < st.nrows; r += 2 * (NT / 32)) {
+          const int r2 = r + NT / 32;
+          const bool two = r2 < st.nrows;
+          const int rb = two ? r2 : r;  // (a second row past the last computes nothing stored)
+          F2 a0(0.0f), a1(0.0f), a2(0.0f), a3(0.0f), b0(0.0f), b1(0.0f), b2(0.0f), b3(0.0f);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const R2<float> E = ey_shared ? sE[r][j]
-                                        : (j < jmax ? ey_at<float>(reinterpret_cast<const float *>(st.EY) +
-                                                                       (long long)r * 2 * st.eyp, ty * TILE_Y + j)
-                                                    : R2<float>{0.0f, 0.0f});
-          const F2 e(E.x, E.y);
-          zxy = fma(Fx8[j], e, zxy);
-          zzw = fma(Fy8[j], e, zzw);
+          for (int j = 0; j < 8; j += 2) {
+            const float4 ea = *reinterpret_cast<const float4 *>(&sE[r][j]);
+            const float4 eb = *reinterpret_cast<const float4 *>(&sE[rb][j]);
+            a0 = fma(Fx8[j], F2(ea.x, ea.y), a0);
+            a1 = fma(Fy8[j], F2(ea.x, ea.y), a1);
+            a2 = fma(Fx8[j + 1], F2(ea.z, ea.w), a2);
+            a3 = fma(Fy8[j + 1], F2(ea.z, ea.w), a3);
+            b0 = fma(Fx8[j], F2(eb.x, eb.y), b0);
+            b1 = fma(Fy8[j], F2(eb.x, eb.y), b1);
+            b2 = fma(Fx8[j + 1], F2(eb.z, eb.w), b2);
+            b3 = fma(Fy8[j + 1], F2(eb.z, eb.w), b3);
+          }
+          if (x < g.nx) {
+            const F2 zxy = a0 + a2, zzw = a1 + a3;
+            zpart[((long long)ty * st.nrows + r) * g.nx + x] = R4<float>{zxy.v.x, zxy.v.y, zzw.v.x, zzw.v.y};
+            if (two) {
+              const F2 uxy = b0 + b2, uzw = b1 + b3;
+              zpart[((long long)ty * st.nrows + r2) * g.nx + x] = R4<float>{uxy.v.x, uxy.v.y, uzw.v.x, uzw.v.y};
+            }
+          }
         }
-        if (x < g.nx) zpart[((long long)ty * st.nrows + r) * g.nx + x] = R4<float>{zxy.v.x, zxy.v.y, zzw.v.x, zzw.v.y};
+      } else {
+        for (int r = warp; r < st.nrows; r += NT / 32) {
+          F2 zxy(0.0f), zzw(0.0f);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const R2<float> E = j < jmax ? ey_at<float>(reinterpret_cast<const float *>(st.EY) +
+                                                            (long long)r * 2 * st.eyp, ty * TILE_Y + j)
+                                         : R2<float>{0.0f, 0.0f};
+            const F2 e(E.x, E.y);
+            zxy = fma(Fx8[j], e, zxy);
+            zzw = fma(Fy8[j], e, zzw);
+          }
+          if (x < g.nx) zpart[((long long)ty * st.nrows + r) * g.nx + x] = R4<float>{zxy.v.x, zxy.v.y, zzw.v.x, zzw.v.y};
+        }
       }
     }
     if (NST == 1) {  // the only stage is free once every thread is done with it
